@@ -1,0 +1,349 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Every check here is computed by a route other than the oracle's own: weighted
+linear least squares (numpy.linalg.lstsq) for Lomb-Scargle and multi-harmonic
+fits, a dense brute-force phase scan with Brent refinement, residual-based
+chi^2, closed-form identities of the final polynomial, and invariances of the
+model y ~ theta1 M(omega t - theta2) + theta3 (Section 2)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize_scalar
+
+import oracle
+import synth
+
+TWO_PI = 2.0 * math.pi
+
+
+# ---------------------------------------------------------------- helpers
+def wls_power(t, y, dy, design):
+    """1 - chi^2/chi^2_0 for a weighted linear least-squares fit of y on the
+    columns of `design` (which must include a constant column)."""
+    w = dy ** -2.0
+    sw = np.sqrt(w)
+    coef, *_ = np.linalg.lstsq(design * sw[:, None], y * sw, rcond=None)
+    chi2 = np.sum(w * (y - design @ coef) ** 2)
+    ybar = np.sum(w * y) / np.sum(w)
+    chi20 = np.sum(w * (y - ybar) ** 2)
+    return 1.0 - chi2 / chi20, coef
+
+
+def ls_power(t, y, dy, f):
+    """Floating-mean (generalised) Lomb-Scargle power at frequency f."""
+    x = TWO_PI * f * t
+    return wls_power(t, y, dy, np.column_stack([np.ones_like(t), np.cos(x), np.sin(x)]))[0]
+
+
+def mhls_power(t, y, dy, f, H):
+    cols = [np.ones_like(t)]
+    for h in range(1, H + 1):
+        cols += [np.cos(TWO_PI * h * f * t), np.sin(TWO_PI * h * f * t)]
+    return wls_power(t, y, dy, np.column_stack(cols))[0]
+
+
+def template_values(c, s, x):
+    out = np.zeros_like(x)
+    for n in range(1, len(c) + 1):
+        out += c[n - 1] * np.cos(n * x) + s[n - 1] * np.sin(n * x)
+    return out
+
+
+def residual_power(t, y, dy, f, c, s, theta2):
+    """P(theta2) from the chi^2 of the best (theta1, theta3), solved as a
+    2-column weighted least-squares problem; vectorised over theta2."""
+    theta2 = np.atleast_1d(theta2)
+    w = dy ** -2.0
+    w = w / w.sum()
+    M = template_values(c, s, TWO_PI * f * t[None, :] - theta2[:, None])  # [K, N]
+    # normal equations of y ~ a M + b, solved per row by Cramer's rule
+    s_m = M @ w
+    s_mm = (M * M) @ w
+    s_y = w @ y
+    s_my = M @ (w * y)
+    det = s_mm - s_m * s_m
+    a = (s_my - s_m * s_y) / det
+    b = (s_mm * s_y - s_m * s_my) / det
+    chi2 = ((y[None, :] - a[:, None] * M - b[:, None]) ** 2) @ w
+    chi20 = w @ (y - s_y) ** 2
+    return 1.0 - chi2 / chi20, a, b
+
+
+def brute_force_best(t, y, dy, f, c, s, n_grid=1 << 16):
+    th = np.linspace(0.0, TWO_PI, n_grid, endpoint=False)
+    P = np.concatenate([residual_power(t, y, dy, f, c, s, th[i:i + 4096])[0]
+                        for i in range(0, n_grid, 4096)])
+    best = None
+    for i in np.argsort(P)[-8:]:          # refine the few best grid points
+        h = TWO_PI / n_grid
+        r = minimize_scalar(lambda x: -residual_power(t, y, dy, f, c, s, x)[0][0],
+                            bounds=(th[i] - 2 * h, th[i] + 2 * h), method="bounded",
+                            options={"xatol": 1e-12})
+        if best is None or -r.fun > best[0]:
+            best = (-r.fun, r.x % TWO_PI)
+    return best
+
+
+def small_case(seed, n_obs=40, H=3, signal=0.3, T=8.0):
+    rng = np.random.default_rng(seed)
+    tpl = synth.make_template(H, 3000 + seed)
+    lc = synth.random_curve(rng, n_obs, T=T, signal=signal, tpl=tpl, period=1.7, phase=0.4)
+    return lc, tpl
+
+
+# ---------------------------------------------------------------- pins
+@pytest.mark.parametrize("seed", range(4))
+def test_h1_is_floating_mean_lomb_scargle(seed):
+    """H = 1: the template periodogram is the floating-mean LS periodogram
+    (Section 3, accuracy discussion; Section 1 model)."""
+    rng = np.random.default_rng(seed)
+    lc = synth.random_curve(rng, 60, T=10.0)
+    lc.y += 0.2 * np.cos(TWO_PI * lc.t / 1.3 + 0.4)
+    c, s = np.array([rng.normal()]), np.array([rng.normal()])
+    freqs = rng.uniform(0.05, 3.0, 12)
+    r = oracle.periodogram(lc.t, lc.y, lc.dy, freqs, c, s)
+    ref = np.array([ls_power(lc.t, lc.y, lc.dy, f) for f in freqs])
+    np.testing.assert_allclose(r["power"], ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("h", [2, 3])
+def test_single_harmonic_template_is_ls_at_harmonic(h):
+    """A template with only c_h, s_h non-zero is a sinusoid at h*omega: its
+    periodogram equals LS at frequency h*f (harmonic indexing of the sums)."""
+    rng = np.random.default_rng(10 + h)
+    lc = synth.random_curve(rng, 50, T=9.0)
+    lc.y += 0.3 * np.sin(TWO_PI * lc.t / 0.9)
+    c, s = np.zeros(h), np.zeros(h)
+    c[h - 1], s[h - 1] = 0.7, -0.4
+    freqs = rng.uniform(0.05, 1.5, 8)
+    r = oracle.periodogram(lc.t, lc.y, lc.dy, freqs, c, s)
+    ref = np.array([ls_power(lc.t, lc.y, lc.dy, h * f) for f in freqs])
+    np.testing.assert_allclose(r["power"], ref, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed,H", [(0, 2), (1, 3), (2, 4), (3, 3)])
+def test_brute_force_phase_scan(seed, H):
+    """Dense theta2 scan + Brent with residual-based chi^2: the oracle's best
+    power is never below brute force and agrees to 1e-10."""
+    lc, tpl = small_case(seed, H=H, signal=0.25 if seed % 2 else 0.0)
+    rng = np.random.default_rng(100 + seed)
+    for f in rng.uniform(0.1, 2.0, 3):
+        r = oracle.periodogram(lc.t, lc.y, lc.dy, [f], tpl.c, tpl.s)
+        Pb, thb = brute_force_best(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+        assert r["power"][0] >= Pb - 1e-12
+        assert abs(r["power"][0] - Pb) <= 1e-10
+        # the oracle's (theta1, theta3) reproduce its power via the residuals
+        Pr, a, b = residual_power(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s, r["theta2"][0])
+        assert abs(Pr[0] - r["power"][0]) <= 1e-10
+        assert abs(a[0] - r["theta1"][0]) <= 1e-8 * max(1.0, abs(a[0]))
+        assert abs(b[0] - r["theta3"][0]) <= 1e-8 * max(1.0, abs(b[0]))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bounds_and_mhls_ceiling(seed):
+    """0 <= P_FTP <= P_MHLS(H) <= 1: the template model is nested in the
+    multi-harmonic model with 2H+1 free parameters (Section 1)."""
+    lc, tpl = small_case(seed, n_obs=45, H=3, signal=0.2)
+    freqs = np.random.default_rng(seed).uniform(0.05, 2.5, 25)
+    r = oracle.periodogram(lc.t, lc.y, lc.dy, freqs, tpl.c, tpl.s)
+    mh = np.array([mhls_power(lc.t, lc.y, lc.dy, f, tpl.H) for f in freqs])
+    assert np.all(r["power"] >= -1e-15)
+    assert np.all(r["power"] <= mh + 1e-10)
+    assert np.all(mh <= 1 + 1e-12)
+
+
+@pytest.mark.parametrize("H", [2, 3, 5])
+def test_noiseless_injection_recovers_parameters(H):
+    """y = A M(omega0 t - phi0) + B exactly: P(omega0) = 1 and theta = (A, phi0, B)."""
+    rng = np.random.default_rng(50 + H)
+    tpl = synth.make_template(H, 4000 + H)
+    t = np.sort(rng.uniform(0, 12.0, 70))
+    f0, A, phi0, B = 0.83, 1.7, 2.2, -0.35
+    y = A * tpl(TWO_PI * f0 * t - phi0) + B
+    dy = rng.uniform(0.05, 0.2, t.size)
+    r = oracle.periodogram(t, y, dy, [f0], tpl.c, tpl.s)
+    assert abs(r["power"][0] - 1.0) < 1e-10
+    assert abs(r["theta1"][0] - A) < 1e-8
+    assert abs(np.angle(np.exp(1j * (r["theta2"][0] - phi0)))) < 1e-8
+    assert abs(r["theta3"][0] - B) < 1e-8
+
+
+def test_invariances():
+    """Time shift moves theta2 by omega*Delta; y -> a y + b rescales theta1,
+    theta3 only; sigma -> lambda sigma and (c, s) -> lambda (c, s) leave P
+    unchanged; rotating the template by phi moves theta2 by -phi."""
+    lc, tpl = small_case(7, n_obs=50, H=3, signal=0.4)
+    f = 1.0 / 1.7
+    base = oracle.periodogram(lc.t, lc.y, lc.dy, [f], tpl.c, tpl.s)
+    P0, a0, th0, b0 = (base[k][0] for k in ("power", "theta1", "theta2", "theta3"))
+
+    d = 3.3
+    r = oracle.periodogram(lc.t + d, lc.y, lc.dy, [f], tpl.c, tpl.s)
+    assert abs(r["power"][0] - P0) < 1e-10
+    assert abs(np.angle(np.exp(1j * (r["theta2"][0] - th0 - TWO_PI * f * d)))) < 1e-8
+
+    r = oracle.periodogram(lc.t, 2.5 * lc.y - 4.0, lc.dy, [f], tpl.c, tpl.s)
+    assert abs(r["power"][0] - P0) < 1e-10
+    assert abs(r["theta1"][0] - 2.5 * a0) < 1e-8
+    assert abs(r["theta3"][0] - (2.5 * b0 - 4.0)) < 1e-8
+
+    r = oracle.periodogram(lc.t, lc.y, 7.0 * lc.dy, [f], 3.0 * tpl.c, 3.0 * tpl.s)
+    assert abs(r["power"][0] - P0) < 1e-10
+    assert abs(r["theta1"][0] - a0 / 3.0) < 1e-8
+
+    phi = 0.9
+    n = np.arange(1, tpl.H + 1)
+    c2 = tpl.c * np.cos(n * phi) - tpl.s * np.sin(n * phi)
+    s2 = tpl.c * np.sin(n * phi) + tpl.s * np.cos(n * phi)
+    r = oracle.periodogram(lc.t, lc.y, lc.dy, [f], c2, s2)
+    assert abs(r["power"][0] - P0) < 1e-10
+    assert abs(np.angle(np.exp(1j * (r["theta2"][0] - (th0 - phi))))) < 1e-8
+
+
+@pytest.mark.parametrize("H", [1, 3, 6])
+def test_final_polynomial_identities(H):
+    """The psi^{6H-1} coefficient of 2 MM' d(YM') - YM' d(MM') vanishes, so
+    the degree is 6H-2; and F is anti-self-inversive, F_{D-j} = -conj(F_j),
+    because MM' and YM' are self-inversive (real MM, YM on |psi| = 1)."""
+    lc, tpl = small_case(20 + H, n_obs=60, H=H, signal=0.3)
+    for f in (0.31, 0.77, 1.9):
+        pol = oracle.polynomials_at(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+        F = pol["F"]
+        assert len(F) == 6 * H - 1
+        scale = np.max(np.abs(F))
+        assert abs(pol["top"]) <= 1e-14 * scale
+        np.testing.assert_allclose(F[::-1], -np.conj(F), rtol=0, atol=1e-13 * scale)
+        MMp, YMp = pol["MMp"], pol["YMp"]
+        np.testing.assert_allclose(MMp[::-1], np.conj(MMp), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(YMp[::-1], np.conj(YMp), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("H", [2, 4])
+def test_polynomials_match_direct_evaluation(H):
+    """P(theta2) from the assembled polynomials, YM(psi)^2/(YY MM(psi)) with
+    YM = psi^-H YM'(psi) and MM = psi^-2H MM'(psi), equals P from a direct
+    residual fit at 50 random phases (1e-12)."""
+    lc, tpl = small_case(30 + H, n_obs=55, H=H, signal=0.35)
+    rng = np.random.default_rng(H)
+    for f in (0.45, 1.3):
+        pol = oracle.polynomials_at(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+        th = rng.uniform(0, TWO_PI, 50)
+        psi = np.exp(1j * th)
+        MM = np.polynomial.polynomial.polyval(psi, pol["MMp"]) * psi ** (-2 * H)
+        YM = np.polynomial.polynomial.polyval(psi, pol["YMp"]) * psi ** (-H)
+        assert np.max(np.abs(MM.imag)) < 1e-12 and np.max(np.abs(YM.imag)) < 1e-12
+        P_poly = YM.real ** 2 / (pol["YY"] * MM.real)
+        P_res = residual_power(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s, th)[0]
+        np.testing.assert_allclose(P_poly, P_res, rtol=0, atol=1e-12)
+
+
+def test_roots_are_stationary_points():
+    """Unit-circle roots of F are stationary points of P(theta2): the
+    numerical derivative of the residual-based P vanishes there."""
+    lc, tpl = small_case(41, n_obs=50, H=3, signal=0.3)
+    f = 0.61
+    pol = oracle.polynomials_at(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+    roots = np.polynomial.polynomial.polyroots(pol["F"])
+    on = roots[np.abs(np.abs(roots) - 1) < 1e-7]
+    assert on.size >= 2
+    h = 1e-5
+    for th in np.angle(on):
+        Pp = residual_power(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s, np.array([th - h, th + h]))[0]
+        P0 = residual_power(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s, np.array([th]))[0][0]
+        assert abs(Pp[1] - Pp[0]) / (2 * h) < 1e-6 * max(1.0, P0)
+
+
+def test_weight_rules_and_errors():
+    """Section 2: all sigma = 0 -> unit weights; mixed zero/non-zero sigma
+    and zero variance are rejected."""
+    t = np.linspace(0, 5, 20)
+    y = np.sin(t)
+    w = oracle.normalized_weights(np.zeros(20))
+    np.testing.assert_allclose(w, np.full(20, 1 / 20))
+    r0 = oracle.periodogram(t, y, np.zeros(20), [0.3], [1.0], [0.0])
+    r1 = oracle.periodogram(t, y, np.ones(20), [0.3], [1.0], [0.0])
+    assert abs(r0["power"][0] - r1["power"][0]) < 1e-14
+    dy = np.ones(20)
+    dy[3] = 0.0
+    with pytest.raises(oracle.OracleInputError):
+        oracle.periodogram(t, y, dy, [0.3], [1.0], [0.0])
+    with pytest.raises(oracle.OracleInputError):
+        oracle.periodogram(t, np.full(20, 2.0), np.ones(20), [0.3], [1.0], [0.0])
+    with pytest.raises(oracle.OracleInputError):
+        oracle.periodogram(t[:1], y[:1], dy[:1], [0.3], [1.0], [0.0])
+
+
+def test_small_workload_recovers_injected_period():
+    """Workload 1 (N=200, H=3): the highest peak sits within one grid step of
+    the injected frequency 1/2.37 d^-1 with P well above the noise floor."""
+    lc, tpl, grid = synth.small_curve()
+    f = grid.freqs()
+    sel = np.arange(0, grid.nf, 7)
+    near = np.flatnonzero(np.abs(f - 1 / 2.37) <= 2 * grid.df)
+    sel = np.union1d(sel, near)
+    r = oracle.periodogram(lc.t, lc.y, lc.dy, f[sel], tpl.c, tpl.s)
+    k = np.argmax(r["power"])
+    assert abs(f[sel][k] - 1 / 2.37) <= grid.df
+    assert r["power"][k] > 0.8
+
+
+# ------------------------------------------ planted mistakes must be caught
+def _mutant_mm_poly(alpha, CC, CS, SS):
+    """mm_poly with the sign of the CS - CS^T term flipped in CSt."""
+    H = alpha.shape[0]
+    CCt = (CC - SS) - 1j * (CS + CS.T)
+    CSt = (CC + SS) - 1j * (CS - CS.T)
+    SSt = (CC - SS) + 1j * (CS + CS.T)
+    out = np.zeros(4 * H + 1, dtype=np.complex128)
+    for n in range(1, H + 1):
+        for m in range(1, H + 1):
+            an, am = alpha[n - 1], alpha[m - 1]
+            out[2 * H + n + m] += an * am * CCt[n - 1, m - 1]
+            out[2 * H + n - m] += 2.0 * an * np.conj(am) * CSt[n - 1, m - 1]
+            out[2 * H - n - m] += np.conj(an) * np.conj(am) * SSt[n - 1, m - 1]
+    return out
+
+
+def _mutant_ym_poly(alpha, YC, YS):
+    """ym_poly with the conjugate term dropped."""
+    H = alpha.shape[0]
+    out = np.zeros(2 * H + 1, dtype=np.complex128)
+    for k in range(1, H + 1):
+        out[H + k] += alpha[k - 1] * (YC[k - 1] - 1j * YS[k - 1])
+    return out
+
+
+@pytest.mark.parametrize("mutant", ["csign", "ymdrop", "cstranspose"])
+def test_planted_mistakes_fail_a_pin(monkeypatch, mutant):
+    """A plausible mistake planted in the oracle (wrong sign, dropped term,
+    transposed operand) makes the brute-force / direct-evaluation pins fail."""
+    mod = oracle.ftp_oracle
+    if mutant == "csign":
+        monkeypatch.setattr(mod, "mm_poly", _mutant_mm_poly)
+    elif mutant == "ymdrop":
+        monkeypatch.setattr(mod, "ym_poly", _mutant_ym_poly)
+    else:
+        orig = mod.direct_sums
+
+        def transposed(*a, **k):
+            d = orig(*a, **k)
+            d["CS"] = d["CS"].T.copy()
+            return d
+        monkeypatch.setattr(mod, "direct_sums", transposed)
+    lc, tpl = small_case(3, n_obs=40, H=3, signal=0.3)
+    caught = False
+    for f in (0.37, 0.59, 1.21, 1.7):
+        r = mod.periodogram(lc.t, lc.y, lc.dy, [f], tpl.c, tpl.s)
+        Pb, _ = brute_force_best(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s, n_grid=1 << 12)
+        pol = mod.polynomials_at(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+        th = np.linspace(0.1, 6.0, 7)
+        psi = np.exp(1j * th)
+        MM = np.polynomial.polynomial.polyval(psi, pol["MMp"]) * psi ** (-2 * tpl.H)
+        YM = np.polynomial.polynomial.polyval(psi, pol["YMp"]) * psi ** (-tpl.H)
+        P_poly = YM.real ** 2 / (pol["YY"] * MM.real)
+        P_res = residual_power(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s, th)[0]
+        if abs(r["power"][0] - Pb) > 1e-8 or np.max(np.abs(P_poly - P_res)) > 1e-10:
+            caught = True
+            break
+    assert caught
