@@ -1,0 +1,183 @@
+/*
+ * ftp.h - C ABI of the GB300 (sm_103a) Fast Template Periodogram library.
+ *
+ * The Fast Template Periodogram (Hoffman, VanderPlas, Hartman & Bakos,
+ * arXiv 2101.12348) fits a fixed-shape periodic template
+ *     M(x) = sum_{n=1..H} c_n cos(n x) + s_n sin(n x)            (Section 2)
+ * to an irregularly sampled series S = {(t_i, y_i, sigma_i)} with the model
+ *     y ~ theta1 * M(omega t - theta2) + theta3,                  (Section 2)
+ * and reports at each trial frequency the power
+ *     P(omega) = 1 - chi^2_min / chi^2_0  in [0, 1]               (Eq. lsp)
+ * together with the best (theta1, theta2, theta3).  For every frequency the
+ * library runs three steps, all as CUDA kernels on one GPU:
+ *   (a) the weighted trigonometric sums at the harmonics h*omega, h <= 2H
+ *       (Eqs. CCdef-YSdef), by an adjoint NFFT: Kaiser-Bessel spreading onto an
+ *       oversampled grid, an equispaced FFT (cuFFT), deconvolution + gather;
+ *   (b) assembly of MM' = psi^{2H} MM and YM' = psi^H YM and of the final
+ *       polynomial 2 MM' d(YM') - YM' d(MM') in psi = exp(i theta2)
+ *       (Section 2, Eq. finalpoly), of degree 6H-2;
+ *   (c) all zeros of that polynomial by Aberth-Ehrlich iteration, scaled onto
+ *       the unit circle (Section 2, end), P evaluated at every candidate,
+ *       the best one polished by a Newton step in FP64.
+ *
+ * Conventions shared by every entry point
+ *   - Frequencies are in cycles per unit time, omega = 2 pi f.  The grid is
+ *     f_k = (k0 + k) * df, k = 0..nf-1, with k0 >= 1 (the NFFT needs the
+ *     harmonics h * f_k on the same integer lattice j * df; f = 0 excluded).
+ *   - theta2 is in radians in [0, 2 pi), relative to t = 0.
+ *   - Weights are w_i = sigma_i^-2 / sum sigma^-2.  All sigma_i = 0 means
+ *     unit weights (Section 2); a mix of zero and non-zero sigma returns
+ *     FTP_ERR_MIXED_ZERO_SIGMA; all-equal y (Var(y) = 0, P undefined) returns
+ *     FTP_ERR_ZERO_VARIANCE (Section 2); negative or non-finite inputs return
+ *     FTP_ERR_NONFINITE; fewer than 2 observations FTP_ERR_INVALID_ARG.
+ *   - Pointers to observation and output arrays may be host or device memory
+ *     of the plan's device; the library asks the CUDA runtime which.  Host
+ *     arrays are staged through the plan's workspace.  Every call returns
+ *     only after its results are in the caller's arrays (it synchronises the
+ *     plan's stream), so a returned status covers the whole computation.
+ *   - Ownership: the caller owns every array it passes; the plan owns its
+ *     device workspace, its cuFFT plan and its stream (unless the caller
+ *     supplied one).  Nothing is retained after a call returns.
+ *   - Errors: a non-FTP_OK status means the outputs were not written.  No
+ *     C++ exception crosses the ABI.  Per-frequency conditions are not errors:
+ *     they set bits in the optional flags array (FTP_FLAG_*).
+ *   - A plan is not thread-safe: use one plan per host thread / stream.
+ */
+#ifndef FTP_GB300_H
+#define FTP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ftp_plan_s* ftp_plan_t;
+
+typedef enum {
+  FTP_OK = 0,
+  FTP_ERR_INVALID_ARG = 1,      /* bad size, null pointer, H out of range, k0 < 1 ... */
+  FTP_ERR_ZERO_VARIANCE = 2,    /* all y equal: P undefined (Section 2) */
+  FTP_ERR_MIXED_ZERO_SIGMA = 3, /* some sigma = 0 and some > 0 (Section 2) */
+  FTP_ERR_NONFINITE = 4,        /* NaN/Inf in t, y or sigma, or sigma < 0 */
+  FTP_ERR_OOM = 5,              /* device allocation failed */
+  FTP_ERR_CUDA = 6,             /* CUDA runtime or cuFFT failure */
+  FTP_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up */
+  FTP_ERR_UNSUPPORTED = 8       /* request exceeds what the plan was built for */
+} ftp_status;
+
+typedef enum {
+  FTP_FP64 = 0,  /* FP64 everywhere: sums, assembly, roots, candidates */
+  FTP_MIXED = 1  /* FP32 sums (FP64 phase reduction), FP64 assembly,
+                    FP32 Aberth, FP64 Newton polish of the chosen root */
+} ftp_precision;
+
+/* Per-frequency flag bits (uint8). */
+#define FTP_FLAG_NONCONVERGED 1u  /* root solver hit its iteration cap */
+#define FTP_FLAG_DEGENERATE_MM 2u /* MM ~ 0 at the chosen phase: P set to 0 */
+#define FTP_FLAG_CONSTANT_P 4u    /* final polynomial ~ 0: P independent of theta2 */
+#define FTP_FLAG_NEGATIVE_AMP 8u  /* best theta1 < 0 (Section 2.1: allowed, reported) */
+
+#define FTP_MAX_H 16
+
+/* Trial-frequency grid f_k = (k0 + k) * df, k = 0..nf-1, k0 >= 1. */
+typedef struct {
+  double df;
+  int64_t k0;
+  int64_t nf;
+} ftp_grid;
+
+/* Template: c[n-1], s[n-1] are the cos / sin coefficients of harmonic n,
+ * n = 1..H, host memory, 1 <= H <= FTP_MAX_H.  No constant term: a constant
+ * is absorbed by theta3 (Section 2). */
+typedef struct {
+  int H;
+  const double* c;
+  const double* s;
+} ftp_template;
+
+/*
+ * ftp_plan - create a plan for lightcurves of at most max_nobs observations,
+ * templates of at most max_H harmonics, a fixed frequency grid and at most
+ * max_templates templates per call.  Allocates all device workspace (the
+ * NFFT grid, the sum tiles, staging for host arrays) and the cuFFT plan on
+ * `device`.  cuda_stream is a cudaStream_t of that device, or NULL to let
+ * the plan create its own.  On success *out receives the plan.
+ */
+ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
+                    int max_templates, ftp_precision prec, int device, void* cuda_stream);
+
+/*
+ * ftp_sums - step (a) only: the trig sums of Eqs. CCdef-YSdef in complex form,
+ *   Z_h(f_k) = sum_i w_i exp(i h omega_k t_i),            h = 1..2*H_sums
+ *   Y_h(f_k) = sum_i w_i (y_i - ybar) exp(i h omega_k t_i), h = 1..H_sums
+ * (so C_h = Re Z_h, S_h = Im Z_h, YC_h = Re Y_h, YS_h = Im Y_h; CC, CS, SS
+ * follow by product-to-sum identities).  sums_out (host or device) receives
+ * complex values of the plan's sum type - float2 (8 bytes) for FTP_MIXED,
+ * double2 (16 bytes) for FTP_FP64 - laid out row-major as [3*H_sums][nf]:
+ * rows 0..2H_sums-1 hold Z_1..Z_2H_sums, rows 2H_sums..3H_sums-1 hold
+ * Y_1..Y_H_sums.  moments_out (host or device, nullable) receives
+ * {ybar, YY} as two doubles.  1 <= H_sums <= max_H.
+ */
+ftp_status ftp_sums(ftp_plan_t plan, const double* t, const double* y, const double* dy,
+                    int64_t nobs, int H_sums, void* sums_out, double* moments_out);
+
+/*
+ * ftp_periodogram - the full path (a)-(c) for one lightcurve and ntemplates
+ * templates sharing its sums.  Outputs are [ntemplates][nf] arrays of double
+ * (host or device): power P, theta1 (amplitude), theta2 (phase, radians,
+ * [0, 2 pi)), theta3 (offset); flags (uint8, same shape) is nullable.
+ */
+ftp_status ftp_periodogram(ftp_plan_t plan, const double* t, const double* y, const double* dy,
+                           int64_t nobs, const ftp_template* tpl, int ntemplates,
+                           double* power, double* theta1, double* theta2, double* theta3,
+                           uint8_t* flags);
+
+/*
+ * ftp_batch - many lightcurves in one call.  Curve c owns observations
+ * [obs_off[c], obs_off[c+1]) of t, y, dy and the frequency grid grids[c]
+ * (each with nf <= the plan's grid.nf and a grid-size no larger than the
+ * plan's); its results start at element out_off[c] of power/theta1/theta2/
+ * theta3/flags and hold, per template it is run with, grids[c].nf values
+ * (template-major).  tpl_of_curve[c] selects one template of `bank` for curve
+ * c; NULL runs every template of the bank on every curve.  obs_off, grids,
+ * out_off, tpl_of_curve and bank are host arrays; t, y, dy and the outputs
+ * may be host or device.  Curves are processed in order through the plan's
+ * workspace; a failing curve stops the batch and its status is returned.
+ */
+ftp_status ftp_batch(ftp_plan_t plan, int64_t ncurves, const int64_t* obs_off, const double* t,
+                     const double* y, const double* dy, const ftp_grid* grids,
+                     const int64_t* out_off, const ftp_template* bank, int nbank,
+                     const int32_t* tpl_of_curve, double* power, double* theta1,
+                     double* theta2, double* theta3, uint8_t* flags);
+
+/* Release the plan's device memory, cuFFT plan and owned stream.  NULL is a no-op. */
+void ftp_destroy(ftp_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* ftp_status_string(ftp_status status);
+
+/*
+ * ftp_plan_info - introspection for tests and benchmarks: fills (each
+ * pointer nullable) the NFFT grid length n, the Kaiser-Bessel half-width m,
+ * the number of spreading tiles, and the number of kernel launches the last
+ * ftp_periodogram / ftp_sums call issued (cuFFT's own kernels excluded).
+ */
+ftp_status ftp_plan_info(ftp_plan_t plan, int64_t* grid_len, int* half_width, int64_t* ntiles,
+                         int* last_launches);
+
+/*
+ * ftp_stage_times - per-stage device times (milliseconds) of the last call
+ * when timing was enabled with ftp_set_timing(plan, 1): [0] preparation and
+ * binning, [1] spreading, [2] FFT, [3] deconvolution + gather,
+ * [4] assembly + roots + candidates.  Timing adds events to the stream.
+ */
+ftp_status ftp_set_timing(ftp_plan_t plan, int enable);
+ftp_status ftp_stage_times(ftp_plan_t plan, float* ms5);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTP_GB300_H */

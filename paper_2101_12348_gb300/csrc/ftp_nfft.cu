@@ -1,0 +1,441 @@
+// Step (a) of the Fast Template Periodogram: the weighted trigonometric sums
+// (Section 2, Eqs. CCdef-YSdef) by an adjoint non-equispaced FFT.
+//
+// All sums the method needs are values of two adjoint transforms on the
+// integer lattice of frequencies j * df:
+//   Gw[j] = sum_i w_i exp(2 pi i j df t_i),  Gy[j] = sum_i w_i (y_i - ybar) exp(...)
+// because h * f_k = h (k0 + k) df.  Z_h(f_k) = Gw[h (k0+k)] (h <= 2H) and
+// Y_h(f_k) = Gy[h (k0+k)] (h <= H).  The two real inputs are packed into one
+// complex coefficient c_i = w_i + i w_i (y_i - ybar), spread with a
+// Kaiser-Bessel window onto n = TILE * ntiles cells covering one period of
+// u = frac(df t), transformed with one complex FFT, and separated again with
+// the Hermitian symmetry of real-input transforms in the gather kernel, which
+// also divides by the window's Fourier transform.
+//
+// Kernels: moments (FP64 reductions, validation), points (FP64 phase
+// reduction into cell + fraction, tile histogram), scan + scatter (counting
+// sort of observations by spreading tile), spread (one CTA per tile, shared
+// memory accumulation, TMA bulk store of the finished tile: every grid cell is
+// written exactly once, no global atomics), gather (deconvolution + harmonic
+// gather into the [3H][nf_pad] sum tiles).
+#include <math.h>
+
+#include "ftp_internal.cuh"
+
+namespace ftp {
+
+namespace {
+
+constexpr int kRedThreads = 1024;
+
+struct OpSum {
+  template <typename T> __device__ T operator()(T a, T b) const { return a + b; }
+};
+struct OpMin {
+  __device__ double operator()(double a, double b) const { return fmin(a, b); }
+};
+struct OpMax {
+  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+};
+
+// Block-wide reduction; every thread receives the result.
+template <typename T, typename Op>
+__device__ T block_reduce(T v, T* sh, Op op) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T r = sh[0];
+    for (int w = 1; w < nw; ++w) r = op(r, sh[w]);
+    sh[0] = r;
+  }
+  __syncthreads();
+  const T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Weighted mean and variance in FP64 with the paper's weight rules
+// (Section 2): w_i ~ sigma_i^-2, all sigma = 0 -> unit weights, mixed zero /
+// non-zero sigma and Var(y) = 0 are errors.  One CTA.
+__global__ void __launch_bounds__(kRedThreads) moments_kernel(const double* __restrict__ t,
+                                                               const double* __restrict__ y,
+                                                               const double* __restrict__ dy,
+                                                               int64_t n, double* moments,
+                                                               int* status) {
+  __shared__ double shd[32];
+  __shared__ long long shl[32];
+  double s0 = 0, s1 = 0, sy = 0, ymin = INFINITY, ymax = -INFINITY;
+  long long nzero = 0, nbad = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double ti = t[i], yi = y[i], si = dy[i];
+    if (!isfinite(ti) || !isfinite(yi) || !isfinite(si) || si < 0.0) {
+      ++nbad;
+      continue;
+    }
+    sy += yi;
+    ymin = fmin(ymin, yi);
+    ymax = fmax(ymax, yi);
+    if (si == 0.0) {
+      ++nzero;
+    } else {
+      const double w = 1.0 / (si * si);
+      s0 += w;
+      s1 += w * yi;
+    }
+  }
+  s0 = block_reduce(s0, shd, OpSum());
+  s1 = block_reduce(s1, shd, OpSum());
+  sy = block_reduce(sy, shd, OpSum());
+  nzero = block_reduce(nzero, shl, OpSum());
+  nbad = block_reduce(nbad, shl, OpSum());
+  const double smin = block_reduce(ymin, shd, OpMin());
+  const double smax = block_reduce(ymax, shd, OpMax());
+
+  int code = DEV_OK;
+  double wsum = 0, ybar = 0;
+  bool unit = false;
+  if (nbad > 0) {
+    code = DEV_NONFINITE;
+  } else if (nzero == n) {
+    unit = true;
+    wsum = (double)n;
+    ybar = sy / (double)n;
+  } else if (nzero > 0) {
+    code = DEV_MIXED_ZERO_SIGMA;
+  } else {
+    wsum = s0;
+    ybar = s1 / s0;
+  }
+  if (code == DEV_OK && !(smax > smin)) code = DEV_ZERO_VARIANCE;
+
+  double yy = 0;
+  if (code == DEV_OK) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const double si = dy[i];
+      const double w = unit ? 1.0 : 1.0 / (si * si);
+      const double r = y[i] - ybar;
+      yy += w * r * r;
+    }
+  }
+  yy = block_reduce(yy, shd, OpSum());
+  if (threadIdx.x == 0) {
+    moments[MO_YBAR] = ybar;
+    moments[MO_YY] = (code == DEV_OK) ? yy / wsum : 0.0;
+    moments[MO_WSUM] = wsum;
+    moments[MO_UNIT] = unit ? 1.0 : 0.0;
+    if (code != DEV_OK) atomicCAS(&status[ST_CODE], DEV_OK, code);
+  }
+}
+
+// Per observation: normalised weight, packed coefficient, FP64 reduction of
+// u = frac(df t) and of its grid position x = n u into an integer cell and a
+// fraction (only the fraction is handed to the working precision), and the
+// spreading-tile histogram.
+template <typename R>
+__global__ void points_kernel(const double* __restrict__ t, const double* __restrict__ y,
+                              const double* __restrict__ dy, int64_t n,
+                              const double* __restrict__ moments, const int* __restrict__ status,
+                              double df, int64_t ngrid, int* __restrict__ tile_count,
+                              int* __restrict__ cell, R* __restrict__ frac,
+                              typename C2<R>::type* __restrict__ coef) {
+  if (status[ST_CODE] != DEV_OK) return;
+  const double ybar = moments[MO_YBAR], wsum = moments[MO_WSUM];
+  const bool unit = moments[MO_UNIT] != 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = dy[i];
+    const double w = (unit ? 1.0 : 1.0 / (si * si)) / wsum;
+    double u = df * t[i];
+    u -= floor(u);
+    const double x = u * (double)ngrid;
+    const double fl = floor(x);
+    int64_t c = (int64_t)fl;
+    if (c >= ngrid) c -= ngrid;
+    if (c < 0) c = 0;
+    cell[i] = (int)c;
+    frac[i] = (R)(x - fl);
+    typename C2<R>::type cc;
+    cc.x = (R)w;
+    cc.y = (R)(w * (y[i] - ybar));
+    coef[i] = cc;
+    atomicAdd(&tile_count[c >> kSpreadTileShift], 1);
+  }
+}
+
+// Exclusive scan of the tile histogram (one CTA); also clears the cursors.
+__global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ count, int64_t ntiles,
+                                                     int* __restrict__ off, int* __restrict__ cursor,
+                                                     const int* __restrict__ status) {
+  __shared__ int sh[32];
+  __shared__ int carry;
+  if (status[ST_CODE] != DEV_OK) return;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int v = (i < ntiles) ? count[i] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int nb = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += nb;
+    }
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int ws = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int nb = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += nb;
+      }
+      sh[lane] = ws;
+    }
+    __syncthreads();
+    const int before = carry + (warp > 0 ? sh[warp - 1] : 0) + incl - v;
+    if (i < ntiles) {
+      off[i] = before;
+      cursor[i] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) off[ntiles] = carry;
+}
+
+template <typename R>
+__global__ void scatter_kernel(int64_t n, const int* __restrict__ off, int* __restrict__ cursor,
+                               const int* __restrict__ cell, const R* __restrict__ frac,
+                               const typename C2<R>::type* __restrict__ coef,
+                               int* __restrict__ cell_s, R* __restrict__ frac_s,
+                               typename C2<R>::type* __restrict__ coef_s,
+                               const int* __restrict__ status) {
+  if (status[ST_CODE] != DEV_OK) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cell[i];
+    const int tile = c >> kSpreadTileShift;
+    const int pos = off[tile] + atomicAdd(&cursor[tile], 1);
+    cell_s[pos] = c;
+    frac_s[pos] = frac[i];
+    coef_s[pos] = coef[i];
+  }
+}
+
+// Modified Bessel function I0 from its power series sum_k (x^2/4)^k / (k!)^2,
+// truncated where the terms fall below the working precision for the window
+// shape parameters used here (beta <= 2 pi m with m <= 8).
+template <typename R> struct I0Terms;
+template <> struct I0Terms<float> { static constexpr int K = 34; };
+template <> struct I0Terms<double> { static constexpr int K = 64; };
+
+template <typename R>
+__device__ __forceinline__ R bessel_i0(R x) {
+  const R q = x * x * R(0.25);
+  R term = R(1), sum = R(1);
+#pragma unroll
+  for (int k = 1; k <= I0Terms<R>::K; ++k) {
+    term *= q * (R(1) / R(k * k));
+    sum += term;
+  }
+  return sum;
+}
+
+// Kaiser-Bessel window phi(x) = I0(beta sqrt(1 - (x/m)^2)) on |x| <= m.
+template <typename R>
+__device__ __forceinline__ R kb_window(R x, R inv_m, R beta) {
+  const R r = x * inv_m;
+  const R a = R(1) - r * r;
+  if (a < R(0)) return R(0);
+  return bessel_i0(beta * sqrt(a));
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+template <typename R>
+__device__ __forceinline__ void smem_atomic_add2(typename C2<R>::type* p, R a, R b) {
+  atomicAdd(&p->x, a);
+  atomicAdd(&p->y, b);
+}
+
+// One CTA per tile of kSpreadTile cells.  The CTA accumulates every window
+// contribution that lands in its tile into shared memory - from the points
+// binned to its own tile and to its two neighbours, whose windows reach
+// across the boundary - and then writes the whole tile, zeros included, with
+// one TMA bulk store.
+template <typename R>
+__global__ void __launch_bounds__(256) spread_kernel(const int* __restrict__ off,
+                                                     const int* __restrict__ cell_s,
+                                                     const R* __restrict__ frac_s,
+                                                     const typename C2<R>::type* __restrict__ coef_s,
+                                                     int64_t ngrid, int64_t ntiles, int m, R beta,
+                                                     typename C2<R>::type* __restrict__ grid,
+                                                     const int* __restrict__ status) {
+  using Cx = typename C2<R>::type;
+  __shared__ __align__(128) Cx tile[kSpreadTile];
+  const int64_t b = blockIdx.x;
+  for (int i = threadIdx.x; i < kSpreadTile; i += blockDim.x) {
+    Cx z;
+    z.x = R(0);
+    z.y = R(0);
+    tile[i] = z;
+  }
+  __syncthreads();
+  if (status[ST_CODE] == DEV_OK) {
+    int64_t nb[3];
+    int nnb;
+    if (ntiles == 1) {
+      nb[0] = 0;
+      nnb = 1;
+    } else if (ntiles == 2) {
+      nb[0] = 0;
+      nb[1] = 1;
+      nnb = 2;
+    } else {
+      nb[0] = (b == 0) ? ntiles - 1 : b - 1;
+      nb[1] = b;
+      nb[2] = (b + 1 == ntiles) ? 0 : b + 1;
+      nnb = 3;
+    }
+    const int w2 = 2 * m;
+    const R inv_m = R(1) / R(m);
+    for (int q = 0; q < nnb; ++q) {
+      const int start = off[nb[q]];
+      const int cnt = off[nb[q] + 1] - start;
+      const int total = cnt * w2;
+      for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int p = start + e / w2;
+        const int d = e % w2 - (m - 1);
+        int64_t ca = (int64_t)cell_s[p] + d;
+        if (ca < 0) ca += ngrid;
+        if (ca >= ngrid) ca -= ngrid;
+        if ((ca >> kSpreadTileShift) != b) continue;
+        const R phi = kb_window<R>((R)d - frac_s[p], inv_m, beta);
+        const Cx c = coef_s[p];
+        smem_atomic_add2<R>(&tile[ca & (kSpreadTile - 1)], c.x * phi, c.y * phi);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Make the generic-proxy shared-memory writes visible to the bulk copy.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    Cx* dst = grid + b * kSpreadTile;
+    asm volatile(
+        "cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+        "cp.async.bulk.commit_group;\n\t"
+        "cp.async.bulk.wait_group.read 0;" ::"l"(dst),
+        "r"(smem_addr(tile)), "r"((unsigned)(kSpreadTile * sizeof(Cx)))
+        : "memory");
+  }
+}
+
+// Deconvolution and harmonic gather: for frequency index k (K = k0 + k) and
+// harmonic h, j = h K; the packed transform X gives
+//   Gw[j] = (X[j] + conj X[n-j]) / 2,  Gy[j] = (X[j] - conj X[n-j]) / (2 i),
+// each divided by the Kaiser-Bessel transform
+//   phihat(nu) = 2 m sinh(sqrt(beta^2 - (2 pi m nu)^2)) / sqrt(...), nu = j/n.
+template <typename R>
+__global__ void gather_kernel(const typename C2<R>::type* __restrict__ X, int64_t ngrid,
+                              int64_t k0, int64_t nf, int64_t nf_pad, int Hs, int m, double beta,
+                              typename C2<R>::type* __restrict__ sums,
+                              const int* __restrict__ status) {
+  using Cx = typename C2<R>::type;
+  if (status[ST_CODE] != DEV_OK) return;
+  const int h = blockIdx.y + 1;
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nf) return;
+  const int64_t j = (int64_t)h * (k0 + k);
+  const Cx xp = X[j];
+  const Cx xm = X[ngrid - j];
+  const double nu = (double)j / (double)ngrid;
+  const R a = (R)(2.0 * M_PI * (double)m * nu);
+  const R bt = (R)beta;
+  const R z = sqrt(bt * bt - a * a);
+  const R inv = z / (R(2 * m) * sinh(z));
+  Cx gw, gy;
+  gw.x = R(0.5) * (xp.x + xm.x) * inv;
+  gw.y = R(0.5) * (xp.y - xm.y) * inv;
+  gy.x = R(0.5) * (xp.y + xm.y) * inv;
+  gy.y = -R(0.5) * (xp.x - xm.x) * inv;
+  sums[(int64_t)(h - 1) * nf_pad + k] = gw;
+  if (h <= Hs) sums[(int64_t)(2 * Hs + h - 1) * nf_pad + k] = gy;
+}
+
+inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)b;
+}
+
+}  // namespace
+
+void launch_moments(const double* t, const double* y, const double* dy, int64_t n,
+                    double* moments, int* status, cudaStream_t s) {
+  moments_kernel<<<1, kRedThreads, 0, s>>>(t, y, dy, n, moments, status);
+}
+
+template <typename R>
+void launch_points(const double* t, const double* y, const double* dy, int64_t n,
+                   const double* moments, const int* status, double df, int64_t ngrid,
+                   int* tile_count, int* cell, R* frac, typename C2<R>::type* coef,
+                   cudaStream_t s) {
+  points_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(t, y, dy, n, moments, status, df, ngrid,
+                                                     tile_count, cell, frac, coef);
+}
+
+void launch_scan(const int* tile_count, int64_t ntiles, int* tile_off, int* cursor,
+                 const int* status, cudaStream_t s) {
+  scan_kernel<<<1, 1024, 0, s>>>(tile_count, ntiles, tile_off, cursor, status);
+}
+
+template <typename R>
+void launch_scatter(int64_t n, const int* tile_off, int* cursor, const int* cell, const R* frac,
+                    const typename C2<R>::type* coef, int* cell_s, R* frac_s,
+                    typename C2<R>::type* coef_s, const int* status, cudaStream_t s) {
+  scatter_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(n, tile_off, cursor, cell, frac, coef,
+                                                      cell_s, frac_s, coef_s, status);
+}
+
+template <typename R>
+void launch_spread(const int* tile_off, const int* cell_s, const R* frac_s,
+                   const typename C2<R>::type* coef_s, int64_t ngrid, int64_t ntiles, int m,
+                   double beta, typename C2<R>::type* grid, const int* status, cudaStream_t s) {
+  spread_kernel<R><<<(unsigned)ntiles, 256, 0, s>>>(tile_off, cell_s, frac_s, coef_s, ngrid,
+                                                     ntiles, m, (R)beta, grid, status);
+}
+
+template <typename R>
+void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int64_t nf,
+                   int64_t nf_pad, int Hs, int m, double beta, typename C2<R>::type* sums,
+                   const int* status, cudaStream_t s) {
+  dim3 g((unsigned)((nf + 255) / 256), (unsigned)(2 * Hs));
+  gather_kernel<R><<<g, 256, 0, s>>>(X, ngrid, k0, nf, nf_pad, Hs, m, beta, sums, status);
+}
+
+#define FTP_INST(R)                                                                            \
+  template void launch_points<R>(const double*, const double*, const double*, int64_t,         \
+                                 const double*, const int*, double, int64_t, int*, int*, R*,   \
+                                 C2<R>::type*, cudaStream_t);                                  \
+  template void launch_scatter<R>(int64_t, const int*, int*, const int*, const R*,             \
+                                  const C2<R>::type*, int*, R*, C2<R>::type*, const int*,      \
+                                  cudaStream_t);                                               \
+  template void launch_spread<R>(const int*, const int*, const R*, const C2<R>::type*,         \
+                                 int64_t, int64_t, int, double, C2<R>::type*, const int*,      \
+                                 cudaStream_t);                                                \
+  template void launch_gather<R>(const C2<R>::type*, int64_t, int64_t, int64_t, int64_t, int,  \
+                                 int, double, C2<R>::type*, const int*, cudaStream_t);
+FTP_INST(float)
+FTP_INST(double)
+#undef FTP_INST
+
+}  // namespace ftp

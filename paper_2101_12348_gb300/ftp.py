@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the C ABI in include/ftp.h.
+
+Argument marshalling only: every step of the periodogram runs in the CUDA
+library.  Functions keep the C names (ftp_plan, ftp_sums, ftp_periodogram,
+ftp_batch, ftp_destroy, ftp_status_string, ftp_plan_info, ftp_set_timing,
+ftp_stage_times).  Arrays may be NumPy arrays (host memory) or torch tensors
+(host or CUDA); pointers are passed through unchanged and the library decides
+whether they are host or device memory.  If the shared library is missing the
+import of this module succeeds but every call raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libftp_gb300.so")
+
+FTP_OK = 0
+FTP_FP64 = 0
+FTP_MIXED = 1
+FTP_MAX_H = 16
+FLAG_NONCONVERGED = 1
+FLAG_DEGENERATE_MM = 2
+FLAG_CONSTANT_P = 4
+FLAG_NEGATIVE_AMP = 8
+
+STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE",
+                3: "FTP_ERR_MIXED_ZERO_SIGMA", 4: "FTP_ERR_NONFINITE", 5: "FTP_ERR_OOM",
+                6: "FTP_ERR_CUDA", 7: "FTP_ERR_TIMEOUT", 8: "FTP_ERR_UNSUPPORTED"}
+
+# every symbol include/ftp.h declares
+EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy",
+           "ftp_status_string", "ftp_plan_info", "ftp_set_timing", "ftp_stage_times")
+
+
+class FtpGrid(C.Structure):
+    _fields_ = [("df", C.c_double), ("k0", C.c_int64), ("nf", C.c_int64)]
+
+
+class FtpTemplate(C.Structure):
+    _fields_ = [("H", C.c_int), ("c", C.POINTER(C.c_double)), ("s", C.POINTER(C.c_double))]
+
+
+class FtpError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{STATUS_NAMES.get(self.status, self.status)}: {what}")
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load (once) and return the CUDA library; raises if it is not built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise FileNotFoundError(f"{p} is not built: run __graft_entry__.build() "
+                                "(the periodogram has no CPU fallback)")
+    lib = C.CDLL(p)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    lib.ftp_plan.argtypes = [C.POINTER(vp), i64, i32, FtpGrid, i32, i32, i32, vp]
+    lib.ftp_sums.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp]
+    lib.ftp_periodogram.argtypes = [vp, vp, vp, vp, i64, C.POINTER(FtpTemplate), i32,
+                                    vp, vp, vp, vp, vp]
+    lib.ftp_batch.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(FtpGrid), vp,
+                              C.POINTER(FtpTemplate), i32, vp, vp, vp, vp, vp, vp]
+    lib.ftp_destroy.argtypes = [vp]
+    lib.ftp_destroy.restype = None
+    lib.ftp_status_string.argtypes = [i32]
+    lib.ftp_status_string.restype = C.c_char_p
+    lib.ftp_plan_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64),
+                                  C.POINTER(i32)]
+    lib.ftp_set_timing.argtypes = [vp, i32]
+    lib.ftp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
+    for name in EXPORTS:
+        if name not in ("ftp_destroy", "ftp_status_string"):
+            getattr(lib, name).restype = i32
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a) -> int | None:
+    """Raw address of a NumPy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(st: int, what: str):
+    if st != FTP_OK:
+        raise FtpError(st, what)
+
+
+def ftp_status_string(status: int) -> str:
+    return load().ftp_status_string(int(status)).decode()
+
+
+def ftp_plan(max_nobs: int, max_H: int, grid, max_templates: int = 1, precision: str = "mixed",
+             device: int = 0, stream: int | None = None) -> int:
+    """Create a plan; grid = (df, k0, nf).  Returns the opaque plan handle."""
+    lib = load()
+    prec = {"mixed": FTP_MIXED, "fp64": FTP_FP64}[precision]
+    h = C.c_void_p()
+    g = FtpGrid(float(grid[0]), int(grid[1]), int(grid[2]))
+    _check(lib.ftp_plan(C.byref(h), int(max_nobs), int(max_H), g, int(max_templates), prec,
+                        int(device), stream), "ftp_plan")
+    return h.value
+
+
+def ftp_destroy(plan: int) -> None:
+    load().ftp_destroy(plan)
+
+
+def _templates(tpls):
+    keep = []
+    arr = (FtpTemplate * len(tpls))()
+    for i, (c, s) in enumerate(tpls):
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        if c.shape != s.shape or c.ndim != 1:
+            raise ValueError("template c and s must be 1-D arrays of equal length")
+        keep += [c, s]
+        arr[i].H = c.shape[0]
+        arr[i].c = c.ctypes.data_as(C.POINTER(C.c_double))
+        arr[i].s = s.ctypes.data_as(C.POINTER(C.c_double))
+    return arr, keep
+
+
+def ftp_sums(plan: int, t, y, dy, nobs: int, H_sums: int, sums_out, moments_out=None) -> None:
+    _check(load().ftp_sums(plan, _ptr(t), _ptr(y), _ptr(dy), int(nobs), int(H_sums),
+                           _ptr(sums_out), _ptr(moments_out)), "ftp_sums")
+
+
+def ftp_periodogram(plan: int, t, y, dy, nobs: int, templates, power, theta1, theta2, theta3,
+                    flags=None) -> None:
+    """templates: sequence of (c, s) coefficient arrays."""
+    arr, keep = _templates(templates)
+    _check(load().ftp_periodogram(plan, _ptr(t), _ptr(y), _ptr(dy), int(nobs), arr, len(keep) // 2,
+                                  _ptr(power), _ptr(theta1), _ptr(theta2), _ptr(theta3),
+                                  _ptr(flags)), "ftp_periodogram")
+
+
+def ftp_batch(plan: int, obs_off, t, y, dy, grids, out_off, bank, tpl_of_curve, power, theta1,
+              theta2, theta3, flags=None) -> None:
+    """obs_off/out_off: int64 host arrays; grids: sequence of (df, k0, nf);
+    bank: sequence of (c, s); tpl_of_curve: int32 host array or None."""
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    out_off = np.ascontiguousarray(out_off, dtype=np.int64)
+    g = (FtpGrid * len(grids))()
+    for i, (df, k0, nf) in enumerate(grids):
+        g[i] = FtpGrid(float(df), int(k0), int(nf))
+    arr, keep = _templates(bank)
+    tpc = None if tpl_of_curve is None else np.ascontiguousarray(tpl_of_curve, dtype=np.int32)
+    _check(load().ftp_batch(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t), _ptr(y), _ptr(dy),
+                            g, _ptr(out_off), arr, len(keep) // 2, _ptr(tpc), _ptr(power),
+                            _ptr(theta1), _ptr(theta2), _ptr(theta3), _ptr(flags)), "ftp_batch")
+
+
+def ftp_plan_info(plan: int) -> dict:
+    n, nt = C.c_int64(), C.c_int64()
+    m, la = C.c_int(), C.c_int()
+    _check(load().ftp_plan_info(plan, C.byref(n), C.byref(m), C.byref(nt), C.byref(la)),
+           "ftp_plan_info")
+    return {"grid_len": n.value, "half_width": m.value, "ntiles": nt.value,
+            "last_launches": la.value}
+
+
+def ftp_set_timing(plan: int, enable: bool) -> None:
+    _check(load().ftp_set_timing(plan, 1 if enable else 0), "ftp_set_timing")
+
+
+def ftp_stage_times(plan: int) -> list:
+    a = (C.c_float * 5)()
+    _check(load().ftp_stage_times(plan, a), "ftp_stage_times")
+    return list(a)
+
+
+class Plan:
+    """Convenience owner of a plan handle (closes it on exit)."""
+
+    def __init__(self, max_nobs, max_H, grid, max_templates=1, precision="mixed", device=0,
+                 stream=None):
+        self.grid = (float(grid[0]), int(grid[1]), int(grid[2]))
+        self.precision = precision
+        self.h = ftp_plan(max_nobs, max_H, self.grid, max_templates, precision, device, stream)
+
+    @property
+    def nf(self) -> int:
+        return self.grid[2]
+
+    def close(self):
+        if self.h:
+            ftp_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def periodogram(self, t, y, dy, templates, flags=True) -> dict:
+        """Host arrays in, host arrays out: dict(power, theta1, theta2, theta3, flags)."""
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        dy = np.ascontiguousarray(dy, dtype=np.float64)
+        nt = len(templates)
+        out = {k: np.empty((nt, self.nf)) for k in ("power", "theta1", "theta2", "theta3")}
+        out["flags"] = np.empty((nt, self.nf), dtype=np.uint8) if flags else None
+        ftp_periodogram(self.h, t, y, dy, t.shape[0], templates, out["power"], out["theta1"],
+                        out["theta2"], out["theta3"], out["flags"])
+        return out
+
+    def sums(self, t, y, dy, H):
+        """Host arrays in: returns (complex sums [3H][nf], (ybar, YY))."""
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        dy = np.ascontiguousarray(dy, dtype=np.float64)
+        dt = np.complex64 if self.precision == "mixed" else np.complex128
+        s = np.empty((3 * H, self.nf), dtype=dt)
+        mo = np.empty(2)
+        ftp_sums(self.h, t, y, dy, t.shape[0], H, s, mo)
+        return s, (float(mo[0]), float(mo[1]))
+
+    def info(self) -> dict:
+        return ftp_plan_info(self.h)

@@ -1,0 +1,67 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/ftp.h declares, and rejects
+bad arguments before touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_2101_12348_gb300 import ftp
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ftp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return ftp.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ftp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_binding_exports():
+    assert declared_functions() == sorted(ftp.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(ftp.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(raw, name), name
+
+
+def test_status_strings(lib):
+    for code in range(9):
+        s = ftp.ftp_status_string(code)
+        assert isinstance(s, str) and s
+    assert ftp.ftp_status_string(0) == "ok"
+    assert "unknown" in ftp.ftp_status_string(99)
+
+
+@pytest.mark.parametrize("args,expect", [
+    (dict(max_nobs=1, max_H=3, grid=(0.1, 1, 10)), 1),
+    (dict(max_nobs=10, max_H=0, grid=(0.1, 1, 10)), 1),
+    (dict(max_nobs=10, max_H=17, grid=(0.1, 1, 10)), 8),
+    (dict(max_nobs=10, max_H=3, grid=(0.0, 1, 10)), 1),
+    (dict(max_nobs=10, max_H=3, grid=(0.1, 0, 10)), 1),
+    (dict(max_nobs=10, max_H=3, grid=(float("nan"), 1, 10)), 1),
+    (dict(max_nobs=10, max_H=3, grid=(0.1, 1, 0)), 1),
+])
+def test_plan_argument_validation(lib, args, expect):
+    with pytest.raises(ftp.FtpError) as e:
+        ftp.ftp_plan(**args)
+    assert e.value.status == expect
+
+
+def test_null_plan_is_rejected(lib):
+    import numpy as np
+    t = np.arange(4.0)
+    with pytest.raises(ftp.FtpError) as e:
+        ftp.ftp_sums(None, t, t, t, 4, 1, np.zeros(4))
+    assert e.value.status == 1
+    ftp.ftp_destroy(None)  # no-op
