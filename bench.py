@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of the Fast Template Periodogram on one GB300 (or N, one per rank).
+
+Workload: the single long lightcurve - N_obs = 1e4 times over a 3000 d
+baseline with nightly gaps, an H = 6 template, N_f = 2.5e5 frequencies
+f_k = k / (5 * 3000 d) - synthetic and seeded (synth.long_curve).  A step is
+one ftp_periodogram call over the whole grid: NFFT sums, polynomial assembly,
+roots, candidates.  `value` is mixed-precision (frequency x template)
+evaluations per second with the inputs resident in HBM, L2 flushed between
+steps; the FP64 path is timed beside it and their largest |dP| over every
+frequency is reported.  `e2e` is the same metric through the C ABI with
+pinned host buffers (copies inside the timed region).  `cpu_baseline` times
+the FP64 CPU oracle on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("FTP freq·template evals/s on 1 GB300, mixed vs FP64 at |ΔP|≤1e-4; "
+          "%roofline")
+UNIT = "evals/s"
+WORKLOAD = ("single long lightcurve: N_obs=1e4 over 3000 d with nightly gaps (8 h windows, "
+            "30% nights dropped), H=6 template, N_f=2.5e5, df=1/(5*3000 d)")
+# Peaks of the plain ALUs (no tensor cores): 152 SMs x 128 FP32 lanes x 2 flop
+# at the 2070 MHz maximum SM clock; FP64 at the nominal 1.25 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sample", type=int, default=128,
+                    help="frequencies of the workload timed on the CPU oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ oracle on CPU
+def _oracle_worker(args):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import numpy as np
+
+    import oracle
+    t, y, dy, freqs, c, s = args
+    r = oracle.periodogram(t, y, dy, freqs, c, s)
+    return r["power"]
+
+
+def oracle_timing(lc, tpl, freqs, cores):
+    """Time the FP64 oracle over `freqs` with a spawn pool of `cores` single-
+    threaded workers; returns (seconds, powers)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    chunks = [c for c in np.array_split(freqs, max(1, cores * 2)) if c.size]
+    ctx = mp.get_context("spawn")
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        with ctx.Pool(cores) as pool:
+            pool.map(_oracle_worker, [(lc.t, lc.y, lc.dy, chunks[0][:1], tpl.c, tpl.s)] * cores)
+            t0 = time.perf_counter()
+            parts = pool.map(_oracle_worker, [(lc.t, lc.y, lc.dy, ch, tpl.c, tpl.s) for ch in chunks])
+            dt = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return dt, np.concatenate(parts)
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value: float, device) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, value: float, device) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ftp_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ncu_traffic_per_item():
+    """DRAM bytes per (frequency, template) item of the roots kernel, from the
+    committed ncu summary (None if absent)."""
+    p = os.path.join(ROOT, "profiles", "roots_kernel_long_curve.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.strip().startswith("dram_bytes_per_item:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_2101_12348_gb300 import ftp
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lc, tpl, grid = synth.long_curve()
+    nf, D = grid.nf, 6 * tpl.H - 2
+    stream = torch.cuda.Stream(device=dev)
+    tpls = [(tpl.c, tpl.s)]
+    dt_, dy_, ds_ = (torch.from_numpy(a).to(dev) for a in (lc.t, lc.y, lc.dy))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def outputs():
+        return ([torch.empty(nf, dtype=torch.float64, device=dev) for _ in range(4)],
+                torch.empty(nf, dtype=torch.uint8, device=dev))
+
+    def timed(plan, steps, warmup, outs, fl):
+        for _ in range(warmup):
+            ftp.ftp_periodogram(plan, dt_, dy_, ds_, lc.t.size, tpls, *outs, fl)
+        ftp.ftp_set_timing(plan, True)
+        step_ms, roots_ms, iters = [], [], []
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ftp.ftp_periodogram(plan, dt_, dy_, ds_, lc.t.size, tpls, *outs, fl)
+                e1.record(stream)
+                e1.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                st = ftp.ftp_stage_times(plan)
+                roots_ms.append(st[4])
+                iters.append(ftp.ftp_solver_stats(plan)["mean_iterations"])
+        ftp.ftp_set_timing(plan, False)
+        return step_ms, roots_ms, iters
+
+    sh = stream.cuda_stream
+    mixed = ftp.ftp_plan(lc.t.size, tpl.H, (grid.df, grid.k0, grid.nf), 1, "mixed", local, sh)
+    fp64 = ftp.ftp_plan(lc.t.size, tpl.H, (grid.df, grid.k0, grid.nf), 1, "fp64", local, sh)
+    out_m, fl_m = outputs()
+    out_d, fl_d = outputs()
+
+    # ---- mixed, device-resident inputs: the headline
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        step_ms, roots_ms, iters = timed(mixed, args.steps, args.warmup, out_m, fl_m)
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    clocks = clk.summary()
+    launches_per_call = ftp.ftp_plan_info(mixed)["last_launches"]
+    stats_m = ftp.ftp_solver_stats(mixed)
+    total_ms = sum(step_ms)
+    total_ms_max = max_over_ranks(pg, total_ms, dev)
+    evals_all = sum_over_ranks(pg, float(args.steps * nf), dev)
+    value = evals_all / (total_ms_max / 1e3)
+
+    # ---- FP64 path beside it, and the mixed-vs-FP64 error on every frequency
+    d_ms, d_roots, _ = timed(fp64, args.fp64_steps, 1, out_d, fl_d)
+    fp64_value = nf * len(d_ms) / (sum(d_ms) / 1e3)
+    dP = float(torch.max(torch.abs(out_m[0] - out_d[0])).item())
+
+    # ---- end to end through the C ABI with pinned host buffers
+    th = [torch.from_numpy(a).pin_memory() for a in (lc.t, lc.y, lc.dy)]
+    oh = [torch.empty(nf, dtype=torch.float64).pin_memory() for _ in range(4)]
+    fh = torch.empty(nf, dtype=torch.uint8).pin_memory()
+    ftp.ftp_periodogram(mixed, *th, lc.t.size, tpls, *oh, fh)
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ftp.ftp_periodogram(mixed, *th, lc.t.size, tpls, *oh, fh)
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0, dev)
+    e2e_value = evals_all / e2e_s
+    h2d = 3 * lc.t.size * 8 + 16 * 16 + 4
+    d2h = 4 * nf * 8 + nf + 8 * 4 * 2
+
+    # ---- roofline of the dominant kernel (assembly + Aberth + candidates)
+    roots_s = statistics.mean(roots_ms) / 1e3
+    ibar = statistics.mean(iters)
+    fp32_flops = nf * 26.0 * D * D * ibar          # Aberth: 26 D^2 flops per iteration
+    achieved = fp32_flops / roots_s / 1e12
+    tpi = ncu_traffic_per_item()
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": (round(tpi * nf) if tpi else None),
+                "kernel": "roots_kernel (FP32 Aberth flops 26*D^2*iterations)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_obs": int(lc.t.size), "H": tpl.H, "n_freq": nf,
+                   "templates": 1, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "fp64_path": {"value": round(fp64_value, 1), "unit": UNIT, "steps": len(d_ms),
+                      "ms_per_step": round(statistics.mean(d_ms), 3),
+                      "max_abs_dP_mixed_vs_fp64": dP},
+        "stage_ms": {"roots": round(statistics.mean(roots_ms), 4)},
+        "solver": {"mean_iterations": round(ibar, 3), "nonconverged": stats_m["nonconverged"],
+                   "resolved_in_fp64": stats_m["resolved"]},
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+        "gpu_launches": args.steps * launches_per_call,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        sel = np.linspace(0, nf - 1, args.cpu_sample).astype(np.int64)
+        sec, pw = oracle_timing(lc, tpl, grid.freqs()[sel], cores)
+        gp = out_m[0].cpu().numpy()[sel]
+        result["cpu_baseline"] = {
+            "value": round(sel.size / sec, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sel.size} evenly spaced frequencies of the workload "
+                      f"({sec:.1f} s wall on {cores} single-threaded processes)",
+            "max_abs_dP_mixed_vs_oracle": float(np.max(np.abs(gp - pw)))}
+    ftp.ftp_destroy(mixed)
+    ftp.ftp_destroy(fp64)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, world, rank, local, pg):
+    """The FP64 CPU oracle on the host cores, on the same workload and metric:
+    each step is a bounded sample of frequencies of the workload."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+    lc, tpl, grid = synth.long_curve()
+    cores = cpu_cores()
+    per_step = max(cores, 32)
+    rng = np.random.default_rng(7)
+    for _ in range(args.warmup):
+        oracle_timing(lc, tpl, grid.freqs()[rng.choice(grid.nf, cores, replace=False)], cores)
+    secs, n = 0.0, 0
+    for _ in range(args.steps):
+        f = grid.freqs()[np.sort(rng.choice(grid.nf, per_step, replace=False))]
+        s, _ = oracle_timing(lc, tpl, f, cores)
+        secs += s
+        n += f.size
+    value = n / secs
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_obs": int(lc.t.size), "H": tpl.H,
+                   "n_freq": grid.nf, "templates": 1},
+        "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{per_step} random frequencies of the workload per step"},
+        "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local, pg = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank, local, pg)
+        else:
+            run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -69,8 +69,10 @@ typedef enum {
 
 typedef enum {
   FTP_FP64 = 0,  /* FP64 everywhere: sums, assembly, roots, candidates */
-  FTP_MIXED = 1  /* FP32 sums (FP64 phase reduction), FP64 assembly,
-                    FP32 Aberth, FP64 Newton polish of the chosen root */
+  FTP_MIXED = 1  /* FP32 NFFT sums (FP64 phase reduction), FP64 assembly of
+                    MM' and YM', FP32 final polynomial, Aberth and screening,
+                    FP64 Newton polish and evaluation of the chosen phase;
+                    ill-conditioned frequencies re-solved from FP64 sums */
 } ftp_precision;
 
 /* Per-frequency flag bits (uint8). */
@@ -168,13 +170,28 @@ ftp_status ftp_plan_info(ftp_plan_t plan, int64_t* grid_len, int* half_width, in
                          int* last_launches);
 
 /*
- * ftp_stage_times - per-stage device times (milliseconds) of the last call
- * when timing was enabled with ftp_set_timing(plan, 1): [0] preparation and
- * binning, [1] spreading, [2] FFT, [3] deconvolution + gather,
- * [4] assembly + roots + candidates.  Timing adds events to the stream.
+ * ftp_solver_stats - root-solver statistics of the last call: the number of
+ * (frequency, template) items solved, the mean number of Aberth iterations
+ * per item (iterations of the warp that solved it), how many items hit the
+ * iteration cap (FTP_FLAG_NONCONVERGED), and how many frequencies were
+ * re-solved from direct FP64 sums because the a-posteriori estimate of the
+ * error of P caused by the NFFT sums exceeded 1e-5 (FTP_MIXED) or 1e-10
+ * (FTP_FP64) - frequencies where clustered phases make MM = Var(M) a small
+ * difference of O(1) sums.  Each pointer is nullable.
+ */
+ftp_status ftp_solver_stats(ftp_plan_t plan, int64_t* items, double* mean_iterations,
+                            int64_t* nonconverged, int64_t* resolved);
+
+/*
+ * ftp_stage_times - per-stage device times (milliseconds) of the last
+ * ftp_periodogram call when timing was enabled with ftp_set_timing(plan, 1),
+ * measured with CUDA events on the plan's stream: [0] moments, phase
+ * reduction and binning, [1] spreading, [2] FFT, [3] deconvolution + gather,
+ * [4] assembly + roots + candidates + polish (all template groups),
+ * [5] re-solve of ill-conditioned frequencies from direct FP64 sums.
  */
 ftp_status ftp_set_timing(ftp_plan_t plan, int enable);
-ftp_status ftp_stage_times(ftp_plan_t plan, float* ms5);
+ftp_status ftp_stage_times(ftp_plan_t plan, float* ms6);
 
 #ifdef __cplusplus
 }

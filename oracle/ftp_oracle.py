@@ -283,15 +283,22 @@ def periodogram(t, y, dy, freqs, c, s, rel_tie: float = 1e-12):
 
 
 def best_candidate_margin(t, y, dy, freq: float, c, s, theta2_best: float,
-                          sep: float = 0.05) -> float:
+                          sep: float = 0.05, rel_tie: float = 1e-9) -> float:
     """P(best) minus the best P among candidates more than `sep` rad away
     (mod 2 pi): used to decide whether the optimum is well separated, in which
-    case the best phase is unique and comparable across implementations."""
+    case the best phase is unique and comparable across implementations.
+
+    A far candidate that ties with the best (within rel_tie * P) but has the
+    opposite amplitude sign is resolved by the tie rule (theta1 > 0 first) and
+    does not count: e.g. templates with only odd harmonics, where theta2 and
+    theta2 + pi give the same P with opposite theta1."""
     pol = polynomials_at(t, y, dy, freq, c, s)
     th2 = candidate_phases(pol["F"])
-    P, _, _, _ = fit_at_phase(t, y, pol["w"], pol["ybar"], pol["YY"], freq, c, s, th2)
+    P, th1, _, _ = fit_at_phase(t, y, pol["w"], pol["ybar"], pol["YY"], freq, c, s, th2)
     d = np.abs(np.angle(np.exp(1j * (th2 - theta2_best))))
-    Pbest = fit_at_phase(t, y, pol["w"], pol["ybar"], pol["YY"], freq, c, s,
-                         np.array([theta2_best]))[0][0]
-    far = P[d > sep]
+    Pb, th1b, _, _ = fit_at_phase(t, y, pol["w"], pol["ybar"], pol["YY"], freq, c, s,
+                                  np.array([theta2_best]))
+    Pbest = Pb[0]
+    twin = (np.sign(th1) != np.sign(th1b[0])) & (np.abs(P - Pbest) <= rel_tie * max(Pbest, 1e-300))
+    far = P[(d > sep) & ~twin]
     return float(Pbest - (far.max() if far.size else 0.0))

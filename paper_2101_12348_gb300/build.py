@@ -17,7 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libftp_gb300.so")
-SOURCES = ["ftp_api.cu", "ftp_nfft.cu", "ftp_roots_mixed.cu", "ftp_roots_fp64.cu"]
+SOURCES = ["ftp_api.cu", "ftp_nfft.cu", "ftp_roots_mixed.cu", "ftp_roots_fp64.cu",
+           "ftp_roots_redo.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,8 +30,9 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
+    checks = ["-DFTP_DEVICE_CHECKS"] if os.environ.get("FTP_DEVICE_CHECKS") == "1" else []
     return ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-            "-I", os.path.join(ROOT, "include"), *ARCH, *extra]
+            "-I", os.path.join(ROOT, "include"), *ARCH, *checks, *extra]
 
 
 def _newer(dst: str, srcs) -> bool:
@@ -52,7 +54,8 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
-        if force or ptxas_info or not _newer(o, [s, *headers, __file__]):
+        if force or ptxas_info or os.environ.get("FTP_DEVICE_CHECKS") == "1" or \
+                not _newer(o, [s, *headers, __file__]):
             extra = ["-Xptxas", "-v"] if ptxas_info else []
             jobs.append([exe, *_flags(extra), "-c", s, "-o", o])
 

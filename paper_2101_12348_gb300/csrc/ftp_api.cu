@@ -2,6 +2,7 @@
 // staging, the step (a) pipeline and the per-H launches of steps (b)-(c).
 #include <cufft.h>
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -15,14 +16,15 @@
 namespace ftp {
 int launch_roots_mixed(const RootsArgs& a, int num_sms, cudaStream_t s);
 int launch_roots_fp64(const RootsArgs& a, int num_sms, cudaStream_t s);
-size_t roots_smem_mixed(int H);
-size_t roots_smem_fp64(int H);
+int launch_roots_redo(const RootsArgs& a, int num_sms, cudaStream_t s);
 
-int launch_roots(bool mixed, const RootsArgs& a, int num_sms, cudaStream_t s) {
-  return mixed ? launch_roots_mixed(a, num_sms, s) : launch_roots_fp64(a, num_sms, s);
-}
-size_t roots_smem_bytes(bool mixed, int H) {
-  return mixed ? roots_smem_mixed(H) : roots_smem_fp64(H);
+int launch_roots(RootsKind kind, const RootsArgs& a, int num_sms, cudaStream_t s) {
+  switch (kind) {
+    case ROOTS_MIXED: return launch_roots_mixed(a, num_sms, s);
+    case ROOTS_FP64: return launch_roots_fp64(a, num_sms, s);
+    case ROOTS_REDO: return launch_roots_redo(a, num_sms, s);
+  }
+  return -1;
 }
 }  // namespace ftp
 
@@ -60,6 +62,12 @@ struct ftp_plan_s {
   double* d_in = nullptr;       // staged t, y, dy
   double* d_moments = nullptr;
   int* d_status = nullptr;
+  unsigned long long* d_counters = nullptr;
+  unsigned long long* d_queue = nullptr;  // work-unit counter of the roots kernel
+  int* d_redo_list = nullptr;            // frequencies to re-solve from direct FP64 sums
+  int* d_redo_mark = nullptr;
+  int* d_redo_count = nullptr;
+  double2* d_redo_sums = nullptr;        // [3 max_H][nf_pad] direct FP64 sums
   int* d_tile_count = nullptr;
   int* d_tile_off = nullptr;
   int* d_cursor = nullptr;
@@ -81,13 +89,14 @@ struct ftp_plan_s {
   std::map<int64_t, FftEntry> ffts;
   // pinned host staging
   int* h_status = nullptr;
+  unsigned long long* h_counters = nullptr;
   double2* h_alpha = nullptr;
   int* h_rows = nullptr;
   // instrumentation
   int last_launches = 0;
   bool timing = false;
-  cudaEvent_t ev[6] = {};
-  float stage_ms[5] = {};
+  cudaEvent_t ev[7] = {};
+  float stage_ms[6] = {};
   int maxit = 60;
   int polish_steps = 1;
 };
@@ -275,14 +284,29 @@ ftp_status stage_obs(ftp_plan_t P, const double* t, const double* y, const doubl
   return FTP_OK;
 }
 
+cudaError_t reset_call(ftp_plan_t P) {
+  cudaError_t e = cudaMemsetAsync(P->d_status, 0, sizeof(int) * ST_WORDS, P->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(P->d_counters, 0, sizeof(unsigned long long) * CNT_WORDS, P->stream);
+  return e;
+}
+
 ftp_status finish(ftp_plan_t P) {
   FTP_CK(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int) * ST_WORDS,
                          cudaMemcpyDeviceToHost, P->stream));
+  FTP_CK(cudaMemcpyAsync(P->h_counters, P->d_counters, sizeof(unsigned long long) * CNT_WORDS,
+                         cudaMemcpyDeviceToHost, P->stream));
   FTP_CK(cudaStreamSynchronize(P->stream));
+#ifdef FTP_DEVICE_CHECKS
+  if (P->h_status[ST_DBG_N] != 0)
+    fprintf(stderr, "ftp device check failed: site %d value %d bound %d (%d failures)\n",
+            P->h_status[ST_DBG_SITE], P->h_status[ST_DBG_A], P->h_status[ST_DBG_B],
+            P->h_status[ST_DBG_N]);
+#endif
   if (P->timing) {
-    for (int i = 0; i < 5; ++i) P->stage_ms[i] = 0.f;
+    for (int i = 0; i < 6; ++i) P->stage_ms[i] = 0.f;
     float ms;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
       if (cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]) == cudaSuccess) P->stage_ms[i] = ms;
     cudaGetLastError();
   }
@@ -336,12 +360,17 @@ ftp_status upload_templates(ftp_plan_t P, const ftp_template* tpl, int ntpl,
   return FTP_OK;
 }
 
-ftp_status run_roots(ftp_plan_t P, int H, int Hs, int64_t nf, const double2* alpha,
-                     const int* rows, int ntpl, double* power, double* th1, double* th2,
-                     double* th3, uint8_t* flags, int64_t out_stride, int* launches) {
+ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int Hs, int64_t nf,
+                     const int* nf_dev, const int* kmap, bool collect_redo, const double2* alpha,
+                     const int* rows, int ntpl, double* const* o, uint8_t* flags,
+                     int64_t out_stride, int64_t out_elems, int* launches) {
   RootsArgs a{};
-  a.sums = P->d_sums;
+  a.sums = sums;
+  a.sums_elems = (int64_t)3 * P->max_H * P->nf_pad;
+  a.out_elems = out_elems;
   a.nf = nf;
+  a.nf_dev = nf_dev;
+  a.kmap = kmap;
   a.nf_pad = P->nf_pad;
   a.Hs = Hs;
   a.H = H;
@@ -349,20 +378,71 @@ ftp_status run_roots(ftp_plan_t P, int H, int Hs, int64_t nf, const double2* alp
   a.alpha = alpha;
   a.rows = rows;
   a.moments = P->d_moments;
-  a.power = power;
-  a.theta1 = th1;
-  a.theta2 = th2;
-  a.theta3 = th3;
+  a.power = o[0];
+  a.theta1 = o[1];
+  a.theta2 = o[2];
+  a.theta3 = o[3];
   a.flags = flags;
   a.out_stride = out_stride;
   a.status = P->d_status;
+  a.counters = P->d_counters;
+  a.queue = P->d_queue;
+  if (collect_redo) {
+    a.redo_list = P->d_redo_list;
+    a.redo_mark = P->d_redo_mark;
+    a.redo_count = P->d_redo_count;
+    a.redo_cap = (int)P->grid.nf;
+    a.sum_err = P->mixed ? kSumErrF32 : kSumErrF64;
+    a.redo_tol = P->mixed ? kRedoTolF32 : kRedoTolF64;
+  }
   a.maxit = P->maxit;
   a.polish_steps = P->polish_steps;
-  const int r = launch_roots(P->mixed, a, P->num_sms, P->stream);
+  FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), P->stream));
+  const int r = launch_roots(kind, a, P->num_sms, P->stream);
   if (r == -1) return FTP_ERR_UNSUPPORTED;
   if (r < 0) return FTP_ERR_CUDA;
   *launches += r;
   FTP_CK(cudaGetLastError());
+  return FTP_OK;
+}
+
+// Steps (b)-(c) for one curve whose sums are in the plan's tiles: one launch
+// per group of templates with equal H.  Frequencies whose estimated error of
+// P from the NFFT sums exceeds the path's threshold (ill-conditioned ones,
+// where clustered phases make MM a small difference of O(1) sums) are then
+// recomputed from direct FP64 sums with the same kernel (FP32 Aberth on the
+// mixed path, FP64 Aberth on the FP64 path).
+ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double* ddy,
+                 int64_t nobs, double df, int64_t k0, int64_t nf, int Hs,
+                 const std::vector<HGroup>& groups, const double2* alpha, const int* rows,
+                 const int* row0, double* const* o, uint8_t* flags, int64_t out_elems,
+                 int* launches) {
+  const bool redo = true;
+  if (redo) {
+    FTP_CK(cudaMemsetAsync(P->d_redo_mark, 0, sizeof(int) * nf, P->stream));
+    FTP_CK(cudaMemsetAsync(P->d_redo_count, 0, sizeof(int), P->stream));
+  }
+  const RootsKind kind = P->mixed ? ROOTS_MIXED : ROOTS_FP64;
+  for (const HGroup& g : groups) {
+    ftp_status st = run_roots(P, kind, P->d_sums, g.H, Hs, nf, nullptr, nullptr, redo,
+                              alpha + (size_t)g.first * kMaxH, row0 ? row0 : rows + g.first,
+                              g.count, o, flags, nf, out_elems, launches);
+    if (st != FTP_OK) return st;
+  }
+  ev_rec(P, 5);
+  if (!redo) return FTP_OK;
+  launch_direct_sums(dt, dyv, ddy, nobs, P->d_moments, P->d_status, df, k0, P->d_redo_list,
+                     P->d_redo_count, (int)nf, Hs, P->nf_pad, P->d_redo_sums,
+                     (int64_t)3 * P->max_H * P->nf_pad, P->d_status, P->stream);
+  *launches += 1;
+  for (const HGroup& g : groups) {
+    ftp_status st = run_roots(P, P->mixed ? ROOTS_REDO : ROOTS_FP64, P->d_redo_sums, g.H, Hs, nf,
+                              P->d_redo_count,
+                              P->d_redo_list, false, alpha + (size_t)g.first * kMaxH,
+                              row0 ? row0 : rows + g.first, g.count, o, flags, nf, out_elems,
+                              launches);
+    if (st != FTP_OK) return st;
+  }
   return FTP_OK;
 }
 
@@ -392,13 +472,15 @@ void ftp_destroy(ftp_plan_t P) {
   cudaSetDevice(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
   for (auto& kv : P->ffts) cufftDestroy(kv.second.h);
-  void* dptrs[] = {P->d_in, P->d_moments, P->d_status, P->d_tile_count, P->d_tile_off,
+  void* dptrs[] = {P->d_in, P->d_moments, P->d_status, P->d_counters, P->d_queue, P->d_redo_list,
+                   P->d_redo_mark, P->d_redo_count, P->d_redo_sums, P->d_tile_count, P->d_tile_off,
                    P->d_cursor, P->d_cell, P->d_cell_s, P->d_frac, P->d_frac_s, P->d_coef,
                    P->d_coef_s, P->d_grid, P->d_sums, P->d_alpha, P->d_rows, P->d_row0, P->d_out,
                    P->d_flags, P->d_fftwork};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (P->h_status) cudaFreeHost(P->h_status);
+  if (P->h_counters) cudaFreeHost(P->h_counters);
   if (P->h_alpha) cudaFreeHost(P->h_alpha);
   if (P->h_rows) cudaFreeHost(P->h_rows);
   for (auto& e : P->ev)
@@ -472,6 +554,12 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
   FTP_AL(P->d_in, 3 * nobs);
   FTP_AL(P->d_moments, MO_WORDS);
   FTP_AL(P->d_status, ST_WORDS);
+  FTP_AL(P->d_counters, CNT_WORDS);
+  FTP_AL(P->d_queue, 1);
+  FTP_AL(P->d_redo_list, (size_t)grid.nf);
+  FTP_AL(P->d_redo_mark, (size_t)grid.nf);
+  FTP_AL(P->d_redo_count, 1);
+  FTP_AL(P->d_redo_sums, (size_t)3 * max_H * P->nf_pad);
   FTP_AL(P->d_tile_count, (size_t)P->ntiles);
   FTP_AL(P->d_tile_off, (size_t)P->ntiles + 1);
   FTP_AL(P->d_cursor, (size_t)P->ntiles);
@@ -502,6 +590,7 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
       cudaMemset(P->d_row0, 0, sizeof(int)) != cudaSuccess)
     return fail(FTP_ERR_CUDA);
   if (cudaMallocHost(&P->h_status, sizeof(int) * ST_WORDS) != cudaSuccess ||
+      cudaMallocHost(&P->h_counters, sizeof(unsigned long long) * CNT_WORDS) != cudaSuccess ||
       cudaMallocHost(&P->h_alpha, sizeof(double2) * kMaxH * max_templates) != cudaSuccess ||
       cudaMallocHost(&P->h_rows, sizeof(int) * max_templates) != cudaSuccess)
     return fail(FTP_ERR_OOM);
@@ -525,15 +614,27 @@ ftp_status ftp_plan_info(ftp_plan_t P, int64_t* grid_len_out, int* half_width, i
   return FTP_OK;
 }
 
+ftp_status ftp_solver_stats(ftp_plan_t P, int64_t* items, double* mean_iterations,
+                            int64_t* nonconverged, int64_t* resolved) {
+  if (!P) return FTP_ERR_INVALID_ARG;
+  const unsigned long long* c = P->h_counters;
+  const unsigned long long n = c ? c[CNT_ITEMS] : 0;
+  if (items) *items = (int64_t)n;
+  if (mean_iterations) *mean_iterations = n ? (double)c[CNT_ITERS] / (double)n : 0.0;
+  if (nonconverged) *nonconverged = n ? (int64_t)c[CNT_NONCONV] : 0;
+  if (resolved) *resolved = n ? (int64_t)c[CNT_REDO] : 0;
+  return FTP_OK;
+}
+
 ftp_status ftp_set_timing(ftp_plan_t P, int enable) {
   if (!P) return FTP_ERR_INVALID_ARG;
   P->timing = enable != 0;
   return FTP_OK;
 }
 
-ftp_status ftp_stage_times(ftp_plan_t P, float* ms5) {
-  if (!P || !ms5) return FTP_ERR_INVALID_ARG;
-  for (int i = 0; i < 5; ++i) ms5[i] = P->stage_ms[i];
+ftp_status ftp_stage_times(ftp_plan_t P, float* ms6) {
+  if (!P || !ms6) return FTP_ERR_INVALID_ARG;
+  for (int i = 0; i < 6; ++i) ms6[i] = P->stage_ms[i];
   return FTP_OK;
 }
 
@@ -550,7 +651,7 @@ ftp_status ftp_sums(ftp_plan_t P, const double* t, const double* y, const double
     int d;
     ~Restore() { cudaSetDevice(d); }
   } restore{prev};
-  FTP_CK(cudaMemsetAsync(P->d_status, 0, sizeof(int) * ST_WORDS, P->stream));
+  FTP_CK(reset_call(P));
   const double *dt, *dyv, *ddy;
   st = stage_obs(P, t, y, dy, nobs, &dt, &dyv, &ddy);
   if (st != FTP_OK) return st;
@@ -585,7 +686,7 @@ ftp_status ftp_periodogram(ftp_plan_t P, const double* t, const double* y, const
   } restore{prev};
   int Hs = 0;
   for (int i = 0; i < ntemplates; ++i) Hs = std::max(Hs, tpl[i].H);
-  FTP_CK(cudaMemsetAsync(P->d_status, 0, sizeof(int) * ST_WORDS, P->stream));
+  FTP_CK(reset_call(P));
   const double *dt, *dyv, *ddy;
   st = stage_obs(P, t, y, dy, nobs, &dt, &dyv, &ddy);
   if (st != FTP_OK) return st;
@@ -607,12 +708,10 @@ ftp_status ftp_periodogram(ftp_plan_t P, const double* t, const double* y, const
     for (int i = 0; i < 4; ++i) o[i] = P->d_out + (size_t)i * P->max_templates * nf;
     of = flags ? P->d_flags : nullptr;
   }
-  for (const HGroup& g : groups) {
-    st = run_roots(P, g.H, Hs, nf, P->d_alpha + (size_t)g.first * kMaxH, P->d_rows + g.first,
-                   g.count, o[0], o[1], o[2], o[3], of, nf, &launches);
-    if (st != FTP_OK) return st;
-  }
-  ev_rec(P, 5);
+  st = solve(P, dt, dyv, ddy, nobs, P->grid.df, P->grid.k0, nf, Hs, groups, P->d_alpha, P->d_rows,
+             nullptr, o, of, direct ? (int64_t)nout : (int64_t)P->max_templates * nf, &launches);
+  if (st != FTP_OK) return st;
+  ev_rec(P, 6);
   if (!direct) {
     double* dsto[4] = {power, theta1, theta2, theta3};
     for (int i = 0; i < 4; ++i)
@@ -659,7 +758,7 @@ ftp_status ftp_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     int d;
     ~Restore() { cudaSetDevice(d); }
   } restore{prev};
-  FTP_CK(cudaMemsetAsync(P->d_status, 0, sizeof(int) * ST_WORDS, P->stream));
+  FTP_CK(reset_call(P));
   std::vector<HGroup> groups;
   std::vector<int> pos_of;
   st = upload_templates(P, bank, nbank, &groups, &pos_of);
@@ -689,23 +788,22 @@ ftp_status ftp_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     double* o[4] = {power + out_off[c], theta1 + out_off[c], theta2 + out_off[c],
                     theta3 + out_off[c]};
     uint8_t* of = flags ? flags + out_off[c] : nullptr;
+    int64_t out_lim = (int64_t)nout;  // caller arrays: this curve's block
     if (!out_dev) {
       for (int i = 0; i < 4; ++i) o[i] = P->d_out + (size_t)i * P->max_templates * P->grid.nf;
       of = flags ? P->d_flags : nullptr;
+      out_lim = (int64_t)P->max_templates * P->grid.nf;
     }
     if (tpl_of_curve) {
       const int q = pos_of[tpl_of_curve[c]];
-      st = run_roots(P, bank[tpl_of_curve[c]].H, Hc, g.nf, P->d_alpha + (size_t)q * kMaxH, P->d_row0, 1,
-                     o[0], o[1], o[2], o[3], of, g.nf, &launches);
-      if (st != FTP_OK) return st;
+      const std::vector<HGroup> one{{bank[tpl_of_curve[c]].H, 0, 1}};
+      st = solve(P, dt, dyv, ddy, n, g.df, g.k0, g.nf, Hc, one, P->d_alpha + (size_t)q * kMaxH,
+                 nullptr, P->d_row0, o, of, out_lim, &launches);
     } else {
-      for (const HGroup& gr : groups) {
-        st = run_roots(P, gr.H, Hc, g.nf, P->d_alpha + (size_t)gr.first * kMaxH,
-                       P->d_rows + gr.first, gr.count, o[0], o[1], o[2], o[3], of, g.nf,
-                       &launches);
-        if (st != FTP_OK) return st;
-      }
+      st = solve(P, dt, dyv, ddy, n, g.df, g.k0, g.nf, Hc, groups, P->d_alpha, P->d_rows,
+                 nullptr, o, of, out_lim, &launches);
     }
+    if (st != FTP_OK) return st;
     if (!out_dev) {
       double* dsto[4] = {power + out_off[c], theta1 + out_off[c], theta2 + out_off[c],
                          theta3 + out_off[c]};

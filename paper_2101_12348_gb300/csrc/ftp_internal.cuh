@@ -18,7 +18,22 @@ enum : int {
 };
 
 // Layout of the device status block (ints).
-enum : int { ST_CODE = 0, ST_TIMEOUT_SITE = 1, ST_NONCONV = 2, ST_WORDS = 4 };
+enum : int { ST_CODE = 0, ST_DBG_SITE = 4, ST_DBG_A = 5, ST_DBG_B = 6, ST_DBG_N = 7, ST_WORDS = 8 };
+
+// Self-checking builds (-DFTP_DEVICE_CHECKS): an index or alignment check
+// that fails records (site, value, bound) in the status block once and the
+// guarded access is skipped.  Release builds compile the checks away.
+#ifdef FTP_DEVICE_CHECKS
+#define FTP_DCHECK(status, cond, site, val, bound)                         \
+  ((cond) ? true                                                           \
+          : (atomicAdd(&(status)[ST_DBG_N], 1) == 0                        \
+                 ? ((status)[ST_DBG_SITE] = (site), (status)[ST_DBG_A] = (int)(val), \
+                    (status)[ST_DBG_B] = (int)(bound), false)              \
+                 : false))
+#else
+#define FTP_DCHECK(status, cond, site, val, bound) true
+#endif
+enum : int { CNT_ITERS = 0, CNT_ITEMS = 1, CNT_NONCONV = 2, CNT_REDO = 3, CNT_WORDS = 4 };
 
 // Layout of the device moments block (doubles).
 enum : int { MO_YBAR = 0, MO_YY = 1, MO_WSUM = 2, MO_UNIT = 3, MO_WORDS = 4 };
@@ -26,6 +41,15 @@ enum : int { MO_YBAR = 0, MO_YY = 1, MO_WSUM = 2, MO_UNIT = 3, MO_WORDS = 4 };
 constexpr int kSpreadTile = 2048;       // grid cells owned by one spreading CTA
 constexpr int kSpreadTileShift = 11;
 constexpr int kMaxH = 16;
+
+// Bound on the absolute error of one NFFT sum Z_h (relative to sum w = 1),
+// used by the a-posteriori error estimate of P, and the estimated error of P
+// above which a frequency is re-solved from direct FP64 sums: FP32 NFFT
+// (mixed path) and FP64 NFFT (FP64 path).
+constexpr double kSumErrF32 = 3e-7;
+constexpr double kRedoTolF32 = 1e-5;
+constexpr double kSumErrF64 = 2e-13;
+constexpr double kRedoTolF64 = 1e-10;
 
 template <typename T> struct C2;
 template <> struct C2<float> { using type = float2; };
@@ -60,10 +84,19 @@ void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int
                    int64_t nf_pad, int Hs, int m, double beta, typename C2<R>::type* sums,
                    const int* status, cudaStream_t s);
 
+void launch_direct_sums(const double* t, const double* y, const double* dy, int64_t n,
+                        const double* moments, const int* status, double df, int64_t k0,
+                        const int* list, const int* count, int cap, int Hs, int64_t nf_pad,
+                        double2* sums, int64_t sums_elems, int* status_rw, cudaStream_t s);
+
 // Steps (b)-(c): assembly, roots, candidates, polish.
 struct RootsArgs {
-  const void* sums;        // [3*Hs][nf_pad] complex (float2 mixed / double2 fp64)
-  int64_t nf;
+  const void* sums;        // [3*Hs][nf_pad] complex (float2 or double2, per kernel)
+  int64_t sums_elems;      // elements of `sums` (bounds of the staged reads)
+  int64_t out_elems;       // elements of each output array
+  int64_t nf;              // items per template (host-side upper bound if nf_dev)
+  const int* nf_dev;       // nullable: the item count, read on the device
+  const int* kmap;         // nullable: output column of item k (else k)
   int64_t nf_pad;
   int Hs;                  // harmonics the sums were computed for
   int H;                   // template harmonics of this launch (<= Hs)
@@ -78,17 +111,26 @@ struct RootsArgs {
   uint8_t* flags;          // nullable
   int64_t out_stride;
   int* status;
+  unsigned long long* counters;  // CNT_* solver statistics
+  unsigned long long* queue;     // work-unit counter, zero at launch
+  // re-solve list (mixed path): frequencies whose estimated error of P from
+  // the FP32 sums exceeds kRedoTol; nullable (no re-solve)
+  int* redo_list;
+  int* redo_mark;          // [nf] 0/1, dedupes frequencies across templates
+  int* redo_count;
+  int redo_cap;
+  double sum_err;          // error bound of one sum (kSumErr*)
+  double redo_tol;         // re-solve threshold on the estimated error of P
   int maxit;
   int polish_steps;
 };
 
-// Launches the assembly + Aberth + candidate kernel for the precision of the
-// plan (mixed: float Aberth on float2 sums; otherwise all double).  Returns
-// the number of kernel launches issued (1) or a negative value for an
-// unsupported H.
-int launch_roots(bool mixed, const RootsArgs& a, int num_sms, cudaStream_t s);
+// Kernel variants: float2 sums + FP32 Aberth (mixed), double2 sums + FP64
+// Aberth (FP64 path), double2 sums + FP32 Aberth (mixed re-solve pass).
+enum RootsKind { ROOTS_MIXED = 0, ROOTS_FP64 = 1, ROOTS_REDO = 2 };
 
-// Dynamic shared memory bytes the roots kernel needs (for tests/tuning).
-size_t roots_smem_bytes(bool mixed, int H);
+// Launches the assembly + Aberth + candidate kernel.  Returns the number of
+// kernel launches issued (1), -1 for an unsupported H, -2 on a CUDA error.
+int launch_roots(RootsKind kind, const RootsArgs& a, int num_sms, cudaStream_t s);
 
 }  // namespace ftp

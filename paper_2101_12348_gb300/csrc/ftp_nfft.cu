@@ -370,6 +370,74 @@ __global__ void gather_kernel(const typename C2<R>::type* __restrict__ X, int64_
   if (h <= Hs) sums[(int64_t)(2 * Hs + h - 1) * nf_pad + k] = gy;
 }
 
+
+// Direct FP64 sums for the frequencies of a list (the re-solve pass of the
+// mixed path): for listed frequency index k, f = (k0 + k) df,
+//   Z_h = sum_i w_i e^{i h 2 pi f t_i} (h <= 2 Hs),  Y_h = sum_i w_i (y_i - ybar) e^{...} (h <= Hs),
+// with the phase f t_i reduced modulo one cycle in FP64 and the harmonics
+// formed by repeated multiplication.  One CTA per listed frequency; each warp
+// reduces its lanes' terms with shuffles into shared accumulators.
+__global__ void __launch_bounds__(256) direct_sums_kernel(
+    const double* __restrict__ t, const double* __restrict__ y, const double* __restrict__ dy,
+    int64_t n, const double* __restrict__ moments, const int* __restrict__ status, double df,
+    int64_t k0, const int* __restrict__ list, const int* __restrict__ count, int cap, int Hs,
+    int64_t nf_pad, double2* __restrict__ sums, int64_t sums_elems, int* status_rw) {
+  __shared__ double2 acc[3 * kMaxH];
+  if (status[ST_CODE] != DEV_OK) return;
+  if (!FTP_DCHECK(status_rw, Hs >= 1 && Hs <= kMaxH, 31, Hs, kMaxH)) return;
+  const int total = min(*count, cap);
+  const double ybar = moments[MO_YBAR], wsum = moments[MO_WSUM];
+  const bool unit = moments[MO_UNIT] != 0.0;
+  const int lane = threadIdx.x & 31;
+  for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
+    if (!FTP_DCHECK(status_rw, list[idx] >= 0 && list[idx] < nf_pad, 32, list[idx], nf_pad)) break;
+    const double f = (double)(k0 + list[idx]) * df;
+    for (int q = threadIdx.x; q < 3 * Hs; q += blockDim.x) acc[q] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+      const int64_t i = base + threadIdx.x;
+      double w = 0.0, r = 0.0, c1 = 1.0, s1 = 0.0;
+      if (i < n) {
+        const double si = dy[i];
+        w = (unit ? 1.0 : 1.0 / (si * si)) / wsum;
+        r = w * (y[i] - ybar);
+        double cyc = f * t[i];
+        cyc -= floor(cyc);
+        sincospi(2.0 * cyc, &s1, &c1);
+      }
+      double pc = c1, ps = s1;  // e^{i h phi}
+      for (int h = 1; h <= 2 * Hs; ++h) {
+        double zx = w * pc, zy = w * ps, yx = r * pc, yy = r * ps;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          zx += __shfl_xor_sync(0xffffffffu, zx, o);
+          zy += __shfl_xor_sync(0xffffffffu, zy, o);
+          if (h <= Hs) {
+            yx += __shfl_xor_sync(0xffffffffu, yx, o);
+            yy += __shfl_xor_sync(0xffffffffu, yy, o);
+          }
+        }
+        if (lane == 0) {
+          atomicAdd(&acc[h - 1].x, zx);
+          atomicAdd(&acc[h - 1].y, zy);
+          if (h <= Hs) {
+            atomicAdd(&acc[2 * Hs + h - 1].x, yx);
+            atomicAdd(&acc[2 * Hs + h - 1].y, yy);
+          }
+        }
+        const double nc = pc * c1 - ps * s1;
+        ps = pc * s1 + ps * c1;
+        pc = nc;
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 3 * Hs; q += blockDim.x)
+      if (FTP_DCHECK(status_rw, (int64_t)q * nf_pad + idx < sums_elems, 33, q, idx))
+        sums[(int64_t)q * nf_pad + idx] = acc[q];
+    __syncthreads();
+  }
+}
+
 inline int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -382,6 +450,17 @@ inline int grid_for(int64_t n, int threads) {
 void launch_moments(const double* t, const double* y, const double* dy, int64_t n,
                     double* moments, int* status, cudaStream_t s) {
   moments_kernel<<<1, kRedThreads, 0, s>>>(t, y, dy, n, moments, status);
+}
+
+
+void launch_direct_sums(const double* t, const double* y, const double* dy, int64_t n,
+                        const double* moments, const int* status, double df, int64_t k0,
+                        const int* list, const int* count, int cap, int Hs, int64_t nf_pad,
+                        double2* sums, int64_t sums_elems, int* status_rw, cudaStream_t s) {
+  int grid = cap < 2 * 152 ? cap : 2 * 152;
+  if (grid < 1) grid = 1;
+  direct_sums_kernel<<<grid, 256, 0, s>>>(t, y, dy, n, moments, status, df, k0, list, count, cap,
+                                          Hs, nf_pad, sums, sums_elems, status_rw);
 }
 
 template <typename R>

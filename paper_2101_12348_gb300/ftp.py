@@ -34,7 +34,8 @@ STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE
 
 # every symbol include/ftp.h declares
 EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy",
-           "ftp_status_string", "ftp_plan_info", "ftp_set_timing", "ftp_stage_times")
+           "ftp_status_string", "ftp_plan_info", "ftp_solver_stats", "ftp_set_timing",
+           "ftp_stage_times")
 
 
 class FtpGrid(C.Structure):
@@ -77,6 +78,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.ftp_status_string.restype = C.c_char_p
     lib.ftp_plan_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64),
                                   C.POINTER(i32)]
+    lib.ftp_solver_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64),
+                                     C.POINTER(i64)]
     lib.ftp_set_timing.argtypes = [vp, i32]
     lib.ftp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
     for name in EXPORTS:
@@ -183,12 +186,21 @@ def ftp_plan_info(plan: int) -> dict:
             "last_launches": la.value}
 
 
+def ftp_solver_stats(plan: int) -> dict:
+    n, nc, rs = C.c_int64(), C.c_int64(), C.c_int64()
+    it = C.c_double()
+    _check(load().ftp_solver_stats(plan, C.byref(n), C.byref(it), C.byref(nc), C.byref(rs)),
+           "ftp_solver_stats")
+    return {"items": n.value, "mean_iterations": it.value, "nonconverged": nc.value,
+            "resolved": rs.value}
+
+
 def ftp_set_timing(plan: int, enable: bool) -> None:
     _check(load().ftp_set_timing(plan, 1 if enable else 0), "ftp_set_timing")
 
 
 def ftp_stage_times(plan: int) -> list:
-    a = (C.c_float * 5)()
+    a = (C.c_float * 6)()
     _check(load().ftp_stage_times(plan, a), "ftp_stage_times")
     return list(a)
 
@@ -248,3 +260,6 @@ class Plan:
 
     def info(self) -> dict:
         return ftp_plan_info(self.h)
+
+    def solver_stats(self) -> dict:
+        return ftp_solver_stats(self.h)

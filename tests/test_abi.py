@@ -65,3 +65,9 @@ def test_null_plan_is_rejected(lib):
         ftp.ftp_sums(None, t, t, t, 4, 1, np.zeros(4))
     assert e.value.status == 1
     ftp.ftp_destroy(None)  # no-op
+
+
+def test_build_compiles_every_translation_unit():
+    from paper_2101_12348_gb300 import build as b
+    cus = sorted(f for f in os.listdir(b.CSRC) if f.endswith(".cu"))
+    assert sorted(b.SOURCES) == cus
