@@ -193,6 +193,49 @@ ftp_status ftp_solver_stats(ftp_plan_t plan, int64_t* items, double* mean_iterat
 ftp_status ftp_set_timing(ftp_plan_t plan, int enable);
 ftp_status ftp_stage_times(ftp_plan_t plan, float* ms6);
 
+/*
+ * ftp_periodogram_sums_noalloc - steps (b)-(c) on sums the caller already
+ * holds, allocating nothing.  The paper has no counterpart: this is an entry
+ * point for callers that cannot call cudaMalloc - a process whose device
+ * memory belongs to another runtime's pool allocator, a latency-bound loop
+ * where cudaMalloc/cudaFree (which may synchronise the device) are not
+ * acceptable, or a service under a hard device-memory cap.  It needs no plan.
+ *
+ *   sums        device pointer, 16-byte aligned: the layout ftp_sums writes
+ *               (rows 0..2H_sums-1 = Z_1..Z_2H_sums, then H_sums rows
+ *               Y_1..Y_H_sums) with consecutive rows row_stride elements
+ *               apart; elements are float2 for FTP_MIXED, double2 for FTP_FP64
+ *   row_stride  >= nf rounded up to a multiple of 64, and row_stride times
+ *               the element size a multiple of 16 bytes (whole work units are
+ *               read; the padding may hold anything)
+ *   ybar, YY    the weighted mean and variance (ftp_sums' moments_out)
+ *   tpl         1..FTP_NOALLOC_MAX_TEMPLATES templates with H <= H_sums
+ *   outputs     device arrays [ntemplates][nf], as ftp_periodogram (flags
+ *               nullable)
+ *   device, cuda_stream   the device the pointers belong to and a stream of
+ *               it (NULL = default stream); the call returns after the stream
+ *               has finished its work
+ *
+ * Scratch: a fixed FTP_NOALLOC_SCRATCH_BYTES-byte array in the library's own
+ * device memory, held by every GPU that loads the library until the process
+ * exits.  The first call on a device looks up its address (make that first
+ * call before any stream capture).  Calls share the array: every value the
+ * kernel reads is written at the start of each call, and calls that overlap
+ * on the GPU race on it.  Requests beyond the array (more than
+ * FTP_NOALLOC_MAX_TEMPLATES templates) return FTP_ERR_UNSUPPORTED before any
+ * device work; bad sizes, strides, alignment or host pointers return
+ * FTP_ERR_INVALID_ARG.  Unlike ftp_periodogram it cannot re-solve
+ * ill-conditioned frequencies from the observations, which it does not see.
+ */
+#define FTP_NOALLOC_MAX_TEMPLATES 64
+#define FTP_NOALLOC_SCRATCH_BYTES (512 + FTP_NOALLOC_MAX_TEMPLATES * FTP_MAX_H * 16)
+ftp_status ftp_periodogram_sums_noalloc(const void* sums, int64_t row_stride,
+                                        ftp_precision prec, int64_t nf, int H_sums, double ybar,
+                                        double YY, const ftp_template* tpl, int ntemplates,
+                                        double* power, double* theta1, double* theta2,
+                                        double* theta3, uint8_t* flags, int device,
+                                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE
 # every symbol include/ftp.h declares
 EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy",
            "ftp_status_string", "ftp_plan_info", "ftp_solver_stats", "ftp_set_timing",
-           "ftp_stage_times")
+           "ftp_stage_times", "ftp_periodogram_sums_noalloc")
 
 
 class FtpGrid(C.Structure):
@@ -81,6 +81,9 @@ def load(path: str | None = None) -> C.CDLL:
     lib.ftp_solver_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64),
                                      C.POINTER(i64)]
     lib.ftp_set_timing.argtypes = [vp, i32]
+    lib.ftp_periodogram_sums_noalloc.argtypes = [vp, i64, i32, i64, i32, dbl, dbl,
+                                                 C.POINTER(FtpTemplate), i32, vp, vp, vp, vp,
+                                                 vp, i32, vp]
     lib.ftp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
     for name in EXPORTS:
         if name not in ("ftp_destroy", "ftp_status_string"):
@@ -203,6 +206,20 @@ def ftp_stage_times(plan: int) -> list:
     a = (C.c_float * 6)()
     _check(load().ftp_stage_times(plan, a), "ftp_stage_times")
     return list(a)
+
+
+def ftp_periodogram_sums_noalloc(sums, row_stride: int, precision: str, nf: int, H_sums: int,
+                                 ybar: float, YY: float, templates, power, theta1, theta2,
+                                 theta3, flags=None, device: int = 0,
+                                 stream: int | None = None) -> None:
+    """Root stage on device-resident sums without any allocation (see
+    include/ftp.h); all arrays must be device memory."""
+    prec = {"mixed": FTP_MIXED, "fp64": FTP_FP64}[precision]
+    arr, keep = _templates(templates)
+    _check(load().ftp_periodogram_sums_noalloc(
+        _ptr(sums), int(row_stride), prec, int(nf), int(H_sums), float(ybar), float(YY), arr,
+        len(keep) // 2, _ptr(power), _ptr(theta1), _ptr(theta2), _ptr(theta3), _ptr(flags),
+        int(device), stream), "ftp_periodogram_sums_noalloc")
 
 
 class Plan:
