@@ -21,6 +21,10 @@
 //   MM(theta) = a_0 + 2 Re sum_{e=1..2H} a_e psi^e,  a_e = [psi^{2H+e}] MM'
 //   YM(theta) = 2 Re sum_{k=1..H} b_k psi^k,         b_k = alpha_k conj(Y_k)
 //   Mbar(theta) = 2 Re sum_{n=1..H} c_n psi^n,        c_n = alpha_n conj(Z_n)
+// With c_n = alpha_n conj(Z_n) the MM' coefficients reduce to
+//   a_e = conj(Z_e) K_e - ( sum_{n+m=e} c_n c_m + 2 sum_{n-m=e} c_n conj(c_m) ),
+//   K_e = sum_{n+m=e} alpha_n alpha_m + 2 sum_{n-m=e} alpha_n conj(alpha_m),
+// where K_e depends on the template only: one complex product per pair term.
 // The final polynomial F = 2 MM' d(YM') - YM' d(MM') is anti-self-inversive,
 // F_{D-p} = -conj(F_p), so only p = 0..3H-1 are formed and the rest mirrored.
 //
@@ -34,7 +38,10 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 #include "ftp_internal.cuh"
+#include "ftp_wide.cuh"
 
 namespace ftp {
 namespace roots {
@@ -51,6 +58,11 @@ template <typename S2, typename R, int H, int G>
 struct Cfg {
   using R2 = typename R2T<R>::type;
   static constexpr bool kFast = sizeof(R) == 4;   // FP32 Aberth
+  // FP64-class steps: float-float on the mixed path (FP32 sums and Aberth),
+  // native FP64 on the FP64 path and the re-solve pass (FP64 sums)
+  static constexpr bool kDD = kFast && sizeof(S2) == 8;
+  using W = std::conditional_t<kDD, wide::dd, double>;
+  using WC = typename wide::CT<W>::type;
   static constexpr int D = 6 * H - 2;
   static constexpr int RR = cdiv_i(D, G);         // roots per lane
   static constexpr int NGW = 32 / G;              // items per warp unit
@@ -61,7 +73,8 @@ struct Cfg {
   static constexpr int NF = 3 * H;                // F_0..F_{3H-1}
   static constexpr int NFL = cdiv_i(NF, G);
   static constexpr int NSLOT = H + 1;             // assembly slots {0}, {e, 2H+1-e}
-  // per-group shared memory (bytes)
+  // per-group shared memory (bytes); WC elements are 16 bytes either way
+  static_assert(sizeof(WC) == 16, "wide complex layout");
   static constexpr size_t G_Z64 = 0;
   static constexpr size_t G_Y64 = G_Z64 + NA * 16;
   static constexpr size_t G_A64 = G_Y64 + NB * 16;
@@ -70,17 +83,16 @@ struct Cfg {
   static constexpr size_t G_F = G_C64 + NB * 16;
   static constexpr size_t G_Z = G_F + rup((D + 1) * sizeof(R2), 16);
   static constexpr size_t G_AW = G_Z + rup(RR * G * sizeof(R2), 16);
-  static constexpr size_t G_BW = G_AW + (kFast ? rup(NA * sizeof(R2), 16) : 0);
-  static constexpr size_t G_END = G_BW + (kFast ? rup(NB * sizeof(R2), 16) : 0);
+  static constexpr size_t G_BW = G_AW + rup(NA * sizeof(R2), 16);
+  static constexpr size_t G_END = G_BW + rup(NB * sizeof(R2), 16);
   static constexpr size_t GROUP_BYTES = rup(G_END, 16);
   // per-warp shared memory
   static constexpr size_t ROW_BYTES = NGW * sizeof(S2);
   static constexpr size_t STAGE_BYTES = ROWS * ROW_BYTES;
   static constexpr size_t W_STAGE = 0;                                   // 2 buffers
   static constexpr size_t W_MBAR = rup(2 * STAGE_BYTES, 16);             // 2 mbarriers
-  static constexpr size_t W_AA = W_MBAR + 16;                            // alpha_n alpha_m
-  static constexpr size_t W_AC = W_AA + H * H * 16;                      // alpha_n conj alpha_m
-  static constexpr size_t W_AL = W_AC + H * H * 16;                      // alpha_n
+  static constexpr size_t W_KE = W_MBAR + 16;                            // K_e, e = 0..2H
+  static constexpr size_t W_AL = W_KE + NA * 16;                         // alpha_n
   static constexpr size_t W_GROUPS = rup(W_AL + H * 16, 128);
   static constexpr size_t WARP_BYTES = rup(W_GROUPS + NGW * GROUP_BYTES, 128) + 16;
   static constexpr size_t SMEM = WARPS * WARP_BYTES;
@@ -122,7 +134,12 @@ template <typename T2, typename T> __device__ __forceinline__ T2 cscale(T2 a, T 
 }
 __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
-__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+// one MUFU reciprocal (flush-to-zero approximation); the iteration corrects it
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 template <typename T2> __device__ __forceinline__ T2 cdiv(T2 a, T2 b) {
   const auto inv = fast_rcp(cabs2(b));
@@ -203,17 +220,22 @@ template <int G> __device__ __forceinline__ bool gor(bool v) {
   return x != 0;
 }
 // psi^(gl+1) in lane gl of each group (inclusive product scan over the group).
-template <int G>
-__device__ __forceinline__ double2 group_powers(double2 psi, int gl) {
-  double2 pw = psi;
+template <int G, typename W>
+__device__ __forceinline__ typename wide::CT<W>::type group_powers(
+    typename wide::CT<W>::type psi, int gl) {
+  using namespace wide;
+  auto pw = psi;
 #pragma unroll
   for (int o = 1; o < G; o <<= 1) {
-    double2 v;
-    v.x = __shfl_up_sync(0xffffffffu, pw.x, o, G);
-    v.y = __shfl_up_sync(0xffffffffu, pw.y, o, G);
-    if (gl >= o) pw = cmul(pw, v);
+    const auto v = mkc(w_shfl_up(re(pw), o, G), w_shfl_up(im(pw), o, G));
+    if (gl >= o) pw = c_mul<W>(pw, v);
   }
   return pw;
+}
+template <int G, typename W> __device__ __forceinline__ W wsum(W v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = wide::w_add(v, wide::w_shfl_xor(v, o, G));
+  return v;
 }
 
 // Real trigonometric polynomial in the working precision, |psi| = 1:
@@ -228,42 +250,45 @@ __device__ __forceinline__ T trig_eval(const T2* c, int n, T2 psi, T v0) {
 
 template <typename S2, typename R, int H, int G>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(const RootsArgs a) {
+  using namespace wide;
   using C = Cfg<S2, R, H, G>;
   using R2 = typename C::R2;
+  using W = typename C::W;
+  using WC = typename C::WC;
   constexpr int D = C::D, RR = C::RR, NGW = C::NGW;
   constexpr bool kFast = C::kFast;
   constexpr R kTwoPi = R(6.283185307179586476925286766559);
-  constexpr double kTwoPiD = 6.283185307179586476925286766559;
   constexpr R tol = kFast ? R(2e-6) : R(1e-12);
   constexpr R tie = kFast ? R(1e-6) : R(1e-12);
   // F ~ 0 relative to |a| |b| (rounding level of the working precision)
-  constexpr double const_rel = kFast ? 1e-5 : 1e-13;
+  constexpr R const_rel = kFast ? R(1e-5) : R(1e-13);
 
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wb = smem + (size_t)warp * C::WARP_BYTES;
   S2* stage = reinterpret_cast<S2*>(wb + C::W_STAGE);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(wb + C::W_MBAR);
-  double2* AA = reinterpret_cast<double2*>(wb + C::W_AA);
-  double2* AC = reinterpret_cast<double2*>(wb + C::W_AC);
-  double2* AL = reinterpret_cast<double2*>(wb + C::W_AL);
+  WC* KE = reinterpret_cast<WC*>(wb + C::W_KE);
+  WC* AL = reinterpret_cast<WC*>(wb + C::W_AL);
   const int gl = lane % G, gi = lane / G;
   unsigned char* gb = wb + C::W_GROUPS + (size_t)gi * C::GROUP_BYTES;
-  double2* Z64 = reinterpret_cast<double2*>(gb + C::G_Z64);
-  double2* Y64 = reinterpret_cast<double2*>(gb + C::G_Y64);
-  double2* A64 = reinterpret_cast<double2*>(gb + C::G_A64);
-  double2* B64 = reinterpret_cast<double2*>(gb + C::G_B64);
-  double2* C64 = reinterpret_cast<double2*>(gb + C::G_C64);
+  WC* Z64 = reinterpret_cast<WC*>(gb + C::G_Z64);
+  WC* Y64 = reinterpret_cast<WC*>(gb + C::G_Y64);
+  WC* A64 = reinterpret_cast<WC*>(gb + C::G_A64);
+  WC* B64 = reinterpret_cast<WC*>(gb + C::G_B64);
+  WC* C64 = reinterpret_cast<WC*>(gb + C::G_C64);
   R2* Fs = reinterpret_cast<R2*>(gb + C::G_F);
   R2* Zs = reinterpret_cast<R2*>(gb + C::G_Z);
-  R2* Aw = kFast ? reinterpret_cast<R2*>(gb + C::G_AW) : reinterpret_cast<R2*>(A64);
-  R2* Bw = kFast ? reinterpret_cast<R2*>(gb + C::G_BW) : reinterpret_cast<R2*>(B64);
+  R2* Aw = reinterpret_cast<R2*>(gb + C::G_AW);  // working-precision copies
+  R2* Bw = reinterpret_cast<R2*>(gb + C::G_BW);
 
   if (a.status[ST_CODE] != DEV_OK) return;
   const int64_t nf = a.nf_dev ? (int64_t)*a.nf_dev : a.nf;
   const int64_t nkb = (nf + NGW - 1) / NGW;
   const int64_t nunits = nkb * a.ntpl;
-  const double ybar = a.moments[MO_YBAR], YY = a.moments[MO_YY];
+  const W ybar = w_of<W>(a.moments[MO_YBAR]), YY = w_of<W>(a.moments[MO_YY]);
+  const R YYr = (R)a.moments[MO_YY];
+  const W twopi = w_of<W>(6.283185307179586476925286766559);
 
   if (lane == 0) {
     mbar_init(&mbar[0], 1);
@@ -301,7 +326,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
   unsigned long long st_iters = 0, st_items = 0, st_nonconv = 0, st_redo = 0;
   unsigned parity[2] = {0u, 0u};
   int buf = 0, cur_tau = -1;
-  double sum_abs_alpha = 0.0;
+  R sum_abs_alpha = R(0);
   int64_t u = grab();
   if (u < nunits) issue(u, 0);
   while (u < nunits) {
@@ -309,17 +334,20 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
     if (un < nunits) issue(un, buf ^ 1);
     const int tau = (int)(u / nkb);
     const int64_t kb = u % nkb;
-    if (tau != cur_tau) {  // warp-uniform: this warp's template tables
-      for (int i = lane; i < H * H; i += 32) {
-        const int n = i / H, m = i % H;
-        const double2 an = a.alpha[(size_t)tau * kMaxH + n];
-        const double2 am = a.alpha[(size_t)tau * kMaxH + m];
-        AA[i] = cmul(an, am);
-        AC[i] = cmul(an, cconj(am));
+    if (tau != cur_tau) {  // warp-uniform: this warp's template tables (FP64, then wide)
+      const double2* al = a.alpha + (size_t)tau * kMaxH;
+      for (int e = lane; e <= 2 * H; e += 32) {
+        double2 k = make_double2(0.0, 0.0);
+        for (int n = 1; n <= H; ++n) {
+          if (e - n >= 1 && e - n <= H) k = cfma(al[n - 1], al[e - n - 1], k);
+          if (n - e >= 1) k = cfma(cscale(al[n - 1], 2.0), cconj(al[n - e - 1]), k);
+        }
+        KE[e] = mkc(w_of<W>(k.x), w_of<W>(k.y));
       }
-      if (lane < H) AL[lane] = a.alpha[(size_t)tau * kMaxH + lane];
-      sum_abs_alpha = 0.0;
-      for (int n = 0; n < H; ++n) sum_abs_alpha += sqrt(cabs2(a.alpha[(size_t)tau * kMaxH + n]));
+      if (lane < H) AL[lane] = mkc(w_of<W>(al[lane].x), w_of<W>(al[lane].y));
+      double sa = 0.0;
+      for (int n = 0; n < H; ++n) sa += sqrt(cabs2(al[n]));
+      sum_abs_alpha = (R)sa;
       cur_tau = tau;
       __syncwarp();
     }
@@ -333,61 +361,66 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
     const int64_t k = kb * NGW + gi;
     const bool valid = k < nf;
 
-    // ---- sums of this item into FP64 shared memory (one conversion each)
+    // ---- sums of this item into wide shared memory (one conversion each)
     for (int q = gl; q < C::ROWS; q += G) {
-      const double2 v = to_d2(st[q * NGW + gi]);
-      if (q < 2 * H) Z64[q + 1] = v;
-      else Y64[q - 2 * H + 1] = v;
+      const S2 v = st[q * NGW + gi];
+      WC wv;
+      if constexpr (C::kDD) {
+        wv = mkc(w_off<W>((float)v.x), w_off<W>((float)v.y));
+      } else {
+        wv = mkc((double)v.x, (double)v.y);
+      }
+      if (q < 2 * H) Z64[q + 1] = wv;
+      else Y64[q - 2 * H + 1] = wv;
     }
     if (gl == 0) {
-      Z64[0] = make_double2(1.0, 0.0);
-      Y64[0] = make_double2(0.0, 0.0);
+      Z64[0] = mkc(w_of<W>(1.0), w_zero<W>());
+      Y64[0] = c_zero<W>();
     }
     __syncwarp();
 
-    // ---- (b) FP64 assembly of a_e: slot 0 = {0}, slot s = {s, 2H+1-s}
-    double amax2 = 0.0, bmax2 = 0.0;
+    // ---- (b) assembly (FP64-class).  b_k = alpha_k conj(Y_k), c_n = alpha_n conj(Z_n)
+    R amax2 = R(0), bmax2 = R(0);
+    for (int kk = gl; kk <= H; kk += G) {
+      WC bv = c_zero<W>(), cv = c_zero<W>();
+      if (kk > 0) {
+        bv = c_mul<W>(AL[kk - 1], c_conj<W>(Y64[kk]));
+        cv = c_mul<W>(AL[kk - 1], c_conj<W>(Z64[kk]));
+      }
+      B64[kk] = bv;
+      C64[kk] = cv;
+      const R2 bw = mk<R2>((R)w_f(re(bv)), (R)w_f(im(bv)));
+      Bw[kk] = bw;
+      bmax2 = fmax(bmax2, cabs2(bw));
+    }
+    __syncwarp();
+    // a_e = conj(Z_e) K_e - S_e over slots {0}, {e, 2H+1-e}
     for (int s = gl; s < C::NSLOT; s += G) {
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         if (s == 0 && half == 1) break;
         const int e = (s == 0) ? 0 : (half == 0 ? s : 2 * H + 1 - s);
-        double2 acc = make_double2(0.0, 0.0);
+        WC acc;
         if (e == 0) {
-          for (int n = 1; n <= H; ++n)
-            acc.x += 2.0 * AC[(n - 1) * H + (n - 1)].x * (1.0 - cabs2(Z64[n]));
+          W q = w_zero<W>();
+          for (int n = 1; n <= H; ++n) q = w_add(q, c_abs2<W>(C64[n]));
+          acc = mkc(w_sub(re(KE[0]), w_mulf(q, 2.0f)), w_zero<W>());
         } else {
-          const double2 Ze = Z64[e];
-          // alpha_n alpha_m conj(Z_e - Z_n Z_m) over n + m = e; symmetric in (n, m)
+          WC S = c_zero<W>();
           const int nlo = e - H > 1 ? e - H : 1;
-          for (int n = nlo; 2 * n <= e; ++n) {
-            const int m = e - n;
-            const double2 t = cconj(csub(Ze, cmul(Z64[n], Z64[m])));
-            const double2 w = AA[(n - 1) * H + (m - 1)];
-            acc = cfma(n == m ? w : cscale(w, 2.0), t, acc);
+          for (int n = nlo; 2 * n <= e; ++n) {  // sum_{n+m=e} c_n c_m, symmetric
+            const WC t = c_mul<W>(C64[n], C64[e - n]);
+            S = c_add<W>(S, (2 * n == e) ? t : c_mulf<W>(t, 2.0f));
           }
-          // 2 alpha_n conj(alpha_m) (conj(Z_e) - conj(Z_n) Z_m) over n - m = e
-          for (int n = e + 1; n <= H; ++n) {
-            const int m = n - e;
-            const double2 t = csub(cconj(Ze), cmul(cconj(Z64[n]), Z64[m]));
-            acc = cfma(cscale(AC[(n - 1) * H + (m - 1)], 2.0), t, acc);
-          }
+          for (int n = e + 1; n <= H; ++n)  // 2 sum_{n-m=e} c_n conj(c_m)
+            S = c_add<W>(S, c_mulf<W>(c_mul<W>(C64[n], c_conj<W>(C64[n - e])), 2.0f));
+          acc = c_sub<W>(c_mul<W>(c_conj<W>(Z64[e]), KE[e]), S);
         }
         A64[e] = acc;
-        if constexpr (kFast) Aw[e] = from_d2<R2>(acc);
-        amax2 = fmax(amax2, cabs2(acc));
+        const R2 aw = mk<R2>((R)w_f(re(acc)), (R)w_f(im(acc)));
+        Aw[e] = aw;
+        amax2 = fmax(amax2, cabs2(aw));
       }
-    }
-    for (int kk = gl; kk <= H; kk += G) {
-      double2 bv = make_double2(0.0, 0.0), cv = make_double2(0.0, 0.0);
-      if (kk > 0) {
-        bv = cmul(AL[kk - 1], cconj(Y64[kk]));
-        cv = cmul(AL[kk - 1], cconj(Z64[kk]));
-      }
-      B64[kk] = bv;
-      C64[kk] = cv;
-      if constexpr (kFast) Bw[kk] = from_d2<R2>(bv);
-      bmax2 = fmax(bmax2, cabs2(bv));
     }
     __syncwarp();
     amax2 = gmax<G>(amax2);
@@ -418,8 +451,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
     }
     fmax2 = gmax<G>(fmax2);
     // P independent of theta2 (or YM == 0): no roots to find.
-    const bool constant = !valid || !(bmax2 > 0.0) ||
-                          !((double)fmax2 > const_rel * const_rel * (double)(H * H) * amax2 * bmax2);
+    const bool constant = !valid || !(bmax2 > R(0)) ||
+                          !(fmax2 > const_rel * const_rel * (R)(H * H) * amax2 * bmax2);
     const R fscale = constant ? R(0) : R(1) / sqrt(fmax2);
 #pragma unroll
     for (int i = 0; i < C::NFL; ++i) {
@@ -478,13 +511,15 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
           p[r] = cfma(p[r], uu[r], f);
         }
       }
+      // sum_{j != i} 1/(z_i - z_j): the j = i term has d = 0 and contributes
+      // conj(0) / (0 + tiny) = 0, so no branch is needed
 #pragma unroll 2
       for (int j = 0; j < D; ++j) {
         const R2 zj = Zs[j];
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
           const R2 d = csub(z[r], zj);
-          const R inv = (j == r * G + gl) ? R(0) : fast_rcp(cabs2(d));
+          const R inv = fast_rcp(fma(d.x, d.x, fma(d.y, d.y, kFast ? R(1e-30) : R(1e-300))));
           S[r].x = fma(d.x, inv, S[r].x);
           S[r].y = fma(-d.y, inv, S[r].y);
         }
@@ -578,91 +613,115 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
         bpsi = mk<R2>(ox, oy);
       }
     }
-    double theta = (bkey < R(1e29)) ? (double)(bkey >= R(16) ? bkey - R(16) : bkey) : 0.0;
-    double2 psi = make_double2((double)bpsi.x, (double)bpsi.y);
-    {  // one Newton step onto |psi| = 1 in FP64
-      const double s = 1.5 - 0.5 * cabs2(psi);
-      psi = make_double2(psi.x * s, psi.y * s);
+    const R theta_w = (bkey < R(1e29)) ? (bkey >= R(16) ? bkey - R(16) : bkey) : R(0);
+    // psi in wide precision, one Newton step onto |psi| = 1
+    WC psi;
+    if constexpr (C::kDD) {
+      psi = mkc(w_off<W>((float)bpsi.x), w_off<W>((float)bpsi.y));
+    } else {
+      psi = mkc((double)bpsi.x, (double)bpsi.y);
+    }
+    {
+      const W sfac = w_sub(w_of<W>(1.5), w_mulf(c_abs2<W>(psi), 0.5f));
+      psi = mkc(w_mul(re(psi), sfac), w_mul(im(psi), sfac));
     }
 
-    // ---- FP64 Newton polish of the phase on g(theta) = 2 MM YM' - YM MM'
-    //      (theta-derivatives), the sums split over the group's lanes.  Every
-    //      lane of the warp runs the shuffles (groups differ in `constant`);
-    //      only the update is conditional.
-    {
-#pragma unroll 1
-      for (int s = 0; s < a.polish_steps; ++s) {
-        const double2 pw0 = group_powers<G>(psi, gl);  // psi^(gl+1)
-        const double2 stp = make_double2(__shfl_sync(0xffffffffu, pw0.x, G - 1, G),
-                                         __shfl_sync(0xffffffffu, pw0.y, G - 1, G));  // psi^G
-        double ma0 = 0, ma1 = 0, ma2 = 0, mb0 = 0, mb1 = 0, mb2 = 0;
-        double2 pw = pw0;
-        for (int e = gl + 1; e <= 2 * H; e += G) {
-          const double2 t = cmul(A64[e], pw);
-          ma0 += t.x;
-          ma1 = fma((double)e, t.y, ma1);
-          ma2 = fma((double)(e * e), t.x, ma2);
-          pw = cmul(pw, stp);
-        }
-        pw = pw0;
-        for (int e = gl + 1; e <= H; e += G) {
-          const double2 t = cmul(B64[e], pw);
-          mb0 += t.x;
-          mb1 = fma((double)e, t.y, mb1);
-          mb2 = fma((double)(e * e), t.x, mb2);
-          pw = cmul(pw, stp);
-        }
-        ma0 = gsum<G>(ma0);
-        ma1 = gsum<G>(ma1);
-        ma2 = gsum<G>(ma2);
-        mb0 = gsum<G>(mb0);
-        mb1 = gsum<G>(mb1);
-        mb2 = gsum<G>(mb2);
-        const double MM = A64[0].x + 2.0 * ma0, MMt = -2.0 * ma1, MMtt = -2.0 * ma2;
-        const double YM = 2.0 * mb0, YMt = -2.0 * mb1, YMtt = -2.0 * mb2;
-        const double g = 2.0 * MM * YMt - YM * MMt;
-        const double gt = MMt * YMt + 2.0 * MM * YMtt - YM * MMtt;
-        const double dl = g / gt;
-        if (!constant && isfinite(dl) && fabs(dl) < 1e-3) {
-          // psi <- psi e^{-i dl} (Taylor series, |dl| < 1e-3: error < 1e-18)
-          const double d2 = dl * dl;
-          const double cs = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0));
-          const double sn = dl * (1.0 - d2 * (1.0 / 6.0 - d2 * (1.0 / 120.0)));
-          psi = make_double2(psi.x * cs + psi.y * sn, psi.y * cs - psi.x * sn);
-          theta -= dl;
-        }
-      }
-    }
-    // ---- FP64 evaluation at the chosen phase: MM, YM, Mbar
-    double MM, YM, Mbar;
-    {
-      const double2 pw0 = group_powers<G>(psi, gl);
-      const double2 stp = make_double2(__shfl_sync(0xffffffffu, pw0.x, G - 1, G),
-                                       __shfl_sync(0xffffffffu, pw0.y, G - 1, G));
-      double sa = 0, sb = 0, sc2 = 0;
-      double2 pw = pw0;
+    // ---- polish and evaluation in one FP64-class pass.  At psi (the chosen
+    //      root) MM, YM, Mbar and their theta-derivatives come from
+    //      trigonometric sums split over the group's lanes; one Newton step on
+    //      g(theta) = 2 MM YM' - YM MM' gives the correction dl.  P is
+    //      stationary, so P at psi differs from P at the corrected phase by
+    //      O(dl^2); theta1 and Mbar are carried to it to first order.  Every
+    //      lane runs the shuffles (groups differ in `constant`).
+    // Trigonometric sums at phase psi over the group's lanes: returns
+    // {Re S_a, Im S'_a, Re S''_a, Re S_b, Im S'_b, Re S''_b, Re S_c, Im S'_c}
+    // with S_x = sum_e x_e psi^e, S'_x = sum_e e x_e psi^e, S''_x = sum e^2 ...
+    auto trig_sums = [&](WC ps0, W* v) {
+      const WC pw0 = group_powers<G, W>(ps0, gl);  // psi^(gl+1)
+      const WC stp = mkc(w_shfl(re(pw0), G - 1, G), w_shfl(im(pw0), G - 1, G));  // psi^G
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = w_zero<W>();
+      WC pw = pw0;
       for (int e = gl + 1; e <= 2 * H; e += G) {
-        sa += A64[e].x * pw.x - A64[e].y * pw.y;
+        const WC t = c_mul<W>(A64[e], pw);
+        v[0] = w_add(v[0], re(t));
+        v[1] = w_add(v[1], w_mulf(im(t), (float)e));
+        v[2] = w_add(v[2], w_mulf(re(t), (float)(e * e)));
         if (e <= H) {
-          sb += B64[e].x * pw.x - B64[e].y * pw.y;
-          sc2 += C64[e].x * pw.x - C64[e].y * pw.y;
+          const WC tb = c_mul<W>(B64[e], pw);
+          v[3] = w_add(v[3], re(tb));
+          v[4] = w_add(v[4], w_mulf(im(tb), (float)e));
+          v[5] = w_add(v[5], w_mulf(re(tb), (float)(e * e)));
+          const WC tc = c_mul<W>(C64[e], pw);
+          v[6] = w_add(v[6], re(tc));
+          v[7] = w_add(v[7], w_mulf(im(tc), (float)e));
         }
-        pw = cmul(pw, stp);
+        pw = c_mul<W>(pw, stp);
       }
-      MM = A64[0].x + 2.0 * gsum<G>(sa);
-      YM = 2.0 * gsum<G>(sb);
-      Mbar = 2.0 * gsum<G>(sc2);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = wsum<G>(v[i]);
+    };
+    W MM, YM, Mbar, dl = w_zero<W>(), th1 = w_zero<W>();
+    {
+      W v[8];
+      trig_sums(psi, v);
+      MM = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
+      const W MMt = w_mulf(v[1], -2.0f), MMtt = w_mulf(v[2], -2.0f);
+      YM = w_mulf(v[3], 2.0f);
+      const W YMt = w_mulf(v[4], -2.0f), YMtt = w_mulf(v[5], -2.0f);
+      Mbar = w_mulf(v[6], 2.0f);
+      const W Mbart = w_mulf(v[7], -2.0f);
+      if (a.polish_steps > 0 && !constant) {
+        const W g = w_sub(w_mulf(w_mul(MM, YMt), 2.0f), w_mul(YM, MMt));
+        const W gt = w_sub(w_add(w_mul(MMt, YMt), w_mulf(w_mul(MM, YMtt), 2.0f)), w_mul(YM, MMtt));
+        const W d = w_div(g, gt);
+        const float df = w_f(d);
+        if (isfinite(df) && fabsf(df) < 1e-3f) dl = d;
+      }
+      if (w_f(MM) > 0.0f) {
+        const W q = w_div(YM, MM);
+        const W dq = w_div(w_sub(w_mul(YMt, MM), w_mul(YM, MMt)), w_mul(MM, MM));
+        th1 = w_sub(q, w_mul(dl, dq));
+      }
+      Mbar = w_sub(Mbar, w_mul(dl, Mbart));
+      // A correction that is not tiny (an ill-conditioned item) makes the
+      // O(dl^2) shortcut too coarse: evaluate again at the corrected phase
+      // psi e^{-i dl} (Taylor series of cos, sin; |dl| < 1e-3).
+      const bool again = fabsf(w_f(dl)) > (kFast ? 1e-5f : 1e-9f);
+      if (__any_sync(0xffffffffu, again)) {
+        const W d2 = w_mul(dl, dl);
+        const W cs = w_sub(w_of<W>(1.0), w_mul(d2, w_sub(w_of<W>(0.5), w_mul(d2, w_of<W>(1.0 / 24.0)))));
+        const W sn = w_mul(dl, w_sub(w_of<W>(1.0), w_mul(d2, w_sub(w_of<W>(1.0 / 6.0),
+                                                                  w_mul(d2, w_of<W>(1.0 / 120.0))))));
+        const WC ps2 = mkc(w_add(w_mul(re(psi), cs), w_mul(im(psi), sn)),
+                           w_sub(w_mul(im(psi), cs), w_mul(re(psi), sn)));
+        W v2[8];
+        trig_sums(ps2, v2);
+        if (again) {
+          MM = w_add(re(A64[0]), w_mulf(v2[0], 2.0f));
+          YM = w_mulf(v2[3], 2.0f);
+          Mbar = w_mulf(v2[6], 2.0f);
+          th1 = (w_f(MM) > 0.0f) ? w_div(YM, MM) : w_zero<W>();
+        }
+      }
     }
-    if constexpr (!kFast) theta = atan2(psi.y, psi.x);
-    const bool degenerate = !(MM > 1e-14 * (MM + Mbar * Mbar));
-    double P = 0.0, th1 = 0.0;
+    W theta;
+    if constexpr (kFast) {
+      theta = w_sub(w_off<W>((float)theta_w), dl);
+    } else {
+      theta = w_sub(atan2(w_d(im(psi)), w_d(re(psi))), dl);
+    }
+    if (w_f(theta) < 0.0f) theta = w_add(theta, twopi);
+    if (w_f(theta) >= w_f(twopi)) theta = w_sub(theta, twopi);
+    const float MMf = w_f(MM), Mbf = w_f(Mbar);
+    const bool degenerate = !(MMf > 1e-14f * (MMf + Mbf * Mbf)) || !(MMf > 0.0f);
+    W P = w_zero<W>();
     if (!degenerate) {
-      th1 = YM / MM;
-      P = YM * th1 / YY;
+      P = w_div(w_mul(YM, YM), w_mul(YY, MM));
+    } else {
+      th1 = w_zero<W>();
     }
-    const double th3 = ybar - th1 * Mbar;
-    theta = fmod(theta, kTwoPiD);
-    if (theta < 0.0) theta += kTwoPiD;
+    const W th3 = w_sub(ybar, w_mul(th1, Mbar));
 
     // ---- a-posteriori error of P from the NFFT sums: |dZ| <= e gives
     //      |dMM| <= 9 e (sum|alpha|)^2 and |dYM| <= 2 e sum|alpha| sqrt(YY);
@@ -673,30 +732,36 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
       if (degenerate) {
         redo = true;
       } else {
-        const double dMM = 9.0 * a.sum_err * sum_abs_alpha * sum_abs_alpha;
-        const double dYM = 2.0 * a.sum_err * sum_abs_alpha * sqrt(YY);
-        const double err = P * dMM / MM + 2.0 * sqrt(fmax(P, 0.0) / (YY * MM)) * dYM;
-        redo = !(err <= a.redo_tol);
+        const R Pf = (R)w_f(P), Mf = (R)MMf;
+        const R dMM = R(9) * (R)a.sum_err * sum_abs_alpha * sum_abs_alpha;
+        const R dYM = R(2) * (R)a.sum_err * sum_abs_alpha * sqrt(YYr);
+        const R err = Pf * dMM / Mf + R(2) * sqrt(fmax(Pf, R(0)) / (YYr * Mf)) * dYM;
+        redo = !(err <= (R)a.redo_tol);
       }
     }
 
-    if (valid && gl == 0) {
-      const int64_t col = a.kmap ? (int64_t)a.kmap[k] : k;
-      const size_t o = (size_t)a.rows[tau] * a.out_stride + col;
-      if (!FTP_DCHECK(a.status, col >= 0 && col < a.out_stride, 21, col, a.out_stride) ||
-          !FTP_DCHECK(a.status, (int64_t)o < a.out_elems, 22, o, a.out_elems)) {
-        // out of range: write nothing (self-checking builds only)
-      } else {
-      a.power[o] = P;
-      a.theta1[o] = th1;
-      a.theta2[o] = theta;
-      a.theta3[o] = th3;
+    // ---- outputs: lanes 0..3 of the group convert one value each (one
+    //      conversion instruction for the whole warp), then write it
+    const int64_t col = valid ? (a.kmap ? (int64_t)a.kmap[k] : k) : 0;
+    const size_t o = (size_t)a.rows[tau] * a.out_stride + col;
+    const bool in_range =
+        FTP_DCHECK(a.status, !valid || (col >= 0 && col < a.out_stride), 21, col, a.out_stride) &&
+        FTP_DCHECK(a.status, !valid || (int64_t)o < a.out_elems, 22, o, a.out_elems);
+    {
+      const W v = gl == 0 ? P : gl == 1 ? th1 : gl == 2 ? theta : th3;
+      const double dv = w_d(v);
+      if (valid && in_range && gl < 4) {
+        double* dst = gl == 0 ? a.power : gl == 1 ? a.theta1 : gl == 2 ? a.theta2 : a.theta3;
+        dst[o] = dv;
+      }
+    }
+    if (valid && in_range && gl == 0) {
       if (a.flags) {
         unsigned f = 0;
         if (nonconv) f |= 1u;
         if (degenerate) f |= 2u;
         if (constant) f |= 4u;
-        if (th1 < 0.0) f |= 8u;
+        if (w_f(th1) < 0.0f) f |= 8u;
         a.flags[o] = (uint8_t)f;
       }
       if (redo && FTP_DCHECK(a.status, col < a.redo_cap, 23, col, a.redo_cap) &&
@@ -704,7 +769,6 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
         const int slot = atomicAdd(a.redo_count, 1);
         if (slot < a.redo_cap) a.redo_list[slot] = (int)col;
         ++st_redo;
-      }
       }
       st_iters += (unsigned long long)iters;
       st_items += 1;
