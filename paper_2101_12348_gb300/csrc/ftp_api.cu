@@ -61,6 +61,7 @@ struct ftp_plan_s {
   // device workspace
   double* d_in = nullptr;       // staged t, y, dy
   double* d_moments = nullptr;
+  unsigned char* d_mom_scratch = nullptr;  // moment partials + ticket
   int* d_status = nullptr;
   unsigned long long* d_counters = nullptr;
   unsigned long long* d_queue = nullptr;  // work-unit counter of the roots kernel
@@ -207,7 +208,7 @@ ftp_status run_sums(ftp_plan_t P, const double* t, const double* y, const double
   cudaStream_t s = P->stream;
   ev_rec(P, 0);
   FTP_CK(cudaMemsetAsync(P->d_tile_count, 0, sizeof(int) * ntiles, s));
-  launch_moments(t, y, dy, nobs, P->d_moments, P->d_status, s);
+  launch_moments(t, y, dy, nobs, P->d_moments, P->d_status, P->d_mom_scratch, s);
   if (P->mixed) {
     launch_points<float>(t, y, dy, nobs, P->d_moments, P->d_status, df, ngrid, P->d_tile_count,
                          P->d_cell, (float*)P->d_frac, (float2*)P->d_coef, s);
@@ -253,7 +254,7 @@ ftp_status run_sums(ftp_plan_t P, const double* t, const double* y, const double
                           P->beta, (double2*)P->d_sums, P->d_status, s);
   }
   ev_rec(P, 4);
-  *launches += 6;
+  *launches += 7;
   FTP_CK(cudaGetLastError());
   return FTP_OK;
 }
@@ -472,7 +473,7 @@ void ftp_destroy(ftp_plan_t P) {
   cudaSetDevice(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
   for (auto& kv : P->ffts) cufftDestroy(kv.second.h);
-  void* dptrs[] = {P->d_in, P->d_moments, P->d_status, P->d_counters, P->d_queue, P->d_redo_list,
+  void* dptrs[] = {P->d_in, P->d_moments, P->d_mom_scratch, P->d_status, P->d_counters, P->d_queue, P->d_redo_list,
                    P->d_redo_mark, P->d_redo_count, P->d_redo_sums, P->d_tile_count, P->d_tile_off,
                    P->d_cursor, P->d_cell, P->d_cell_s, P->d_frac, P->d_frac_s, P->d_coef,
                    P->d_coef_s, P->d_grid, P->d_sums, P->d_alpha, P->d_rows, P->d_row0, P->d_out,
@@ -553,6 +554,7 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
   } while (0)
   FTP_AL(P->d_in, 3 * nobs);
   FTP_AL(P->d_moments, MO_WORDS);
+  FTP_AL(P->d_mom_scratch, kMomentScratchBytes);
   FTP_AL(P->d_status, ST_WORDS);
   FTP_AL(P->d_counters, CNT_WORDS);
   FTP_AL(P->d_queue, 1);
@@ -585,7 +587,9 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
   FTP_AL(P->d_out, 4 * nout);
   FTP_AL(P->d_flags, nout);
 #undef FTP_AL
-  if (cudaMemset(P->d_sums, 0, sums_bytes) != cudaSuccess) return fail(FTP_ERR_CUDA);
+  if (cudaMemset(P->d_sums, 0, sums_bytes) != cudaSuccess ||
+      cudaMemset(P->d_mom_scratch, 0, kMomentScratchBytes) != cudaSuccess)
+    return fail(FTP_ERR_CUDA);
   if (cudaMemset(P->d_status, 0, sizeof(int) * ST_WORDS) != cudaSuccess ||
       cudaMemset(P->d_row0, 0, sizeof(int)) != cudaSuccess)
     return fail(FTP_ERR_CUDA);

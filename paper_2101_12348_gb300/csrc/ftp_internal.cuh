@@ -57,8 +57,12 @@ template <> struct C2<double> { using type = double2; };
 
 // ------------------------------------------------------------------ launches
 // Step (a): observation preparation, binning, spreading, FFT (host), gather.
+// Moments use a small scratch block (partials of at most kMomentBlocks CTAs
+// and an atomic ticket that must be zero before the first use).
+constexpr int kMomentBlocks = 304;
+constexpr size_t kMomentScratchBytes = 64 * kMomentBlocks + 16;
 void launch_moments(const double* t, const double* y, const double* dy, int64_t n,
-                    double* moments, int* status, cudaStream_t s);
+                    double* moments, int* status, void* scratch, cudaStream_t s);
 
 template <typename R>
 void launch_points(const double* t, const double* y, const double* dy, int64_t n,

@@ -26,7 +26,6 @@ namespace ftp {
 
 namespace {
 
-constexpr int kRedThreads = 1024;
 
 struct OpSum {
   template <typename T> __device__ T operator()(T a, T b) const { return a + b; }
@@ -60,17 +59,35 @@ __device__ T block_reduce(T v, T* sh, Op op) {
 
 // Weighted mean and variance in FP64 with the paper's weight rules
 // (Section 2): w_i ~ sigma_i^-2, all sigma = 0 -> unit weights, mixed zero /
-// non-zero sigma and Var(y) = 0 are errors.  One CTA.
-__global__ void __launch_bounds__(kRedThreads) moments_kernel(const double* __restrict__ t,
-                                                               const double* __restrict__ y,
-                                                               const double* __restrict__ dy,
-                                                               int64_t n, double* moments,
-                                                               int* status) {
+// non-zero sigma and Var(y) = 0 are errors.  Two passes (mean, then the sum
+// of squared deviations), each a grid-wide reduction: every CTA writes its
+// partial, and the CTA that takes the last ticket of an atomic counter
+// combines them (no CTA waits for another).
+struct MomentPartial {
+  double s0, s1, sy, ymin, ymax;  // sum w (sigma > 0), sum w y, sum y, min y, max y
+  long long nzero, nbad;
+};
+
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  return last;
+}
+
+__global__ void __launch_bounds__(256) moments_pass1(const double* __restrict__ t,
+                                                     const double* __restrict__ y,
+                                                     const double* __restrict__ dy, int64_t n,
+                                                     MomentPartial* part, unsigned* ticket,
+                                                     double* moments, int* status) {
   __shared__ double shd[32];
   __shared__ long long shl[32];
   double s0 = 0, s1 = 0, sy = 0, ymin = INFINITY, ymax = -INFINITY;
   long long nzero = 0, nbad = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const double ti = t[i], yi = y[i], si = dy[i];
     if (!isfinite(ti) || !isfinite(yi) || !isfinite(si) || si < 0.0) {
       ++nbad;
@@ -87,47 +104,77 @@ __global__ void __launch_bounds__(kRedThreads) moments_kernel(const double* __re
       s1 += w * yi;
     }
   }
-  s0 = block_reduce(s0, shd, OpSum());
-  s1 = block_reduce(s1, shd, OpSum());
-  sy = block_reduce(sy, shd, OpSum());
-  nzero = block_reduce(nzero, shl, OpSum());
-  nbad = block_reduce(nbad, shl, OpSum());
-  const double smin = block_reduce(ymin, shd, OpMin());
-  const double smax = block_reduce(ymax, shd, OpMax());
-
-  int code = DEV_OK;
-  double wsum = 0, ybar = 0;
-  bool unit = false;
-  if (nbad > 0) {
-    code = DEV_NONFINITE;
-  } else if (nzero == n) {
-    unit = true;
-    wsum = (double)n;
-    ybar = sy / (double)n;
-  } else if (nzero > 0) {
-    code = DEV_MIXED_ZERO_SIGMA;
-  } else {
-    wsum = s0;
-    ybar = s1 / s0;
-  }
-  if (code == DEV_OK && !(smax > smin)) code = DEV_ZERO_VARIANCE;
-
-  double yy = 0;
-  if (code == DEV_OK) {
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const double si = dy[i];
-      const double w = unit ? 1.0 : 1.0 / (si * si);
-      const double r = y[i] - ybar;
-      yy += w * r * r;
-    }
-  }
-  yy = block_reduce(yy, shd, OpSum());
+  MomentPartial p;
+  p.s0 = block_reduce(s0, shd, OpSum());
+  p.s1 = block_reduce(s1, shd, OpSum());
+  p.sy = block_reduce(sy, shd, OpSum());
+  p.ymin = block_reduce(ymin, shd, OpMin());
+  p.ymax = block_reduce(ymax, shd, OpMax());
+  p.nzero = block_reduce(nzero, shl, OpSum());
+  p.nbad = block_reduce(nbad, shl, OpSum());
+  if (threadIdx.x == 0) part[blockIdx.x] = p;
+  if (!last_block(ticket)) return;
   if (threadIdx.x == 0) {
+    MomentPartial q = part[0];
+    for (unsigned b = 1; b < gridDim.x; ++b) {
+      const MomentPartial r = part[b];
+      q.s0 += r.s0;
+      q.s1 += r.s1;
+      q.sy += r.sy;
+      q.ymin = fmin(q.ymin, r.ymin);
+      q.ymax = fmax(q.ymax, r.ymax);
+      q.nzero += r.nzero;
+      q.nbad += r.nbad;
+    }
+    int code = DEV_OK;
+    double wsum = 0, ybar = 0;
+    bool unit = false;
+    if (q.nbad > 0) {
+      code = DEV_NONFINITE;
+    } else if (q.nzero == n) {
+      unit = true;
+      wsum = (double)n;
+      ybar = q.sy / (double)n;
+    } else if (q.nzero > 0) {
+      code = DEV_MIXED_ZERO_SIGMA;
+    } else {
+      wsum = q.s0;
+      ybar = q.s1 / q.s0;
+    }
+    if (code == DEV_OK && !(q.ymax > q.ymin)) code = DEV_ZERO_VARIANCE;
     moments[MO_YBAR] = ybar;
-    moments[MO_YY] = (code == DEV_OK) ? yy / wsum : 0.0;
+    moments[MO_YY] = 0.0;
     moments[MO_WSUM] = wsum;
     moments[MO_UNIT] = unit ? 1.0 : 0.0;
     if (code != DEV_OK) atomicCAS(&status[ST_CODE], DEV_OK, code);
+    *ticket = 0u;  // ready for the next reduction
+  }
+}
+
+__global__ void __launch_bounds__(256) moments_pass2(const double* __restrict__ y,
+                                                     const double* __restrict__ dy, int64_t n,
+                                                     double* part, unsigned* ticket,
+                                                     double* moments, const int* status) {
+  __shared__ double shd[32];
+  if (status[ST_CODE] != DEV_OK) return;  // uniform: every CTA returns
+  const double ybar = moments[MO_YBAR];
+  const bool unit = moments[MO_UNIT] != 0.0;
+  double yy = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = dy[i];
+    const double w = unit ? 1.0 : 1.0 / (si * si);
+    const double r = y[i] - ybar;
+    yy += w * r * r;
+  }
+  yy = block_reduce(yy, shd, OpSum());
+  if (threadIdx.x == 0) part[blockIdx.x] = yy;
+  if (!last_block(ticket)) return;
+  if (threadIdx.x == 0) {
+    double tot = 0;
+    for (unsigned b = 0; b < gridDim.x; ++b) tot += part[b];
+    moments[MO_YY] = tot / moments[MO_WSUM];
+    *ticket = 0u;
   }
 }
 
@@ -356,8 +403,10 @@ __global__ void gather_kernel(const typename C2<R>::type* __restrict__ X, int64_
   const int64_t j = (int64_t)h * (k0 + k);
   const Cx xp = X[j];
   const Cx xm = X[ngrid - j];
-  const double nu = (double)j / (double)ngrid;
-  const R a = (R)(2.0 * M_PI * (double)m * nu);
+  // nu = j/n and the window transform in the working precision: its relative
+  // error is at the rounding level of the sums themselves
+  const R nu = (R)j / (R)ngrid;
+  const R a = R(6.283185307179586476925286766559) * (R)m * nu;
   const R bt = (R)beta;
   const R z = sqrt(bt * bt - a * a);
   const R inv = z / (R(2 * m) * sinh(z));
@@ -448,8 +497,16 @@ inline int grid_for(int64_t n, int threads) {
 }  // namespace
 
 void launch_moments(const double* t, const double* y, const double* dy, int64_t n,
-                    double* moments, int* status, cudaStream_t s) {
-  moments_kernel<<<1, kRedThreads, 0, s>>>(t, y, dy, n, moments, status);
+                    double* moments, int* status, void* scratch, cudaStream_t s) {
+  // scratch: [kMomentBlocks] partials + one ticket (zero between uses)
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > kMomentBlocks) blocks = kMomentBlocks;
+  if (blocks < 1) blocks = 1;
+  auto* part = static_cast<MomentPartial*>(scratch);
+  auto* ticket = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + kMomentScratchBytes - 16);
+  moments_pass1<<<blocks, 256, 0, s>>>(t, y, dy, n, part, ticket, moments, status);
+  moments_pass2<<<blocks, 256, 0, s>>>(y, dy, n, reinterpret_cast<double*>(part), ticket, moments,
+                                       status);
 }
 
 
