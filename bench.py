@@ -54,6 +54,10 @@ def parse_args():
                     help="timed steps of the FP64 path (0 skips it)")
     ap.add_argument("--n-freq", type=int, default=250_000,
                     help="frequencies of the grid (smaller only for profiling captures)")
+    ap.add_argument("--workload", choices=["long", "survey", "bank"], default="long",
+                    help="long: one long lightcurve (the headline line); survey: 4096 "
+                         "curves batched; bank: 32 templates over one N=1e5 lightcurve")
+    ap.add_argument("--ncurves", type=int, default=4096, help="curves of the survey workload")
     return ap.parse_args()
 
 
@@ -71,10 +75,17 @@ def _oracle_worker(args):
 def oracle_timing(lc, tpl, freqs, cores):
     """Time the FP64 oracle over `freqs` with a spawn pool of `cores` single-
     threaded workers; returns (seconds, powers)."""
-    import multiprocessing as mp
-
     import numpy as np
     chunks = [c for c in np.array_split(freqs, max(1, cores * 2)) if c.size]
+    jobs = [(lc.t, lc.y, lc.dy, ch, tpl.c, tpl.s) for ch in chunks]
+    dt, parts = oracle_jobs(jobs, cores)
+    return dt, np.concatenate(parts)
+
+
+def oracle_jobs(jobs, cores):
+    """Time oracle jobs (t, y, dy, freqs, c, s) on a spawn pool of `cores`
+    single-threaded workers; returns (seconds, [powers per job])."""
+    import multiprocessing as mp
     ctx = mp.get_context("spawn")
     env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {k: os.environ.get(k) for k in env_keys}
@@ -82,9 +93,10 @@ def oracle_timing(lc, tpl, freqs, cores):
         os.environ[k] = "1"
     try:
         with ctx.Pool(cores) as pool:
-            pool.map(_oracle_worker, [(lc.t, lc.y, lc.dy, chunks[0][:1], tpl.c, tpl.s)] * cores)
+            j0 = jobs[0]
+            pool.map(_oracle_worker, [(j0[0], j0[1], j0[2], j0[3][:1], j0[4], j0[5])] * cores)
             t0 = time.perf_counter()
-            parts = pool.map(_oracle_worker, [(lc.t, lc.y, lc.dy, ch, tpl.c, tpl.s) for ch in chunks])
+            parts = pool.map(_oracle_worker, jobs)
             dt = time.perf_counter() - t0
     finally:
         for k, v in saved.items():
@@ -92,7 +104,7 @@ def oracle_timing(lc, tpl, freqs, cores):
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    return dt, np.concatenate(parts)
+    return dt, parts
 
 
 def cpu_cores():
@@ -353,6 +365,297 @@ def run_ours(args, world, rank, local, pg):
         print(json.dumps(result), flush=True)
 
 
+# ------------------------------------------------------------------ extra workloads
+SURVEY = ("batched survey: {n} lightcurves, N_obs lognormal (median 1000, clipped 50-20000), "
+          "baselines U(100,3000) d, bank of 16 templates H in (2,4,6), one per curve, "
+          "df=1/(5T), f<=10/d")
+BANK = ("template bank over one long lightcurve: N_obs=1e5 over 4000 d with nightly gaps, "
+        "32 templates H=10, N_f=1e6, df=1/(5*4000 d)")
+
+
+def _timed_calls(stream, flush, steps, call):
+    """CUDA-event times (ms) of `steps` calls on `stream`, L2 flushed before each."""
+    import torch
+    out = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _result(args, world, metric_value, step_ms, cfg, **extra):
+    r = {"metric": METRIC, "value": round(metric_value, 1), "unit": UNIT, "n_gpus": world,
+         "steps": args.steps, "warmup": args.warmup,
+         "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+         "data": "synthetic", "config": cfg}
+    r.update(extra)
+    return r
+
+
+def run_survey(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_2101_12348_gb300 import ftp
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sv = synth.survey(ncurves=args.ncurves, seed=1003)
+    bank = [(b.c, b.s) for b in sv.bank]
+    grids = [(g.df, g.k0, g.nf) for g in sv.grids]
+    nfs = np.array([g.nf for g in sv.grids], dtype=np.int64)
+    Hc = np.array([sv.bank[i].H for i in sv.tpl_of_curve])
+    out_off = np.zeros(sv.ncurves + 1, dtype=np.int64)
+    out_off[1:] = np.cumsum(nfs)
+    tot = int(out_off[-1])
+    gj = max(sv.grids, key=lambda g: g.k0 + g.nf)
+    plan_grid = (gj.df, gj.k0, int(nfs.max()))
+    max_nobs = int(np.max(np.diff(sv.obs_off)))
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    dt_, dy_, ds_ = (torch.from_numpy(a).to(dev) for a in (sv.t, sv.y, sv.dy))
+    outs = [torch.empty(tot, dtype=torch.float64, device=dev) for _ in range(4)]
+    fl = torch.empty(tot, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    plan = ftp.ftp_plan(max_nobs, 6, plan_grid, len(bank), "mixed", local, sh)
+
+    def call():
+        ftp.ftp_batch(plan, sv.obs_off, dt_, dy_, ds_, grids, out_off[:-1], bank,
+                      sv.tpl_of_curve, *outs, fl)
+
+    t_first = time.perf_counter()
+    call()  # first call: FFT plans, workspace
+    first_s = time.perf_counter() - t_first
+    for _ in range(max(0, args.warmup - 1)):
+        call()
+    barrier(pg)
+    with ClockSampler(local) as clk:
+        step_ms = _timed_calls(stream, flush, args.steps, call)
+    barrier(pg)
+    clocks = clk.summary()
+    info = ftp.ftp_batch_info(plan)
+    launches = ftp.ftp_plan_info(plan)["last_launches"]
+    total_ms = max_over_ranks(pg, sum(step_ms), dev)
+    value = sum_over_ranks(pg, float(args.steps * tot), dev) / (total_ms / 1e3)
+    # one eager call with stage timing: the split between sums and roots
+    ftp.ftp_set_timing(plan, True)
+    call()
+    st = ftp.ftp_stage_times(plan)
+    stats = ftp.ftp_solver_stats(plan)
+    ftp.ftp_set_timing(plan, False)
+    ibar = stats["mean_iterations"]
+    flops = float(np.sum(nfs * 26.0 * (6 * Hc - 2) ** 2)) * ibar
+    achieved = flops / (st[4] / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "kernel": "roots_kernel (FP32 Aberth flops 26*D^2*iterations, summed over "
+                          "curves with the batch's mean iteration count)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    # FP64 path on the first 64 curves, and the mixed-vs-FP64 error there
+    nsub = min(64, sv.ncurves)
+    sub_tot = int(out_off[nsub])
+    p64 = ftp.ftp_plan(max_nobs, 6, plan_grid, len(bank), "fp64", local, sh)
+    o64 = [torch.empty(sub_tot, dtype=torch.float64, device=dev) for _ in range(4)]
+    sub_off = sv.obs_off[:nsub + 1].copy()
+
+    def call64():
+        ftp.ftp_batch(p64, sub_off, dt_, dy_, ds_, grids[:nsub], out_off[:nsub], bank,
+                      sv.tpl_of_curve[:nsub], *o64, None)
+
+    call64()
+    d_ms = _timed_calls(stream, flush, max(1, args.fp64_steps), call64)
+    fp64_path = {"value": round(sub_tot * len(d_ms) / (sum(d_ms) / 1e3), 1), "unit": UNIT,
+                 "curves": nsub, "ms_per_step": round(statistics.mean(d_ms), 3),
+                 "max_abs_dP_mixed_vs_fp64":
+                     float(torch.max(torch.abs(outs[0][:sub_tot] - o64[0])).item())}
+    ftp.ftp_destroy(p64)
+    del o64
+    # end to end: pinned host inputs and outputs, copies inside the timed region
+    th = [torch.from_numpy(a).pin_memory() for a in (sv.t, sv.y, sv.dy)]
+    oh = [torch.empty(tot, dtype=torch.float64).pin_memory() for _ in range(4)]
+    fh = torch.empty(tot, dtype=torch.uint8).pin_memory()
+
+    def call_host():
+        ftp.ftp_batch(plan, sv.obs_off, *th, grids, out_off[:-1], bank, sv.tpl_of_curve, *oh, fh)
+
+    call_host()
+    e2e_steps = min(3, args.steps)
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        call_host()
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0, dev)
+    e2e = {"value": round(sum_over_ranks(pg, float(e2e_steps * tot), dev) / e2e_s, 1),
+           "unit": UNIT, "h2d_bytes_per_step": int(3 * sv.t.size * 8),
+           "d2h_bytes_per_step": int(tot * 33), "steps": e2e_steps}
+    cfg = {"workload": SURVEY.format(n=sv.ncurves), "curves": sv.ncurves,
+           "n_obs_total": int(sv.t.size), "evals_per_step": tot, "templates_per_curve": 1,
+           "l2": "flushed between steps (512 MiB write); sum tiles exceed L2",
+           "graph": {0: "eager", 1: "captured", 2: "replayed"}[info["graph"]],
+           "chunks": info["chunks"], "parallelism": "single GPU"}
+    result = _result(args, world, value, step_ms, cfg,
+                     fp64_path=fp64_path,
+                     stage_ms={"sums": round(st[0], 3), "roots": round(st[4], 3),
+                               "resolve": round(st[5], 3)},
+                     first_call_s=round(first_s, 3),
+                     solver={"mean_iterations": round(ibar, 3),
+                             "nonconverged": stats["nonconverged"],
+                             "resolved_in_fp64": stats["resolved"]},
+                     roofline=roofline, e2e=e2e, clocks=clocks,
+                     gpu_launches=args.steps * launches)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        rng = np.random.default_rng(11)
+        jobs, picks = [], []
+        for c in rng.choice(sv.ncurves, 2 * cores, replace=False):
+            lc, g, tp = sv.curve(c), sv.grids[c], sv.bank[sv.tpl_of_curve[c]]
+            k = np.sort(rng.choice(g.nf, 4, replace=False))
+            jobs.append((lc.t, lc.y, lc.dy, g.freqs()[k], tp.c, tp.s))
+            picks.append(out_off[c] + k)
+        sec, parts = oracle_jobs(jobs, cores)
+        gp = outs[0].cpu().numpy()
+        err = max(float(np.max(np.abs(gp[pk] - pw))) for pk, pw in zip(picks, parts))
+        n = sum(len(pk) for pk in picks)
+        result["cpu_baseline"] = {
+            "value": round(n / sec, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"4 random frequencies of each of {len(jobs)} random curves "
+                      f"({sec:.1f} s wall on {cores} single-threaded processes)",
+            "max_abs_dP_mixed_vs_oracle": err}
+    ftp.ftp_destroy(plan)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def run_bank(args, world, rank, local, pg):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_2101_12348_gb300 import ftp
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lc, bank_t, grid = synth.bank_curve()
+    bank = [(b.c, b.s) for b in bank_t]
+    H, ntpl, nf = bank_t[0].H, len(bank), grid.nf
+    D = 6 * H - 2
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    dt_, dy_, ds_ = (torch.from_numpy(a).to(dev) for a in (lc.t, lc.y, lc.dy))
+    outs = [torch.empty(ntpl * nf, dtype=torch.float64, device=dev) for _ in range(4)]
+    fl = torch.empty(ntpl * nf, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    plan = ftp.ftp_plan(lc.t.size, H, (grid.df, grid.k0, nf), ntpl, "mixed", local, sh)
+
+    def call():
+        ftp.ftp_periodogram(plan, dt_, dy_, ds_, lc.t.size, bank, *outs, fl)
+
+    for _ in range(args.warmup):
+        call()
+    barrier(pg)
+    ftp.ftp_set_timing(plan, True)
+    roots, sums = [], []
+
+    def call_t():
+        call()
+
+    with ClockSampler(local) as clk:
+        step_ms = []
+        for _ in range(args.steps):
+            step_ms += _timed_calls(stream, flush, 1, call_t)
+            st = ftp.ftp_stage_times(plan)
+            roots.append(st[4])
+            sums.append(st[0] + st[1] + st[2] + st[3])
+    barrier(pg)
+    ftp.ftp_set_timing(plan, False)
+    clocks = clk.summary()
+    stats = ftp.ftp_solver_stats(plan)
+    launches = ftp.ftp_plan_info(plan)["last_launches"]
+    total_ms = max_over_ranks(pg, sum(step_ms), dev)
+    evals = ntpl * nf
+    value = sum_over_ranks(pg, float(args.steps * evals), dev) / (total_ms / 1e3)
+    ibar = stats["mean_iterations"]
+    achieved = evals * 26.0 * D * D * ibar / (statistics.mean(roots) / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "kernel": "roots_kernel (FP32 Aberth flops 26*D^2*iterations)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    # FP64 path on the first 20000 frequencies (all 32 templates)
+    nf64 = min(20_000, nf)
+    p64 = ftp.ftp_plan(lc.t.size, H, (grid.df, grid.k0, nf64), ntpl, "fp64", local, sh)
+    o64 = [torch.empty(ntpl * nf64, dtype=torch.float64, device=dev) for _ in range(4)]
+
+    def call64():
+        ftp.ftp_periodogram(p64, dt_, dy_, ds_, lc.t.size, bank, *o64, None)
+
+    call64()
+    d_ms = _timed_calls(stream, flush, max(1, args.fp64_steps), call64)
+    pm = outs[0].view(ntpl, nf)[:, :nf64]
+    fp64_path = {"value": round(ntpl * nf64 * len(d_ms) / (sum(d_ms) / 1e3), 1), "unit": UNIT,
+                 "n_freq": nf64, "ms_per_step": round(statistics.mean(d_ms), 3),
+                 "max_abs_dP_mixed_vs_fp64":
+                     float(torch.max(torch.abs(pm - o64[0].view(ntpl, nf64))).item())}
+    ftp.ftp_destroy(p64)
+    th = [torch.from_numpy(a).pin_memory() for a in (lc.t, lc.y, lc.dy)]
+    oh = [torch.empty(ntpl * nf, dtype=torch.float64).pin_memory() for _ in range(4)]
+    fh = torch.empty(ntpl * nf, dtype=torch.uint8).pin_memory()
+    ftp.ftp_periodogram(plan, *th, lc.t.size, bank, *oh, fh)
+    e2e_steps = min(3, args.steps)
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ftp.ftp_periodogram(plan, *th, lc.t.size, bank, *oh, fh)
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0, dev)
+    e2e = {"value": round(sum_over_ranks(pg, float(e2e_steps * evals), dev) / e2e_s, 1),
+           "unit": UNIT, "h2d_bytes_per_step": int(3 * lc.t.size * 8),
+           "d2h_bytes_per_step": int(evals * 33), "steps": e2e_steps}
+    cfg = {"workload": BANK, "n_obs": int(lc.t.size), "H": H, "templates": ntpl, "n_freq": nf,
+           "l2": "flushed between steps (512 MiB write); sum tiles exceed L2",
+           "parallelism": "single GPU"}
+    result = _result(args, world, value, step_ms, cfg, fp64_path=fp64_path,
+                     stage_ms={"sums": round(statistics.mean(sums), 3),
+                               "roots": round(statistics.mean(roots), 3)},
+                     solver={"mean_iterations": round(ibar, 3),
+                             "nonconverged": stats["nonconverged"],
+                             "resolved_in_fp64": stats["resolved"]},
+                     roofline=roofline, e2e=e2e, clocks=clocks,
+                     gpu_launches=args.steps * launches)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        rng = np.random.default_rng(12)
+        jobs, picks = [], []
+        for i in rng.choice(ntpl, min(ntpl, cores), replace=False):
+            k = np.sort(rng.choice(nf, 2, replace=False))
+            jobs.append((lc.t, lc.y, lc.dy, grid.freqs()[k], bank_t[i].c, bank_t[i].s))
+            picks.append(i * nf + k)
+        sec, parts = oracle_jobs(jobs, cores)
+        gp = outs[0].cpu().numpy()
+        err = max(float(np.max(np.abs(gp[pk] - pw))) for pk, pw in zip(picks, parts))
+        n = sum(len(pk) for pk in picks)
+        result["cpu_baseline"] = {
+            "value": round(n / sec, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"2 random frequencies for each of {len(jobs)} templates "
+                      f"({sec:.1f} s wall on {cores} single-threaded processes)",
+            "max_abs_dP_mixed_vs_oracle": err}
+    ftp.ftp_destroy(plan)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, world, rank, local, pg):
     """The FP64 CPU oracle on the host cores, on the same workload and metric:
@@ -396,6 +699,10 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank, local, pg)
+        elif args.workload == "survey":
+            run_survey(args, world, rank, local, pg)
+        elif args.workload == "bank":
+            run_bank(args, world, rank, local, pg)
         else:
             run_ours(args, world, rank, local, pg)
     finally:

@@ -80,6 +80,8 @@ typedef enum {
 #define FTP_FLAG_DEGENERATE_MM 2u /* MM ~ 0 at the chosen phase: P set to 0 */
 #define FTP_FLAG_CONSTANT_P 4u    /* final polynomial ~ 0: P independent of theta2 */
 #define FTP_FLAG_NEGATIVE_AMP 8u  /* best theta1 < 0 (Section 2.1: allowed, reported) */
+#define FTP_FLAG_UNRESOLVED 16u   /* ill-conditioned but not re-solved: the batch's
+                                     re-solve list was full (ftp_batch only) */
 
 #define FTP_MAX_H 16
 
@@ -145,14 +147,39 @@ ftp_status ftp_periodogram(ftp_plan_t plan, const double* t, const double* y, co
  * (template-major).  tpl_of_curve[c] selects one template of `bank` for curve
  * c; NULL runs every template of the bank on every curve.  obs_off, grids,
  * out_off, tpl_of_curve and bank are host arrays; t, y, dy and the outputs
- * may be host or device.  Curves are processed in order through the plan's
- * workspace; a failing curve stops the batch and its status is returned.
+ * may be host or device.
+ *
+ * Execution: the curves are cut into chunks whose sum tiles fit the plan's
+ * chunk budget (ftp_set_batch_options; 8 GiB by default).  Per chunk, step
+ * (a) runs curve by curve into the chunk's sum tiles, then steps (b)-(c) run
+ * as one persistent kernel launch per harmonic count H over every
+ * (frequency, template) item of every curve of the chunk, and the chunk's
+ * ill-conditioned frequencies are re-solved from direct FP64 sums in one more
+ * launch per H (at most 2^18 per chunk; beyond that they keep their result
+ * and get FTP_FLAG_UNRESOLVED).  When every array is device memory and a call
+ * repeats the previous one exactly (same pointers, offsets, grids and
+ * templates), the second call captures the device work into a CUDA graph and
+ * later calls replay it.  The plan's batch workspace (sum tiles of one chunk,
+ * staging for host arrays) is allocated on first use and kept.  A
+ * device-side error (e.g. zero variance of one curve) stops the batch and is
+ * returned.
  */
 ftp_status ftp_batch(ftp_plan_t plan, int64_t ncurves, const int64_t* obs_off, const double* t,
                      const double* y, const double* dy, const ftp_grid* grids,
                      const int64_t* out_off, const ftp_template* bank, int nbank,
                      const int32_t* tpl_of_curve, double* power, double* theta1,
                      double* theta2, double* theta3, uint8_t* flags);
+
+/*
+ * ftp_set_batch_options - chunk budget of ftp_batch in bytes of sum tiles
+ * (0 keeps the current value) and whether repeated all-device calls may be
+ * captured into and replayed from a CUDA graph (default 1).
+ * ftp_batch_info - of the last ftp_batch call: the number of chunks and how
+ * its device work ran (0 eagerly, 1 captured into a graph and launched,
+ * 2 replayed from the graph).  Each pointer is nullable.
+ */
+ftp_status ftp_set_batch_options(ftp_plan_t plan, int64_t chunk_bytes, int use_graph);
+ftp_status ftp_batch_info(ftp_plan_t plan, int64_t* chunks, int* graph);
 
 /* Release the plan's device memory, cuFFT plan and owned stream.  NULL is a no-op. */
 void ftp_destroy(ftp_plan_t plan);
@@ -189,6 +216,9 @@ ftp_status ftp_solver_stats(ftp_plan_t plan, int64_t* items, double* mean_iterat
  * reduction and binning, [1] spreading, [2] FFT, [3] deconvolution + gather,
  * [4] assembly + roots + candidates + polish (all template groups),
  * [5] re-solve of ill-conditioned frequencies from direct FP64 sums.
+ * After ftp_batch (timed calls run eagerly, without a graph): [0] all of
+ * step (a) for every curve, [1]-[3] zero, [4] and [5] as above, summed over
+ * the chunks.
  */
 ftp_status ftp_set_timing(ftp_plan_t plan, int enable);
 ftp_status ftp_stage_times(ftp_plan_t plan, float* ms6);

@@ -18,6 +18,17 @@ int launch_roots_mixed(const RootsArgs& a, int num_sms, cudaStream_t s);
 int launch_roots_fp64(const RootsArgs& a, int num_sms, cudaStream_t s);
 int launch_roots_redo(const RootsArgs& a, int num_sms, cudaStream_t s);
 
+int roots_lanes_mixed(int H);
+int roots_lanes_fp64(int H);
+int roots_lanes_redo(int H);
+
+int roots_items_per_unit(RootsKind kind, int H) {
+  const int g = kind == ROOTS_MIXED ? roots_lanes_mixed(H)
+                : kind == ROOTS_FP64 ? roots_lanes_fp64(H)
+                                     : roots_lanes_redo(H);
+  return g > 0 ? 32 / g : 0;
+}
+
 int launch_roots(RootsKind kind, const RootsArgs& a, int num_sms, cudaStream_t s) {
   switch (kind) {
     case ROOTS_MIXED: return launch_roots_mixed(a, num_sms, s);
@@ -100,6 +111,38 @@ struct ftp_plan_s {
   float stage_ms[6] = {};
   int maxit = 60;
   int polish_steps = 1;
+  // ---- batch workspace (grown on demand by ftp_batch; never shrinks)
+  bool in_batch = false;
+  size_t chunk_bytes = (size_t)8 << 30;  // sum tiles of one chunk of curves
+  bool use_graph = true;
+  void* d_bsums = nullptr;
+  size_t bsums_cap = 0;
+  double* d_bmom = nullptr;
+  size_t bmom_cap = 0;
+  double* d_bobs = nullptr;  // staged host observations [3][count]
+  size_t bobs_cap = 0;
+  double* d_bout = nullptr;  // staged host outputs [4][extent]
+  size_t bout_cap = 0;
+  uint8_t* d_bflags = nullptr;
+  size_t bflags_cap = 0;
+  int* d_bmark = nullptr;  // re-solve marks, one per frequency of a chunk
+  size_t bmark_cap = 0;
+  int* d_blist = nullptr;  // re-solve list [kBatchRedoCap]
+  int* d_bslot_curve = nullptr;
+  int* d_bcount = nullptr;
+  double2* d_bredo_sums = nullptr;  // [3 max_H][kBatchRedoStride]
+  unsigned char* d_bdesc = nullptr;  // segment / unit / curve descriptors
+  size_t bdesc_cap = 0;
+  unsigned char* h_bdesc = nullptr;  // pinned twin of d_bdesc
+  size_t hbdesc_cap = 0;
+  std::vector<cudaEvent_t> bev;      // batch stage events (timing only)
+  int64_t last_chunks = 0;
+  int last_graph = 0;                // 0 eager, 1 captured + launched, 2 replayed
+  // the captured graph of the last repeated all-device batch call
+  uint64_t graph_key = 0;
+  uint64_t eager_key = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_launches = 0;
 };
 
 namespace {
@@ -191,29 +234,29 @@ ftp_status get_fft(ftp_plan_t P, int64_t n, cufftHandle* out) {
 }
 
 void ev_rec(ftp_plan_t P, int i) {
-  if (P->timing) cudaEventRecord(P->ev[i], P->stream);
+  if (P->timing && !P->in_batch) cudaEventRecord(P->ev[i], P->stream);
 }
 
 // Step (a) for one curve: moments, binning, spreading, FFT, gather into the
-// plan's sum tiles (layout [3 Hs][nf_pad]).  t, y, dy are device pointers.
+// sum tiles `sums` (layout [3 Hs][nf_pad]) and the moments block `moments`.
+// t, y, dy are device pointers; ngrid/ntiles give the NFFT grid (at most the
+// plan's).
 ftp_status run_sums(ftp_plan_t P, const double* t, const double* y, const double* dy,
-                    int64_t nobs, double df, int64_t k0, int64_t nf, int Hs, int* launches) {
-  const int64_t J = 2 * (int64_t)Hs * (k0 + nf - 1);
-  int64_t ntiles = 0;
-  const int64_t ngrid = grid_len(J, P->sigma, &ntiles);
-  if (ngrid > P->ngrid) return FTP_ERR_UNSUPPORTED;
+                    int64_t nobs, double df, int64_t k0, int64_t nf, int Hs, int64_t ngrid,
+                    int64_t ntiles, double* moments, void* sums, int64_t nf_pad, int* launches) {
+  if (ngrid > P->ngrid || ntiles > P->ntiles) return FTP_ERR_UNSUPPORTED;
   cufftHandle fft;
   ftp_status st = get_fft(P, ngrid, &fft);
   if (st != FTP_OK) return st;
   cudaStream_t s = P->stream;
   ev_rec(P, 0);
   FTP_CK(cudaMemsetAsync(P->d_tile_count, 0, sizeof(int) * ntiles, s));
-  launch_moments(t, y, dy, nobs, P->d_moments, P->d_status, P->d_mom_scratch, s);
+  launch_moments(t, y, dy, nobs, moments, P->d_status, P->d_mom_scratch, s);
   if (P->mixed) {
-    launch_points<float>(t, y, dy, nobs, P->d_moments, P->d_status, df, ngrid, P->d_tile_count,
+    launch_points<float>(t, y, dy, nobs, moments, P->d_status, df, ngrid, P->d_tile_count,
                          P->d_cell, (float*)P->d_frac, (float2*)P->d_coef, s);
   } else {
-    launch_points<double>(t, y, dy, nobs, P->d_moments, P->d_status, df, ngrid, P->d_tile_count,
+    launch_points<double>(t, y, dy, nobs, moments, P->d_status, df, ngrid, P->d_tile_count,
                           P->d_cell, (double*)P->d_frac, (double2*)P->d_coef, s);
   }
   launch_scan(P->d_tile_count, ntiles, P->d_tile_off, P->d_cursor, P->d_status, s);
@@ -247,16 +290,26 @@ ftp_status run_sums(ftp_plan_t P, const double* t, const double* y, const double
   if (fr != CUFFT_SUCCESS) return FTP_ERR_CUDA;
   ev_rec(P, 3);
   if (P->mixed) {
-    launch_gather<float>((const float2*)P->d_grid, ngrid, k0, nf, P->nf_pad, Hs, P->m, P->beta,
-                         (float2*)P->d_sums, P->d_status, s);
+    launch_gather<float>((const float2*)P->d_grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
+                         (float2*)sums, P->d_status, s);
   } else {
-    launch_gather<double>((const double2*)P->d_grid, ngrid, k0, nf, P->nf_pad, Hs, P->m,
-                          P->beta, (double2*)P->d_sums, P->d_status, s);
+    launch_gather<double>((const double2*)P->d_grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
+                          (double2*)sums, P->d_status, s);
   }
   ev_rec(P, 4);
   *launches += 7;
   FTP_CK(cudaGetLastError());
   return FTP_OK;
+}
+
+// Step (a) on the plan's own grid into the plan's sum tiles and moments.
+ftp_status run_sums_plan(ftp_plan_t P, const double* t, const double* y, const double* dy,
+                         int64_t nobs, int Hs, int* launches) {
+  const int64_t J = 2 * (int64_t)Hs * (P->grid.k0 + P->grid.nf - 1);
+  int64_t ntiles = 0;
+  const int64_t ngrid = grid_len(J, P->sigma, &ntiles);
+  return run_sums(P, t, y, dy, nobs, P->grid.df, P->grid.k0, P->grid.nf, Hs, ngrid, ntiles,
+                  P->d_moments, P->d_sums, P->nf_pad, launches);
 }
 
 ftp_status check_obs(ftp_plan_t P, const double* t, const double* y, const double* dy,
@@ -393,6 +446,7 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
     a.redo_mark = P->d_redo_mark;
     a.redo_count = P->d_redo_count;
     a.redo_cap = (int)P->grid.nf;
+    a.redo_marks = P->grid.nf;
     a.sum_err = P->mixed ? kSumErrF32 : kSumErrF64;
     a.redo_tol = P->mixed ? kRedoTolF32 : kRedoTolF64;
   }
@@ -449,6 +503,561 @@ ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double
 
 }  // namespace
 
+namespace {
+
+// ------------------------------------------------------------------ batches
+// ftp_batch runs many lightcurves through one pipeline:
+//   - curves are cut into chunks whose sum tiles fit the chunk budget;
+//   - step (a) runs per curve (moments .. gather, cuFFT at one of a few grid
+//     size classes) into the curve's slice of the chunk's sum tiles;
+//   - steps (b)-(c) run as ONE persistent roots launch per harmonic count H
+//     over every (frequency, template) item of every curve in the chunk: the
+//     warps' work queue walks a segment table (one segment per curve);
+//   - ill-conditioned frequencies of the whole chunk go through one batched
+//     direct-sums launch and one re-solve launch per H;
+//   - when every array is on the device and a call repeats the previous one
+//     (same pointers, sizes and templates), the device work of the call is
+//     captured once into a CUDA graph and replayed afterwards.
+constexpr int kBatchRedoCap = 1 << 18;                    // re-solve slots per chunk
+constexpr int64_t kBatchRedoStride = kBatchRedoCap + 64;  // row stride of their sums
+
+// Grid length for a batched curve: at least 2 sigma J cells, rounded up to
+// 2048 * q with q <= 8 or q in {4, 5, 6, 7} * 2^e, so that a batch of curves
+// needs only a few cuFFT plans (at most 25 % extra cells).
+int64_t grid_len_class(int64_t J, double sigma, int64_t* ntiles) {
+  const double nmin = std::max(2.0 * sigma * (double)J, 2.0 * (double)J + 2.0);
+  const int64_t need = (int64_t)ceil(nmin / (double)kSpreadTile);
+  int64_t nt = need;
+  if (need > 8) {
+    bool found = false;
+    for (int64_t p2 = 2; !found; p2 *= 2)
+      for (int m : {4, 5, 6, 7})
+        if (!found && m * p2 >= need) {
+          nt = m * p2;
+          found = true;
+        }
+  }
+  *ntiles = nt;
+  return nt * kSpreadTile;
+}
+
+// Grow-only device buffer; dropping the old one waits for queued work.
+template <typename T>
+ftp_status grow_dev(T** p, size_t* cap, size_t count, bool* grew) {
+  if (count == 0) count = 1;
+  if (*p && *cap >= count) return FTP_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  *grew = true;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return FTP_ERR_OOM;
+  }
+  *cap = count;
+  return FTP_OK;
+}
+
+struct BCurve {
+  const double* t;  // device
+  const double* y;
+  const double* dy;
+  int64_t n, nf, nf_pad, ngrid, ntiles, k0;
+  int64_t sums_off;   // elements, within the chunk
+  int64_t redo_base;  // within the chunk
+  int64_t out_off;
+  double df;
+  int Hc, ntc, tpl;
+};
+struct BLaunch {
+  int H, ntpl, Hs;
+  int64_t seg_first, units_first, cseg_first, units;
+  int nseg;
+};
+struct BChunk {
+  int64_t c0, c1, sums_elems, nf_total;
+  int Hs;
+  std::vector<BLaunch> launches;
+};
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
+                                const std::vector<BChunk>& chunks, const RootsSeg* d_segs,
+                                const int64_t* d_units, const CurveDesc* d_curves,
+                                const int* d_cseg, double* const* o, uint8_t* of,
+                                int64_t extent, int* launches) {
+  cudaStream_t s = P->stream;
+  const RootsKind kind = P->mixed ? ROOTS_MIXED : ROOTS_FP64;
+  const RootsKind rkind = P->mixed ? ROOTS_REDO : ROOTS_FP64;
+  const bool tm = P->timing;
+  for (size_t q = 0; q < chunks.size(); ++q) {
+    const BChunk& ch = chunks[q];
+    if (tm) cudaEventRecord(P->bev[4 * q + 0], s);
+    for (int64_t c = ch.c0; c < ch.c1; ++c) {
+      const BCurve& b = cv[(size_t)c];
+      ftp_status st = run_sums(P, b.t, b.y, b.dy, b.n, b.df, b.k0, b.nf, b.Hc, b.ngrid, b.ntiles,
+                               P->d_bmom + (size_t)(c - ch.c0) * MO_WORDS,
+                               (unsigned char*)P->d_bsums + (size_t)b.sums_off * P->csz,
+                               b.nf_pad, launches);
+      if (st != FTP_OK) return st;
+    }
+    if (tm) cudaEventRecord(P->bev[4 * q + 1], s);
+    FTP_CK(cudaMemsetAsync(P->d_bmark, 0, sizeof(int) * (size_t)ch.nf_total, s));
+    FTP_CK(cudaMemsetAsync(P->d_bcount, 0, sizeof(int), s));
+    for (const BLaunch& L : ch.launches) {
+      RootsArgs a{};
+      a.sums = P->d_bsums;
+      a.sums_elems = ch.sums_elems;
+      a.out_elems = extent;
+      a.Hs = L.Hs;
+      a.H = L.H;
+      a.ntpl = L.ntpl;
+      a.alpha = P->d_alpha;
+      a.rows = P->d_rows;
+      a.moments = P->d_bmom;
+      a.power = o[0];
+      a.theta1 = o[1];
+      a.theta2 = o[2];
+      a.theta3 = o[3];
+      a.flags = of;
+      a.status = P->d_status;
+      a.counters = P->d_counters;
+      a.queue = P->d_queue;
+      a.redo_list = P->d_blist;
+      a.redo_mark = P->d_bmark;
+      a.redo_count = P->d_bcount;
+      a.redo_cap = kBatchRedoCap;
+      a.redo_marks = ch.nf_total;
+      a.sum_err = P->mixed ? kSumErrF32 : kSumErrF64;
+      a.redo_tol = P->mixed ? kRedoTolF32 : kRedoTolF64;
+      a.maxit = P->maxit;
+      a.polish_steps = P->polish_steps;
+      a.segs = d_segs + L.seg_first;
+      a.seg_units = d_units + L.units_first;
+      a.nseg = L.nseg;
+      a.host_units = L.units;
+      FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), s));
+      const int r = launch_roots(kind, a, P->num_sms, s);
+      if (r == -1) return FTP_ERR_UNSUPPORTED;
+      if (r < 0) return FTP_ERR_CUDA;
+      *launches += r;
+    }
+    if (tm) cudaEventRecord(P->bev[4 * q + 2], s);
+    const int ncc = (int)(ch.c1 - ch.c0);
+    const CurveDesc* dcur = d_curves + ch.c0;
+    launch_direct_sums_batch(dcur, ncc, P->d_bmom, P->d_status, P->d_blist, P->d_bcount,
+                             kBatchRedoCap, kBatchRedoStride, P->d_bredo_sums,
+                             (int64_t)3 * P->max_H * kBatchRedoStride, P->d_bslot_curve,
+                             P->d_status, s);
+    *launches += 1;
+    for (const BLaunch& L : ch.launches) {
+      RootsArgs a{};
+      a.sums = P->d_bredo_sums;
+      a.sums_elems = (int64_t)3 * P->max_H * kBatchRedoStride;
+      a.out_elems = extent;
+      a.nf = kBatchRedoCap;
+      a.nf_dev = P->d_bcount;
+      a.kmap = P->d_blist;
+      a.nf_pad = kBatchRedoStride;
+      a.Hs = ch.Hs;
+      a.H = L.H;
+      a.ntpl = L.ntpl;
+      a.alpha = P->d_alpha;
+      a.rows = P->d_rows;
+      a.moments = P->d_bmom;
+      a.power = o[0];
+      a.theta1 = o[1];
+      a.theta2 = o[2];
+      a.theta3 = o[3];
+      a.flags = of;
+      a.status = P->d_status;
+      a.counters = P->d_counters;
+      a.queue = P->d_queue;
+      a.redo_cap = kBatchRedoCap;
+      a.maxit = P->maxit;
+      a.polish_steps = P->polish_steps;
+      a.segs = d_segs + L.seg_first;
+      a.seg_units = d_units + L.units_first;
+      a.nseg = L.nseg;
+      a.slot_curve = P->d_bslot_curve;
+      a.curve_seg = d_cseg + L.cseg_first;
+      a.ncurves = ncc;
+      a.host_units = (int64_t)kBatchRedoCap * L.ntpl;
+      FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), s));
+      const int r = launch_roots(rkind, a, P->num_sms, s);
+      if (r == -1) return FTP_ERR_UNSUPPORTED;
+      if (r < 0) return FTP_ERR_CUDA;
+      *launches += r;
+    }
+    if (of) {
+      launch_redo_overflow(dcur, ncc, P->d_bmark, ch.nf_total, P->d_bcount, kBatchRedoCap, of, s);
+      *launches += 1;
+    }
+    if (tm) cudaEventRecord(P->bev[4 * q + 3], s);
+    FTP_CK(cudaGetLastError());
+  }
+  return FTP_OK;
+}
+
+ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, const double* t,
+                     const double* y, const double* dy, const ftp_grid* grids,
+                     const int64_t* out_off, const ftp_template* bank, int nbank,
+                     const int32_t* tpl_of_curve, double* power, double* theta1, double* theta2,
+                     double* theta3, uint8_t* flags) {
+  if (!P || ncurves < 0 || !obs_off || !t || !y || !dy || !grids || !out_off || !power ||
+      !theta1 || !theta2 || !theta3)
+    return FTP_ERR_INVALID_ARG;
+  if (ncurves == 0) return FTP_OK;
+  if (ncurves > (int64_t)1 << 30) return FTP_ERR_UNSUPPORTED;
+  ftp_status st = check_templates(P, bank, nbank);
+  if (st != FTP_OK) return st;
+  int Hs = 0;
+  for (int i = 0; i < nbank; ++i) Hs = std::max(Hs, bank[i].H);
+  // ---- validate every curve on the host before any work is queued
+  int64_t o_lo = obs_off[0], o_hi = obs_off[0], extent = 0;
+  for (int64_t c = 0; c < ncurves; ++c) {
+    const int64_t n = obs_off[c + 1] - obs_off[c];
+    if (obs_off[c] < 0 || n < 2) return FTP_ERR_INVALID_ARG;
+    if (n > P->max_nobs) return FTP_ERR_UNSUPPORTED;
+    const ftp_grid& g = grids[c];
+    if (!(g.df > 0.0) || !isfinite(g.df) || g.k0 < 1 || g.nf < 1 || out_off[c] < 0)
+      return FTP_ERR_INVALID_ARG;
+    if (g.nf > P->grid.nf) return FTP_ERR_UNSUPPORTED;
+    if (tpl_of_curve && (tpl_of_curve[c] < 0 || tpl_of_curve[c] >= nbank))
+      return FTP_ERR_INVALID_ARG;
+    const int H = tpl_of_curve ? bank[tpl_of_curve[c]].H : Hs;
+    int64_t nt = 0;
+    if (grid_len(2 * (int64_t)H * (g.k0 + g.nf - 1), P->sigma, &nt) > P->ngrid)
+      return FTP_ERR_UNSUPPORTED;
+    o_lo = std::min(o_lo, obs_off[c]);
+    o_hi = std::max(o_hi, obs_off[c + 1]);
+    extent = std::max(extent, out_off[c] + (tpl_of_curve ? 1 : nbank) * g.nf);
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->device);
+  struct Restore {
+    int d;
+    ~Restore() { cudaSetDevice(d); }
+  } restore{prev};
+  const bool in_dev = is_device_ptr(t) && is_device_ptr(y) && is_device_ptr(dy);
+  const bool out_dev = is_device_ptr(power) && is_device_ptr(theta1) && is_device_ptr(theta2) &&
+                       is_device_ptr(theta3) && (!flags || is_device_ptr(flags));
+
+  // ---- per-curve layout and chunks
+  bool grew = false;
+  const int64_t nobs_all = o_hi - o_lo;
+  if (!in_dev) {
+    st = grow_dev(&P->d_bobs, &P->bobs_cap, (size_t)3 * nobs_all, &grew);
+    if (st != FTP_OK) return st;
+  }
+  std::vector<BCurve> cv((size_t)ncurves);
+  std::vector<BChunk> chunks;
+  {
+    BChunk cur{0, 0, 0, 0, 0, {}};
+    for (int64_t c = 0; c < ncurves; ++c) {
+      BCurve& b = cv[(size_t)c];
+      const ftp_grid& g = grids[c];
+      const int64_t rel = obs_off[c] - o_lo;  // position in the staged copy
+      b.t = in_dev ? t + obs_off[c] : P->d_bobs + rel;
+      b.y = in_dev ? y + obs_off[c] : P->d_bobs + nobs_all + rel;
+      b.dy = in_dev ? dy + obs_off[c] : P->d_bobs + 2 * nobs_all + rel;
+      b.n = obs_off[c + 1] - obs_off[c];
+      b.nf = g.nf;
+      b.k0 = g.k0;
+      b.df = g.df;
+      b.nf_pad = (g.nf + 63) / 64 * 64;
+      b.tpl = tpl_of_curve ? tpl_of_curve[c] : -1;
+      b.Hc = tpl_of_curve ? bank[b.tpl].H : Hs;
+      b.ntc = tpl_of_curve ? 1 : nbank;
+      b.out_off = out_off[c];
+      const int64_t J = 2 * (int64_t)b.Hc * (g.k0 + g.nf - 1);
+      b.ngrid = grid_len_class(J, P->sigma, &b.ntiles);
+      if (b.ngrid > P->ngrid) b.ngrid = grid_len(J, P->sigma, &b.ntiles);
+      const int64_t elems = 3 * (int64_t)b.Hc * b.nf_pad;
+      const bool full = cur.c1 > cur.c0 &&
+                        ((size_t)(cur.sums_elems + elems) * P->csz > P->chunk_bytes ||
+                         cur.nf_total + b.nf > ((int64_t)1 << 30));
+      if (full) {
+        chunks.push_back(cur);
+        cur = BChunk{c, c, 0, 0, 0, {}};
+      }
+      b.sums_off = cur.sums_elems;
+      b.redo_base = cur.nf_total;
+      cur.sums_elems += elems;
+      cur.nf_total += b.nf;
+      cur.Hs = std::max(cur.Hs, b.Hc);
+      cur.c1 = c + 1;
+    }
+    chunks.push_back(cur);
+  }
+
+  // ---- templates (grouped by H) and the segment tables of every chunk
+  std::vector<HGroup> groups;
+  std::vector<int> pos_of;
+  FTP_CK(reset_call(P));
+  st = upload_templates(P, bank, nbank, &groups, &pos_of);
+  if (st != FTP_OK) return st;
+  const RootsKind kind = P->mixed ? ROOTS_MIXED : ROOTS_FP64;
+  std::vector<RootsSeg> segs;
+  std::vector<int64_t> units;
+  std::vector<int> cseg;
+  size_t max_chunk_curves = 0;
+  int64_t max_sums_elems = 0, max_nf_total = 0;
+  for (BChunk& ch : chunks) {
+    const int64_t ncc = ch.c1 - ch.c0;
+    max_chunk_curves = std::max(max_chunk_curves, (size_t)ncc);
+    max_sums_elems = std::max(max_sums_elems, ch.sums_elems);
+    max_nf_total = std::max(max_nf_total, ch.nf_total);
+    // (H, first, count) of each launch: one per template group (whole bank),
+    // or one per distinct H of the chunk's curves (one template per curve)
+    std::vector<HGroup> lg;
+    if (tpl_of_curve) {
+      std::vector<int> hs;
+      for (int64_t c = ch.c0; c < ch.c1; ++c) hs.push_back(cv[(size_t)c].Hc);
+      std::sort(hs.begin(), hs.end());
+      hs.erase(std::unique(hs.begin(), hs.end()), hs.end());
+      for (int h : hs) lg.push_back({h, 0, 1});
+    } else {
+      lg = groups;
+    }
+    for (const HGroup& g : lg) {
+      const int ngw = roots_items_per_unit(kind, g.H);
+      if (ngw <= 0) return FTP_ERR_UNSUPPORTED;
+      BLaunch L{};
+      L.H = g.H;
+      L.ntpl = g.count;
+      L.Hs = ch.Hs;
+      L.seg_first = (int64_t)segs.size();
+      L.units_first = (int64_t)units.size();
+      L.cseg_first = (int64_t)cseg.size();
+      int64_t acc = 0;
+      for (int64_t c = ch.c0; c < ch.c1; ++c) {
+        const BCurve& b = cv[(size_t)c];
+        if (tpl_of_curve && b.Hc != g.H) {
+          cseg.push_back(-1);
+          continue;
+        }
+        RootsSeg sg{};
+        sg.sums_off = b.sums_off;
+        sg.nf_pad = b.nf_pad;
+        sg.nf = b.nf;
+        sg.out_off = b.out_off;
+        sg.redo_base = b.redo_base;
+        sg.Hs = b.Hc;
+        sg.curve = (int32_t)(c - ch.c0);
+        sg.tpl_first = tpl_of_curve ? pos_of[b.tpl] : g.first;
+        sg.ntpl = tpl_of_curve ? 1 : g.count;
+        sg.row_first = tpl_of_curve ? -1 : g.first;
+        cseg.push_back((int)(segs.size() - L.seg_first));
+        segs.push_back(sg);
+        units.push_back(acc);
+        acc += (b.nf + ngw - 1) / ngw * sg.ntpl;
+      }
+      units.push_back(acc);
+      L.nseg = (int)(segs.size() - L.seg_first);
+      L.units = acc;
+      ch.launches.push_back(L);
+    }
+  }
+  std::vector<CurveDesc> curves((size_t)ncurves);
+  for (int64_t c = 0; c < ncurves; ++c) {
+    const BCurve& b = cv[(size_t)c];
+    curves[(size_t)c] = CurveDesc{b.t, b.y, b.dy, b.n, b.df, b.k0, b.redo_base, b.nf,
+                                  b.out_off, b.Hc, b.ntc};
+  }
+  // one descriptor blob: segs | units | curves | curve -> segment maps
+  auto al64 = [](size_t x) { return (x + 63) / 64 * 64; };
+  const size_t off_units = al64(segs.size() * sizeof(RootsSeg));
+  const size_t off_curves = off_units + al64(units.size() * sizeof(int64_t));
+  const size_t off_cseg = off_curves + al64(curves.size() * sizeof(CurveDesc));
+  const size_t blob = off_cseg + al64(cseg.size() * sizeof(int));
+
+  // ---- workspace (growing it drops a captured graph)
+  st = grow_dev(reinterpret_cast<unsigned char**>(&P->d_bsums), &P->bsums_cap,
+                (size_t)max_sums_elems * P->csz, &grew);
+  if (st == FTP_OK) st = grow_dev(&P->d_bmom, &P->bmom_cap, max_chunk_curves * MO_WORDS, &grew);
+  if (st == FTP_OK) st = grow_dev(&P->d_bmark, &P->bmark_cap, (size_t)max_nf_total, &grew);
+  if (st == FTP_OK) st = grow_dev(&P->d_bdesc, &P->bdesc_cap, blob, &grew);
+  if (st == FTP_OK && !P->d_blist) {
+    grew = true;
+    if (dalloc(&P->d_blist, kBatchRedoCap) != FTP_OK ||
+        dalloc(&P->d_bslot_curve, kBatchRedoCap) != FTP_OK || dalloc(&P->d_bcount, 1) != FTP_OK ||
+        dalloc(&P->d_bredo_sums, (size_t)3 * P->max_H * kBatchRedoStride) != FTP_OK)
+      st = FTP_ERR_OOM;
+  }
+  if (st == FTP_OK && !out_dev) {
+    st = grow_dev(&P->d_bout, &P->bout_cap, (size_t)4 * extent, &grew);
+    if (st == FTP_OK && flags) st = grow_dev(&P->d_bflags, &P->bflags_cap, (size_t)extent, &grew);
+  }
+  if (st != FTP_OK) return st;
+  if (!P->h_bdesc || P->hbdesc_cap < blob) {
+    if (P->h_bdesc) cudaFreeHost(P->h_bdesc);
+    P->h_bdesc = nullptr;
+    P->hbdesc_cap = 0;
+    if (cudaMallocHost(&P->h_bdesc, blob) != cudaSuccess) return FTP_ERR_OOM;
+    P->hbdesc_cap = blob;
+  }
+  memcpy(P->h_bdesc, segs.data(), segs.size() * sizeof(RootsSeg));
+  memcpy(P->h_bdesc + off_units, units.data(), units.size() * sizeof(int64_t));
+  memcpy(P->h_bdesc + off_curves, curves.data(), curves.size() * sizeof(CurveDesc));
+  memcpy(P->h_bdesc + off_cseg, cseg.data(), cseg.size() * sizeof(int));
+  // every FFT size first: making a plan may resize (and so synchronise) the work area
+  for (const BCurve& b : cv) {
+    cufftHandle h;
+    st = get_fft(P, b.ngrid, &h);
+    if (st != FTP_OK) return st;
+  }
+  if (P->timing) {
+    while (P->bev.size() < 4 * chunks.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return FTP_ERR_CUDA;
+      P->bev.push_back(e);
+    }
+  }
+  if (grew && P->graph_exec) {
+    cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
+    P->graph_key = 0;
+  }
+
+  // ---- eager uploads: descriptors (and host observations)
+  cudaStream_t s = P->stream;
+  FTP_CK(cudaMemcpyAsync(P->d_bdesc, P->h_bdesc, blob, cudaMemcpyHostToDevice, s));
+  if (!in_dev) {
+    FTP_CK(cudaMemcpyAsync(P->d_bobs, t + o_lo, sizeof(double) * nobs_all, cudaMemcpyHostToDevice, s));
+    FTP_CK(cudaMemcpyAsync(P->d_bobs + nobs_all, y + o_lo, sizeof(double) * nobs_all,
+                           cudaMemcpyHostToDevice, s));
+    FTP_CK(cudaMemcpyAsync(P->d_bobs + 2 * nobs_all, dy + o_lo, sizeof(double) * nobs_all,
+                           cudaMemcpyHostToDevice, s));
+  }
+  const RootsSeg* d_segs = reinterpret_cast<const RootsSeg*>(P->d_bdesc);
+  const int64_t* d_units = reinterpret_cast<const int64_t*>(P->d_bdesc + off_units);
+  const CurveDesc* d_curves = reinterpret_cast<const CurveDesc*>(P->d_bdesc + off_curves);
+  const int* d_cseg = reinterpret_cast<const int*>(P->d_bdesc + off_cseg);
+  double* o[4] = {power, theta1, theta2, theta3};
+  uint8_t* of = flags;
+  if (!out_dev) {
+    for (int i = 0; i < 4; ++i) o[i] = P->d_bout + (size_t)i * extent;
+    of = flags ? P->d_bflags : nullptr;
+  }
+
+  // ---- the device work: eager, captured, or a replay of the captured graph
+  P->in_batch = true;
+  struct EndBatch {
+    ftp_plan_t p;
+    ~EndBatch() { p->in_batch = false; }
+  } end_batch{P};
+  int launches = 0;
+  const bool graphable = P->use_graph && !P->timing && in_dev && out_dev;
+  uint64_t key = 0;
+  if (graphable) {
+    key = 1469598103934665603ull;
+    const void* ptrs[] = {t, y, dy, power, theta1, theta2, theta3, flags};
+    key = fnv(key, ptrs, sizeof(ptrs));
+    key = fnv(key, &ncurves, sizeof(ncurves));
+    key = fnv(key, obs_off, sizeof(int64_t) * (size_t)(ncurves + 1));
+    key = fnv(key, grids, sizeof(ftp_grid) * (size_t)ncurves);
+    key = fnv(key, out_off, sizeof(int64_t) * (size_t)ncurves);
+    if (tpl_of_curve) key = fnv(key, tpl_of_curve, sizeof(int32_t) * (size_t)ncurves);
+    key = fnv(key, &nbank, sizeof(nbank));
+    key = fnv(key, P->h_alpha, sizeof(double2) * kMaxH * nbank);
+    key = fnv(key, P->h_rows, sizeof(int) * nbank);
+    key = fnv(key, &P->chunk_bytes, sizeof(P->chunk_bytes));
+    if (key == 0) key = 1;
+  }
+  P->last_graph = 0;
+  if (graphable && P->graph_exec && key == P->graph_key) {
+    FTP_CK(cudaGraphLaunch(P->graph_exec, s));
+    launches = P->graph_launches;
+    P->last_graph = 2;
+  } else if (graphable && key == P->eager_key) {
+    // second identical call: capture the device work once, then launch it
+    cudaGraph_t graph = nullptr;
+    FTP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
+                              &launches);
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (st == FTP_OK && ce == cudaSuccess && graph &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+      if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+      P->graph_exec = exec;
+      P->graph_key = key;
+      P->graph_launches = launches;
+      cudaGraphDestroy(graph);
+      FTP_CK(cudaGraphLaunch(P->graph_exec, s));
+      P->last_graph = 1;
+    } else {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      if (st != FTP_OK) return st;
+      P->eager_key = 0;  // capture failed: stay eager for this call pattern
+      launches = 0;
+      st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
+                                &launches);
+      if (st != FTP_OK) return st;
+    }
+  } else {
+    st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
+                              &launches);
+    if (st != FTP_OK) return st;
+    if (graphable) P->eager_key = key;
+  }
+
+  // ---- host outputs: one copy when the curves' blocks tile [lo, extent)
+  if (!out_dev) {
+    std::vector<std::pair<int64_t, int64_t>> blocks((size_t)ncurves);
+    for (int64_t c = 0; c < ncurves; ++c)
+      blocks[(size_t)c] = {out_off[c], out_off[c] + (int64_t)cv[(size_t)c].ntc * cv[(size_t)c].nf};
+    std::sort(blocks.begin(), blocks.end());
+    bool tiled = true;
+    for (size_t i = 1; i < blocks.size(); ++i) tiled = tiled && blocks[i].first == blocks[i - 1].second;
+    double* dsto[4] = {power, theta1, theta2, theta3};
+    auto copy_range = [&](int64_t a0, int64_t a1) -> cudaError_t {
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(dsto[i] + a0, o[i] + a0, sizeof(double) * (size_t)(a1 - a0),
+                            cudaMemcpyDefault, s);
+      if (e == cudaSuccess && flags)
+        e = cudaMemcpyAsync(flags + a0, of + a0, (size_t)(a1 - a0), cudaMemcpyDefault, s);
+      return e;
+    };
+    if (tiled) {
+      FTP_CK(copy_range(blocks.front().first, blocks.back().second));
+    } else {
+      for (const auto& b : blocks) FTP_CK(copy_range(b.first, b.second));
+    }
+  }
+  P->last_launches = launches;
+  P->last_chunks = (int64_t)chunks.size();
+  st = finish(P);
+  if (P->timing) {
+    for (int i = 0; i < 6; ++i) P->stage_ms[i] = 0.f;
+    for (size_t q = 0; q < chunks.size(); ++q) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, P->bev[4 * q], P->bev[4 * q + 1]) == cudaSuccess)
+        P->stage_ms[0] += ms;
+      if (cudaEventElapsedTime(&ms, P->bev[4 * q + 1], P->bev[4 * q + 2]) == cudaSuccess)
+        P->stage_ms[4] += ms;
+      if (cudaEventElapsedTime(&ms, P->bev[4 * q + 2], P->bev[4 * q + 3]) == cudaSuccess)
+        P->stage_ms[5] += ms;
+    }
+    cudaGetLastError();
+  }
+  return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* ftp_status_string(ftp_status s) {
@@ -480,6 +1089,14 @@ void ftp_destroy(ftp_plan_t P) {
                    P->d_flags, P->d_fftwork};
   for (void* p : dptrs)
     if (p) cudaFree(p);
+  void* bptrs[] = {P->d_bsums, P->d_bmom, P->d_bobs, P->d_bout, P->d_bflags, P->d_bmark,
+                   P->d_blist, P->d_bslot_curve, P->d_bcount, P->d_bredo_sums, P->d_bdesc};
+  for (void* p : bptrs)
+    if (p) cudaFree(p);
+  if (P->h_bdesc) cudaFreeHost(P->h_bdesc);
+  for (auto& e : P->bev)
+    if (e) cudaEventDestroy(e);
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
   if (P->h_status) cudaFreeHost(P->h_status);
   if (P->h_counters) cudaFreeHost(P->h_counters);
   if (P->h_alpha) cudaFreeHost(P->h_alpha);
@@ -660,7 +1277,7 @@ ftp_status ftp_sums(ftp_plan_t P, const double* t, const double* y, const double
   st = stage_obs(P, t, y, dy, nobs, &dt, &dyv, &ddy);
   if (st != FTP_OK) return st;
   int launches = 0;
-  st = run_sums(P, dt, dyv, ddy, nobs, P->grid.df, P->grid.k0, P->grid.nf, H_sums, &launches);
+  st = run_sums_plan(P, dt, dyv, ddy, nobs, H_sums, &launches);
   if (st != FTP_OK) return st;
   ev_rec(P, 5);
   const size_t row = (size_t)P->grid.nf * P->csz;
@@ -699,7 +1316,7 @@ ftp_status ftp_periodogram(ftp_plan_t P, const double* t, const double* y, const
   st = upload_templates(P, tpl, ntemplates, &groups, &pos_of);
   if (st != FTP_OK) return st;
   int launches = 0;
-  st = run_sums(P, dt, dyv, ddy, nobs, P->grid.df, P->grid.k0, P->grid.nf, Hs, &launches);
+  st = run_sums_plan(P, dt, dyv, ddy, nobs, Hs, &launches);
   if (st != FTP_OK) return st;
 
   const int64_t nf = P->grid.nf;
@@ -732,95 +1349,22 @@ ftp_status ftp_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
                      const int64_t* out_off, const ftp_template* bank, int nbank,
                      const int32_t* tpl_of_curve, double* power, double* theta1, double* theta2,
                      double* theta3, uint8_t* flags) {
-  if (!P || ncurves < 0 || !obs_off || !t || !y || !dy || !grids || !out_off || !power ||
-      !theta1 || !theta2 || !theta3)
-    return FTP_ERR_INVALID_ARG;
-  if (ncurves == 0) return FTP_OK;
-  ftp_status st = check_templates(P, bank, nbank);
-  if (st != FTP_OK) return st;
-  int Hs = 0;
-  for (int i = 0; i < nbank; ++i) Hs = std::max(Hs, bank[i].H);
-  // validate every curve on the host before any work is queued
-  for (int64_t c = 0; c < ncurves; ++c) {
-    const int64_t n = obs_off[c + 1] - obs_off[c];
-    if (obs_off[c] < 0 || n < 2) return FTP_ERR_INVALID_ARG;
-    if (n > P->max_nobs) return FTP_ERR_UNSUPPORTED;
-    const ftp_grid& g = grids[c];
-    if (!(g.df > 0.0) || !isfinite(g.df) || g.k0 < 1 || g.nf < 1 || out_off[c] < 0)
-      return FTP_ERR_INVALID_ARG;
-    if (g.nf > P->grid.nf) return FTP_ERR_UNSUPPORTED;
-    int64_t nt = 0;
-    if (grid_len(2 * (int64_t)Hs * (g.k0 + g.nf - 1), P->sigma, &nt) > P->ngrid)
-      return FTP_ERR_UNSUPPORTED;
-    if (tpl_of_curve && (tpl_of_curve[c] < 0 || tpl_of_curve[c] >= nbank))
-      return FTP_ERR_INVALID_ARG;
-  }
-  int prev = 0;
-  cudaGetDevice(&prev);
-  cudaSetDevice(P->device);
-  struct Restore {
-    int d;
-    ~Restore() { cudaSetDevice(d); }
-  } restore{prev};
-  FTP_CK(reset_call(P));
-  std::vector<HGroup> groups;
-  std::vector<int> pos_of;
-  st = upload_templates(P, bank, nbank, &groups, &pos_of);
-  if (st != FTP_OK) return st;
-  const bool in_dev = is_device_ptr(t) && is_device_ptr(y) && is_device_ptr(dy);
-  const bool out_dev = is_device_ptr(power) && is_device_ptr(theta1) && is_device_ptr(theta2) &&
-                       is_device_ptr(theta3) && (!flags || is_device_ptr(flags));
-  int launches = 0;
-  for (int64_t c = 0; c < ncurves; ++c) {
-    const int64_t a0 = obs_off[c], n = obs_off[c + 1] - obs_off[c];
-    const ftp_grid& g = grids[c];
-    const double *dt, *dyv, *ddy;
-    if (in_dev) {
-      dt = t + a0;
-      dyv = y + a0;
-      ddy = dy + a0;
-    } else {
-      st = stage_obs(P, t + a0, y + a0, dy + a0, n, &dt, &dyv, &ddy);
-      if (st != FTP_OK) return st;
-    }
-    int Hc = Hs;
-    if (tpl_of_curve) Hc = bank[tpl_of_curve[c]].H;
-    st = run_sums(P, dt, dyv, ddy, n, g.df, g.k0, g.nf, Hc, &launches);
-    if (st != FTP_OK) return st;
-    const int ntc = tpl_of_curve ? 1 : nbank;
-    const size_t nout = (size_t)ntc * g.nf;
-    double* o[4] = {power + out_off[c], theta1 + out_off[c], theta2 + out_off[c],
-                    theta3 + out_off[c]};
-    uint8_t* of = flags ? flags + out_off[c] : nullptr;
-    int64_t out_lim = (int64_t)nout;  // caller arrays: this curve's block
-    if (!out_dev) {
-      for (int i = 0; i < 4; ++i) o[i] = P->d_out + (size_t)i * P->max_templates * P->grid.nf;
-      of = flags ? P->d_flags : nullptr;
-      out_lim = (int64_t)P->max_templates * P->grid.nf;
-    }
-    if (tpl_of_curve) {
-      const int q = pos_of[tpl_of_curve[c]];
-      const std::vector<HGroup> one{{bank[tpl_of_curve[c]].H, 0, 1}};
-      st = solve(P, dt, dyv, ddy, n, g.df, g.k0, g.nf, Hc, one, P->d_alpha + (size_t)q * kMaxH,
-                 nullptr, P->d_row0, o, of, out_lim, &launches);
-    } else {
-      st = solve(P, dt, dyv, ddy, n, g.df, g.k0, g.nf, Hc, groups, P->d_alpha, P->d_rows,
-                 nullptr, o, of, out_lim, &launches);
-    }
-    if (st != FTP_OK) return st;
-    if (!out_dev) {
-      double* dsto[4] = {power + out_off[c], theta1 + out_off[c], theta2 + out_off[c],
-                         theta3 + out_off[c]};
-      for (int i = 0; i < 4; ++i)
-        FTP_CK(cudaMemcpyAsync(dsto[i], o[i], sizeof(double) * nout, cudaMemcpyDefault,
-                               P->stream));
-      if (flags)
-        FTP_CK(cudaMemcpyAsync(flags + out_off[c], P->d_flags, nout, cudaMemcpyDefault,
-                               P->stream));
-    }
-  }
-  P->last_launches = launches;
-  return finish(P);
+  return run_batch(P, ncurves, obs_off, t, y, dy, grids, out_off, bank, nbank, tpl_of_curve,
+                   power, theta1, theta2, theta3, flags);
+}
+
+ftp_status ftp_set_batch_options(ftp_plan_t P, int64_t chunk_bytes, int use_graph) {
+  if (!P || chunk_bytes < 0) return FTP_ERR_INVALID_ARG;
+  if (chunk_bytes > 0) P->chunk_bytes = (size_t)chunk_bytes;
+  P->use_graph = use_graph != 0;
+  return FTP_OK;
+}
+
+ftp_status ftp_batch_info(ftp_plan_t P, int64_t* chunks, int* graph) {
+  if (!P) return FTP_ERR_INVALID_ARG;
+  if (chunks) *chunks = P->last_chunks;
+  if (graph) *graph = P->last_graph;
+  return FTP_OK;
 }
 
 }  // extern "C"

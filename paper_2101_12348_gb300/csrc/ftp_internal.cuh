@@ -93,7 +93,58 @@ void launch_direct_sums(const double* t, const double* y, const double* dy, int6
                         const int* list, const int* count, int cap, int Hs, int64_t nf_pad,
                         double2* sums, int64_t sums_elems, int* status_rw, cudaStream_t s);
 
+// One lightcurve of a batch, as the batched re-solve pass sees it.  Curves
+// are listed in increasing redo_base (the global index of their frequency
+// k = 0 in the batch's re-solve marks).
+struct CurveDesc {
+  const double* t;
+  const double* y;
+  const double* dy;
+  int64_t n;
+  double df;
+  int64_t k0;
+  int64_t redo_base;
+  int64_t nf;
+  int64_t out_off;  // element offset of the curve's output block [nrows][nf]
+  int32_t Hs;
+  int32_t nrows;
+};
+static_assert(sizeof(CurveDesc) == 80, "CurveDesc layout");
+
+// Direct FP64 sums for the listed global frequency indices of a batch:
+// slot i of `list` (< min(*count, cap)) gets the sums of its curve at row
+// stride `stride` and slot_curve[i] = the curve's index.  moments holds
+// MO_WORDS doubles per curve.
+// After a batched pass whose re-solve list overflowed (*count > cap): sets
+// FTP_FLAG_UNRESOLVED on every output item of the frequencies marked 2.
+void launch_redo_overflow(const CurveDesc* curves, int ncurves, const int* marks, int64_t nmarks,
+                          const int* count, int cap, uint8_t* flags, cudaStream_t s);
+
+void launch_direct_sums_batch(const CurveDesc* curves, int ncurves, const double* moments,
+                              const int* status, const int* list, const int* count, int cap,
+                              int64_t stride, double2* sums, int64_t sums_elems, int* slot_curve,
+                              int* status_rw, cudaStream_t s);
+
 // Steps (b)-(c): assembly, roots, candidates, polish.
+//
+// A batched launch covers many lightcurves: segment s is one curve's share
+// (its frequencies times this launch's templates of the curve), and its work
+// units are seg_units[s] .. seg_units[s+1]-1.
+struct RootsSeg {
+  int64_t sums_off;   // element offset of the curve's sum rows in `sums`
+  int64_t nf_pad;     // row stride of those rows (elements)
+  int64_t nf;         // frequencies of the curve
+  int64_t out_off;    // element offset of the curve's output block [rows][nf]
+  int64_t redo_base;  // global index of the curve's k = 0 in the re-solve marks
+  int32_t Hs;         // harmonics the curve's sums were computed for
+  int32_t curve;      // index of the curve's moments (MO_WORDS doubles each)
+  int32_t tpl_first;  // first template (index into alpha) of this segment
+  int32_t ntpl;       // templates of this segment
+  int32_t row_first;  // output row of template j: rows[row_first + j]; -1: row 0
+  int32_t pad_;
+};
+static_assert(sizeof(RootsSeg) == 64, "RootsSeg layout");
+
 struct RootsArgs {
   const void* sums;        // [3*Hs][nf_pad] complex (float2 or double2, per kernel)
   int64_t sums_elems;      // elements of `sums` (bounds of the staged reads)
@@ -120,13 +171,28 @@ struct RootsArgs {
   // re-solve list (mixed path): frequencies whose estimated error of P from
   // the FP32 sums exceeds kRedoTol; nullable (no re-solve)
   int* redo_list;
-  int* redo_mark;          // [nf] 0/1, dedupes frequencies across templates
+  int* redo_mark;          // [redo_marks] 0 / 1 listed / 2 list full; dedupes across templates
   int* redo_count;
-  int redo_cap;
+  int redo_cap;            // entries of redo_list (batched re-solve pass: slots to read)
+  int64_t redo_marks;      // entries of redo_mark
   double sum_err;          // error bound of one sum (kSumErr*)
   double redo_tol;         // re-solve threshold on the estimated error of P
   int maxit;
   int polish_steps;
+  // batched launches (segs != nullptr): `moments` holds MO_WORDS doubles per
+  // curve, outputs are addressed through the segments, and re-solve marks and
+  // list entries are global frequency indices (redo_base + k).
+  const RootsSeg* segs;
+  const int64_t* seg_units;  // [nseg + 1] first work unit of each segment
+  int nseg;
+  // batched re-solve pass (slot_curve != nullptr): one listed frequency per
+  // work unit; kmap holds the global frequency indices, nf_dev their count,
+  // slot_curve the curve of each slot and curve_seg[curve] its segment in
+  // this launch (-1: the curve has no templates here)
+  const int* slot_curve;
+  const int* curve_seg;
+  int ncurves;         // entries of curve_seg
+  int64_t host_units;  // upper bound of the work units (grid sizing); 0: from nf
 };
 
 // Kernel variants: float2 sums + FP32 Aberth (mixed), double2 sums + FP64
@@ -136,5 +202,9 @@ enum RootsKind { ROOTS_MIXED = 0, ROOTS_FP64 = 1, ROOTS_REDO = 2 };
 // Launches the assembly + Aberth + candidate kernel.  Returns the number of
 // kernel launches issued (1), -1 for an unsupported H, -2 on a CUDA error.
 int launch_roots(RootsKind kind, const RootsArgs& a, int num_sms, cudaStream_t s);
+
+// Frequencies per work unit (32 / lanes per item) of the kernel that
+// launch_roots picks for (kind, H); 0 for an unsupported H.
+int roots_items_per_unit(RootsKind kind, int H);
 
 }  // namespace ftp

@@ -399,7 +399,15 @@ __global__ void gather_kernel(const typename C2<R>::type* __restrict__ X, int64_
   if (status[ST_CODE] != DEV_OK) return;
   const int h = blockIdx.y + 1;
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nf) return;
+  if (k >= nf_pad) return;
+  if (k >= nf) {  // row padding read by whole work units: zeros
+    Cx zero;
+    zero.x = R(0);
+    zero.y = R(0);
+    sums[(int64_t)(h - 1) * nf_pad + k] = zero;
+    if (h <= Hs) sums[(int64_t)(2 * Hs + h - 1) * nf_pad + k] = zero;
+    return;
+  }
   const int64_t j = (int64_t)h * (k0 + k);
   const Cx xp = X[j];
   const Cx xm = X[ngrid - j];
@@ -420,12 +428,58 @@ __global__ void gather_kernel(const typename C2<R>::type* __restrict__ X, int64_
 }
 
 
-// Direct FP64 sums for the frequencies of a list (the re-solve pass of the
-// mixed path): for listed frequency index k, f = (k0 + k) df,
+// Direct FP64 sums for the frequencies of a list (the re-solve pass):
+// for listed frequency index k, f = (k0 + k) df,
 //   Z_h = sum_i w_i e^{i h 2 pi f t_i} (h <= 2 Hs),  Y_h = sum_i w_i (y_i - ybar) e^{...} (h <= Hs),
 // with the phase f t_i reduced modulo one cycle in FP64 and the harmonics
 // formed by repeated multiplication.  One CTA per listed frequency; each warp
 // reduces its lanes' terms with shuffles into shared accumulators.
+//
+// direct_sums_block: the block-wide sums of one curve at frequency f into
+// acc[3 Hs] (Z_1..Z_2Hs, then Y_1..Y_Hs); acc must be zero on entry and every
+// thread of the block calls it.
+__device__ void direct_sums_block(const double* __restrict__ t, const double* __restrict__ y,
+                                  const double* __restrict__ dy, int64_t n, double ybar,
+                                  double wsum, bool unit, double f, int Hs, double2* acc) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = 0; base < n; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    double w = 0.0, r = 0.0, c1 = 1.0, s1 = 0.0;
+    if (i < n) {
+      const double si = dy[i];
+      w = (unit ? 1.0 : 1.0 / (si * si)) / wsum;
+      r = w * (y[i] - ybar);
+      double cyc = f * t[i];
+      cyc -= floor(cyc);
+      sincospi(2.0 * cyc, &s1, &c1);
+    }
+    double pc = c1, ps = s1;  // e^{i h phi}
+    for (int h = 1; h <= 2 * Hs; ++h) {
+      double zx = w * pc, zy = w * ps, yx = r * pc, yy = r * ps;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        zx += __shfl_xor_sync(0xffffffffu, zx, o);
+        zy += __shfl_xor_sync(0xffffffffu, zy, o);
+        if (h <= Hs) {
+          yx += __shfl_xor_sync(0xffffffffu, yx, o);
+          yy += __shfl_xor_sync(0xffffffffu, yy, o);
+        }
+      }
+      if (lane == 0) {
+        atomicAdd(&acc[h - 1].x, zx);
+        atomicAdd(&acc[h - 1].y, zy);
+        if (h <= Hs) {
+          atomicAdd(&acc[2 * Hs + h - 1].x, yx);
+          atomicAdd(&acc[2 * Hs + h - 1].y, yy);
+        }
+      }
+      const double nc = pc * c1 - ps * s1;
+      ps = pc * s1 + ps * c1;
+      pc = nc;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) direct_sums_kernel(
     const double* __restrict__ t, const double* __restrict__ y, const double* __restrict__ dy,
     int64_t n, const double* __restrict__ moments, const int* __restrict__ status, double df,
@@ -437,52 +491,54 @@ __global__ void __launch_bounds__(256) direct_sums_kernel(
   const int total = min(*count, cap);
   const double ybar = moments[MO_YBAR], wsum = moments[MO_WSUM];
   const bool unit = moments[MO_UNIT] != 0.0;
-  const int lane = threadIdx.x & 31;
   for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
     if (!FTP_DCHECK(status_rw, list[idx] >= 0 && list[idx] < nf_pad, 32, list[idx], nf_pad)) break;
     const double f = (double)(k0 + list[idx]) * df;
     for (int q = threadIdx.x; q < 3 * Hs; q += blockDim.x) acc[q] = make_double2(0.0, 0.0);
     __syncthreads();
-    for (int64_t base = 0; base < n; base += blockDim.x) {
-      const int64_t i = base + threadIdx.x;
-      double w = 0.0, r = 0.0, c1 = 1.0, s1 = 0.0;
-      if (i < n) {
-        const double si = dy[i];
-        w = (unit ? 1.0 : 1.0 / (si * si)) / wsum;
-        r = w * (y[i] - ybar);
-        double cyc = f * t[i];
-        cyc -= floor(cyc);
-        sincospi(2.0 * cyc, &s1, &c1);
-      }
-      double pc = c1, ps = s1;  // e^{i h phi}
-      for (int h = 1; h <= 2 * Hs; ++h) {
-        double zx = w * pc, zy = w * ps, yx = r * pc, yy = r * ps;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          zx += __shfl_xor_sync(0xffffffffu, zx, o);
-          zy += __shfl_xor_sync(0xffffffffu, zy, o);
-          if (h <= Hs) {
-            yx += __shfl_xor_sync(0xffffffffu, yx, o);
-            yy += __shfl_xor_sync(0xffffffffu, yy, o);
-          }
-        }
-        if (lane == 0) {
-          atomicAdd(&acc[h - 1].x, zx);
-          atomicAdd(&acc[h - 1].y, zy);
-          if (h <= Hs) {
-            atomicAdd(&acc[2 * Hs + h - 1].x, yx);
-            atomicAdd(&acc[2 * Hs + h - 1].y, yy);
-          }
-        }
-        const double nc = pc * c1 - ps * s1;
-        ps = pc * s1 + ps * c1;
-        pc = nc;
-      }
-    }
+    direct_sums_block(t, y, dy, n, ybar, wsum, unit, f, Hs, acc);
     __syncthreads();
     for (int q = threadIdx.x; q < 3 * Hs; q += blockDim.x)
       if (FTP_DCHECK(status_rw, (int64_t)q * nf_pad + idx < sums_elems, 33, q, idx))
         sums[(int64_t)q * nf_pad + idx] = acc[q];
+    __syncthreads();
+  }
+}
+
+// Batched form: slot idx holds a global frequency index g of the batch; its
+// curve is the last one with redo_base <= g.
+__global__ void __launch_bounds__(256) direct_sums_batch_kernel(
+    const CurveDesc* __restrict__ curves, int ncurves, const double* __restrict__ moments,
+    const int* __restrict__ status, const int* __restrict__ list, const int* __restrict__ count,
+    int cap, int64_t stride, double2* __restrict__ sums, int64_t sums_elems,
+    int* __restrict__ slot_curve, int* status_rw) {
+  __shared__ double2 acc[3 * kMaxH];
+  if (status[ST_CODE] != DEV_OK) return;
+  const int total = min(*count, cap);
+  for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
+    const int64_t g = list[idx];
+    int lo = 0, hi = ncurves;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (curves[mid].redo_base <= g) lo = mid;
+      else hi = mid;
+    }
+    const CurveDesc cd = curves[lo];
+    const int64_t k = g - cd.redo_base;
+    if (!FTP_DCHECK(status_rw, k >= 0 && k < cd.nf, 34, k, cd.nf) ||
+        !FTP_DCHECK(status_rw, cd.Hs >= 1 && cd.Hs <= kMaxH, 35, cd.Hs, kMaxH))
+      break;
+    const double* mo = moments + (size_t)lo * MO_WORDS;
+    const double f = (double)(cd.k0 + k) * cd.df;
+    for (int q = threadIdx.x; q < 3 * cd.Hs; q += blockDim.x) acc[q] = make_double2(0.0, 0.0);
+    __syncthreads();
+    direct_sums_block(cd.t, cd.y, cd.dy, cd.n, mo[MO_YBAR], mo[MO_WSUM], mo[MO_UNIT] != 0.0, f,
+                      cd.Hs, acc);
+    __syncthreads();
+    for (int q = threadIdx.x; q < 3 * cd.Hs; q += blockDim.x)
+      if (FTP_DCHECK(status_rw, (int64_t)q * stride + idx < sums_elems, 36, q, idx))
+        sums[(int64_t)q * stride + idx] = acc[q];
+    if (threadIdx.x == 0) slot_curve[idx] = lo;
     __syncthreads();
   }
 }
@@ -520,6 +576,45 @@ void launch_direct_sums(const double* t, const double* y, const double* dy, int6
                                           Hs, nf_pad, sums, sums_elems, status_rw);
 }
 
+__global__ void __launch_bounds__(256) redo_overflow_kernel(const CurveDesc* __restrict__ curves,
+                                                            int ncurves,
+                                                            const int* __restrict__ marks,
+                                                            int64_t nmarks,
+                                                            const int* __restrict__ count,
+                                                            int cap, uint8_t* __restrict__ flags) {
+  if (*count <= cap) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nmarks; g += stride) {
+    if (marks[g] != 2) continue;
+    int lo = 0, hi = ncurves;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (curves[mid].redo_base <= g) lo = mid;
+      else hi = mid;
+    }
+    const CurveDesc& cd = curves[lo];
+    const int64_t k = g - cd.redo_base;
+    if (k < 0 || k >= cd.nf) continue;
+    for (int r = 0; r < cd.nrows; ++r) flags[cd.out_off + (int64_t)r * cd.nf + k] |= 16u;
+  }
+}
+
+void launch_redo_overflow(const CurveDesc* curves, int ncurves, const int* marks, int64_t nmarks,
+                          const int* count, int cap, uint8_t* flags, cudaStream_t s) {
+  redo_overflow_kernel<<<2 * 152, 256, 0, s>>>(curves, ncurves, marks, nmarks, count, cap, flags);
+}
+
+void launch_direct_sums_batch(const CurveDesc* curves, int ncurves, const double* moments,
+                              const int* status, const int* list, const int* count, int cap,
+                              int64_t stride, double2* sums, int64_t sums_elems, int* slot_curve,
+                              int* status_rw, cudaStream_t s) {
+  int grid = cap < 2 * 152 ? cap : 2 * 152;
+  if (grid < 1) grid = 1;
+  direct_sums_batch_kernel<<<grid, 256, 0, s>>>(curves, ncurves, moments, status, list, count,
+                                                cap, stride, sums, sums_elems, slot_curve,
+                                                status_rw);
+}
+
 template <typename R>
 void launch_points(const double* t, const double* y, const double* dy, int64_t n,
                    const double* moments, const int* status, double df, int64_t ngrid,
@@ -554,7 +649,7 @@ template <typename R>
 void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int64_t nf,
                    int64_t nf_pad, int Hs, int m, double beta, typename C2<R>::type* sums,
                    const int* status, cudaStream_t s) {
-  dim3 g((unsigned)((nf + 255) / 256), (unsigned)(2 * Hs));
+  dim3 g((unsigned)((nf_pad + 255) / 256), (unsigned)(2 * Hs));
   gather_kernel<R><<<g, 256, 0, s>>>(X, ngrid, k0, nf, nf_pad, Hs, m, beta, sums, status);
 }
 

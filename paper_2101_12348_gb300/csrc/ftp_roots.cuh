@@ -283,11 +283,24 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
   R2* Bw = reinterpret_cast<R2*>(gb + C::G_BW);
 
   if (a.status[ST_CODE] != DEV_OK) return;
-  const int64_t nf = a.nf_dev ? (int64_t)*a.nf_dev : a.nf;
+  // Three ways to number the work units:
+  //   one curve      (segs == nullptr): unit = tau * nkb + kb over a.ntpl
+  //                  templates, NGW consecutive frequencies per unit;
+  //   batched        (segs, no slot_curve): the units of segment s follow
+  //                  those of segment s-1 (seg_units), numbered as above
+  //                  within the segment;
+  //   batched redo   (segs and slot_curve): unit = tau * count + slot, one
+  //                  listed frequency per unit (group 0; the others idle).
+  const bool batched = a.segs != nullptr;
+  const bool redo_pass = batched && a.slot_curve != nullptr;
+  const int64_t nf = a.nf_dev ? (int64_t)min(*a.nf_dev, a.redo_cap > 0 ? a.redo_cap : *a.nf_dev)
+                              : a.nf;
   const int64_t nkb = (nf + NGW - 1) / NGW;
-  const int64_t nunits = nkb * a.ntpl;
-  const W ybar = w_of<W>(a.moments[MO_YBAR]), YY = w_of<W>(a.moments[MO_YY]);
-  const R YYr = (R)a.moments[MO_YY];
+  const int64_t nunits = redo_pass ? nf * a.ntpl : batched ? a.seg_units[a.nseg] : nkb * a.ntpl;
+  const double* mom = a.moments;
+  W ybar = w_of<W>(mom[MO_YBAR]), YY = w_of<W>(mom[MO_YY]);
+  R YYr = (R)mom[MO_YY];
+  int cur_curve = 0;
   const W twopi = w_of<W>(6.283185307179586476925286766559);
 
   if (lane == 0) {
@@ -302,24 +315,70 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
     if (lane == 0) v = atomicAdd(a.queue, 1ull);
     return (int64_t)__shfl_sync(0xffffffffu, v, 0);
   };
-  // Lane 0 stages the 3H sum rows of unit u into buffer `buf`.
-  auto issue = [&](int64_t u, int buf) {
+  // Segment of unit u (batched main pass): the last s >= lo with
+  // seg_units[s] <= u.  Units only grow along a warp's queue, so `lo` is the
+  // previous answer and the first probe usually settles it.
+  auto find_seg = [&](int64_t u, int lo) -> int {
+    if (u < a.seg_units[lo + 1]) return lo;
+    int hi = a.nseg;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.seg_units[mid] <= u) lo = mid;
+      else hi = mid;
+    }
+    return lo;
+  };
+  struct URef {
+    int seg;         // segment (-1: none), 0 for one curve
+    int tl;          // template within the segment / launch
+    int64_t kfirst;  // first frequency (slot in the redo pass) of the unit
+  };
+  auto resolve = [&](int64_t u, int hint) -> URef {
+    URef r;
+    if (!batched) {
+      r.seg = 0;
+      r.tl = (int)(u / nkb);
+      r.kfirst = (u % nkb) * NGW;
+    } else if (!redo_pass) {
+      r.seg = find_seg(u, hint);
+      const int64_t local = u - a.seg_units[r.seg];
+      const int64_t nkb_s = (a.segs[r.seg].nf + NGW - 1) / NGW;
+      r.tl = (int)(local / nkb_s);
+      r.kfirst = (local % nkb_s) * NGW;
+    } else {
+      r.kfirst = u % nf;
+      r.tl = (int)(u / nf);
+      const int c = a.slot_curve[r.kfirst];
+      r.seg = (c >= 0 && c < a.ncurves) ? a.curve_seg[c] : -1;
+    }
+    return r;
+  };
+  // Lane 0 stages the 3H sum rows of unit r into buffer `buf`.
+  auto issue = [&](const URef& r, int buf) {
     if (lane != 0) return;
-    const int64_t kb = u % nkb;
+    int64_t base = r.kfirst, stride = a.nf_pad;
+    int Hs = a.Hs;
+    if (batched && r.seg >= 0) {
+      Hs = a.segs[r.seg].Hs;
+      if (!redo_pass) {
+        base += a.segs[r.seg].sums_off;
+        stride = a.segs[r.seg].nf_pad;
+      }
+    }
     S2* dst = stage + (size_t)buf * (C::STAGE_BYTES / sizeof(S2));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&mbar[buf], (unsigned)C::STAGE_BYTES);
     const S2* sums = reinterpret_cast<const S2*>(a.sums);
 #pragma unroll 1
-    for (int r = 0; r < C::ROWS; ++r) {
-      const int src_row = (r < 2 * H) ? r : 2 * a.Hs + (r - 2 * H);
-      const int64_t off = (int64_t)src_row * a.nf_pad + kb * NGW;
+    for (int r2 = 0; r2 < C::ROWS; ++r2) {
+      const int src_row = (r2 < 2 * H) ? r2 : 2 * Hs + (r2 - 2 * H);
+      const int64_t off = (int64_t)src_row * stride + base;
       if (!FTP_DCHECK(a.status, off >= 0 && off + NGW <= a.sums_elems, 11, off, a.sums_elems) ||
           !FTP_DCHECK(a.status, (gaddr(sums + off) & 15) == 0, 12, gaddr(sums + off) & 15, 16) ||
-          !FTP_DCHECK(a.status, (saddr(dst + (size_t)r * NGW) & 15) == 0, 13, 0, 16)) {
+          !FTP_DCHECK(a.status, (saddr(dst + (size_t)r2 * NGW) & 15) == 0, 13, 0, 16)) {
         continue;  // the row never lands: the bounded wait reports a timeout
       }
-      bulk_g2s(dst + (size_t)r * NGW, sums + off, (unsigned)C::ROW_BYTES, &mbar[buf]);
+      bulk_g2s(dst + (size_t)r2 * NGW, sums + off, (unsigned)C::ROW_BYTES, &mbar[buf]);
     }
   };
 
@@ -328,12 +387,42 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
   int buf = 0, cur_tau = -1;
   R sum_abs_alpha = R(0);
   int64_t u = grab();
-  if (u < nunits) issue(u, 0);
+  int seg_hint = 0;
+  if (u < nunits) {
+    const URef r0 = resolve(u, 0);
+    seg_hint = batched && !redo_pass ? r0.seg : 0;
+    issue(r0, 0);
+  }
   while (u < nunits) {
+    const URef cu = resolve(u, seg_hint);
     const int64_t un = grab();
-    if (un < nunits) issue(un, buf ^ 1);
-    const int tau = (int)(u / nkb);
-    const int64_t kb = u % nkb;
+    if (un < nunits) {
+      const URef rn = resolve(un, batched && !redo_pass ? cu.seg : 0);
+      issue(rn, buf ^ 1);
+    }
+    if (batched && !redo_pass) seg_hint = cu.seg;
+    // template (index into alpha) and validity of this unit
+    int tau = cu.tl;
+    bool unit_ok = true;
+    int64_t seg_nf = nf;
+    if (batched) {
+      if (cu.seg < 0) {
+        unit_ok = false;
+        tau = cur_tau < 0 ? 0 : cur_tau;
+      } else {
+        const RootsSeg& sg = a.segs[cu.seg];
+        unit_ok = cu.tl < sg.ntpl;
+        tau = sg.tpl_first + (unit_ok ? cu.tl : 0);
+        seg_nf = sg.nf;
+        if (sg.curve != cur_curve) {  // warp-uniform: this curve's moments
+          mom = a.moments + (size_t)sg.curve * MO_WORDS;
+          ybar = w_of<W>(mom[MO_YBAR]);
+          YY = w_of<W>(mom[MO_YY]);
+          YYr = (R)mom[MO_YY];
+          cur_curve = sg.curve;
+        }
+      }
+    }
     if (tau != cur_tau) {  // warp-uniform: this warp's template tables (FP64, then wide)
       const double2* al = a.alpha + (size_t)tau * kMaxH;
       for (int e = lane; e <= 2 * H; e += 32) {
@@ -358,8 +447,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
       break;
     }
     const S2* st = stage + (size_t)buf * (C::STAGE_BYTES / sizeof(S2));
-    const int64_t k = kb * NGW + gi;
-    const bool valid = k < nf;
+    const int64_t k = redo_pass ? cu.kfirst : cu.kfirst + gi;
+    const bool valid = unit_ok && (redo_pass ? gi == 0 : k < seg_nf);
 
     // ---- sums of this item into wide shared memory (one conversion each)
     for (int q = gl; q < C::ROWS; q += G) {
@@ -742,10 +831,24 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
 
     // ---- outputs: lanes 0..3 of the group convert one value each (one
     //      conversion instruction for the whole warp), then write it
-    const int64_t col = valid ? (a.kmap ? (int64_t)a.kmap[k] : k) : 0;
-    const size_t o = (size_t)a.rows[tau] * a.out_stride + col;
+    int64_t col = 0, ridx = 0, ostride = a.out_stride;
+    size_t o = 0;
+    if (valid) {
+      if (!batched) {
+        col = a.kmap ? (int64_t)a.kmap[k] : k;
+        o = (size_t)a.rows[tau] * a.out_stride + col;
+        ridx = col;
+      } else {
+        const RootsSeg& sg = a.segs[cu.seg];
+        col = redo_pass ? (int64_t)a.kmap[k] - sg.redo_base : k;
+        const int row = sg.row_first < 0 ? 0 : a.rows[sg.row_first + cu.tl];
+        o = (size_t)(sg.out_off + (int64_t)row * sg.nf + col);
+        ostride = sg.nf;
+        ridx = sg.redo_base + col;
+      }
+    }
     const bool in_range =
-        FTP_DCHECK(a.status, !valid || (col >= 0 && col < a.out_stride), 21, col, a.out_stride) &&
+        FTP_DCHECK(a.status, !valid || (col >= 0 && col < ostride), 21, col, ostride) &&
         FTP_DCHECK(a.status, !valid || (int64_t)o < a.out_elems, 22, o, a.out_elems);
     {
       const W v = gl == 0 ? P : gl == 1 ? th1 : gl == 2 ? theta : th3;
@@ -756,6 +859,18 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
       }
     }
     if (valid && in_range && gl == 0) {
+      // a frequency goes on the re-solve list once (mark 0 -> 1); if the
+      // list is full its mark becomes 2 and a later pass flags its items
+      if (redo && FTP_DCHECK(a.status, ridx < a.redo_marks, 23, ridx, a.redo_marks) &&
+          atomicCAS(&a.redo_mark[ridx], 0, 1) == 0) {
+        const int slot = atomicAdd(a.redo_count, 1);
+        if (slot < a.redo_cap) {
+          a.redo_list[slot] = (int)ridx;
+          ++st_redo;
+        } else {
+          atomicExch(&a.redo_mark[ridx], 2);
+        }
+      }
       if (a.flags) {
         unsigned f = 0;
         if (nonconv) f |= 1u;
@@ -763,12 +878,6 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
         if (constant) f |= 4u;
         if (w_f(th1) < 0.0f) f |= 8u;
         a.flags[o] = (uint8_t)f;
-      }
-      if (redo && FTP_DCHECK(a.status, col < a.redo_cap, 23, col, a.redo_cap) &&
-          atomicExch(&a.redo_mark[col], 1) == 0) {
-        const int slot = atomicAdd(a.redo_count, 1);
-        if (slot < a.redo_cap) a.redo_list[slot] = (int)col;
-        ++st_redo;
       }
       st_iters += (unsigned long long)iters;
       st_items += 1;
@@ -812,7 +921,7 @@ int launch_h(const RootsArgs& a, int num_sms, cudaStream_t s) {
     blocks_per_sm = b;
   }
   const int64_t nf = a.nf;  // upper bound when the count lives on the device
-  const int64_t nunits = (nf + C::NGW - 1) / C::NGW * a.ntpl;
+  const int64_t nunits = a.host_units > 0 ? a.host_units : (nf + C::NGW - 1) / C::NGW * a.ntpl;
   int64_t grid = (int64_t)num_sms * blocks_per_sm;
   const int64_t need = (nunits + C::WARPS - 1) / C::WARPS;
   if (grid > need) grid = need;

@@ -17,6 +17,8 @@ constexpr int pick_g(int H) {
 }
 }  // namespace
 
+int roots_lanes_fp64(int H) { return (H >= 1 && H <= kMaxH) ? pick_g(H) : 0; }
+
 int launch_roots_fp64(const RootsArgs& a, int num_sms, cudaStream_t s) {
   switch (a.H) {
 #define FTP_CASE(h) \

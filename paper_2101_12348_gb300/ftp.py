@@ -35,7 +35,8 @@ STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE
 # every symbol include/ftp.h declares
 EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy",
            "ftp_status_string", "ftp_plan_info", "ftp_solver_stats", "ftp_set_timing",
-           "ftp_stage_times", "ftp_periodogram_sums_noalloc")
+           "ftp_stage_times", "ftp_periodogram_sums_noalloc", "ftp_set_batch_options",
+           "ftp_batch_info")
 
 
 class FtpGrid(C.Structure):
@@ -85,6 +86,8 @@ def load(path: str | None = None) -> C.CDLL:
                                                  C.POINTER(FtpTemplate), i32, vp, vp, vp, vp,
                                                  vp, i32, vp]
     lib.ftp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
+    lib.ftp_set_batch_options.argtypes = [vp, i64, i32]
+    lib.ftp_batch_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
     for name in EXPORTS:
         if name not in ("ftp_destroy", "ftp_status_string"):
             getattr(lib, name).restype = i32
@@ -178,6 +181,17 @@ def ftp_batch(plan: int, obs_off, t, y, dy, grids, out_off, bank, tpl_of_curve, 
     _check(load().ftp_batch(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t), _ptr(y), _ptr(dy),
                             g, _ptr(out_off), arr, len(keep) // 2, _ptr(tpc), _ptr(power),
                             _ptr(theta1), _ptr(theta2), _ptr(theta3), _ptr(flags)), "ftp_batch")
+
+
+def ftp_set_batch_options(plan: int, chunk_bytes: int = 0, use_graph: bool = True) -> None:
+    _check(load().ftp_set_batch_options(plan, int(chunk_bytes), 1 if use_graph else 0),
+           "ftp_set_batch_options")
+
+
+def ftp_batch_info(plan: int) -> dict:
+    n, g = C.c_int64(), C.c_int()
+    _check(load().ftp_batch_info(plan, C.byref(n), C.byref(g)), "ftp_batch_info")
+    return {"chunks": n.value, "graph": g.value}
 
 
 def ftp_plan_info(plan: int) -> dict:
