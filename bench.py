@@ -54,10 +54,17 @@ def parse_args():
                     help="timed steps of the FP64 path (0 skips it)")
     ap.add_argument("--n-freq", type=int, default=250_000,
                     help="frequencies of the grid (smaller only for profiling captures)")
-    ap.add_argument("--workload", choices=["long", "survey", "bank"], default="long",
+    ap.add_argument("--workload", choices=["long", "survey", "bank", "screen"], default="long",
                     help="long: one long lightcurve (the headline line); survey: 4096 "
-                         "curves batched; bank: 32 templates over one N=1e5 lightcurve")
+                         "curves batched; bank: 32 templates over one N=1e5 lightcurve; "
+                         "screen: surrogate-screened survey vs exhaustive, with training")
     ap.add_argument("--ncurves", type=int, default=4096, help="curves of the survey workload")
+    ap.add_argument("--train-curves", type=int, default=50_000,
+                    help="training curves of the screen workload")
+    ap.add_argument("--heldout-curves", type=int, default=2048,
+                    help="held-out curves of the screen workload")
+    ap.add_argument("--train-steps", type=int, default=4000,
+                    help="Adam steps of the screen workload's training")
     return ap.parse_args()
 
 
@@ -656,6 +663,130 @@ def run_bank(args, world, rank, local, pg):
         print(json.dumps(result), flush=True)
 
 
+SCREEN = ("learned screening: {n} held-out lightcurves drawn as the batched survey with H=4 "
+          "templates (bank of 16), surrogate 10->128->128->1 BF16 trained on exact FTP of "
+          "{m} curves; exact solve on the top 1% of frequencies +-3 neighbours")
+
+
+def run_screen(args, world, rank, local, pg):
+    """Surrogate screening (2H+2 features -> BF16 MLP -> top 1% +- 3 -> exact
+    solve) against the exhaustive batch on held-out curves.  Training data
+    are exact GPU results on separate curves; training is untimed and
+    reported.  A step is one screened batch over every held-out curve; value
+    counts every frequency of those curves (the periodogram peak question is
+    answered for all of them), exact_evals counts the ones solved exactly."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_2101_12348_gb300 import ftp, screen
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    H, nfeat, top, nbr = 4, 10, 0.01, 3
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    # plan large enough for every curve drawn as the survey (T <= 3000 d, N <= 20000)
+    plan = ftp.ftp_plan(20_000, H, (1.0 / 15000.0, 1, 150_000), 16, "mixed", local, sh)
+    # ---- training rows from exact results, 1024 curves at a time
+    cap = 250_000_000  # rows (11 GB of features and labels)
+    Xt = torch.empty((cap, nfeat), dtype=torch.float32, device=dev)
+    yt = torch.empty(cap, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    nrows, done, group = 0, 0, 0
+    while done < args.train_curves:
+        m = min(1024, args.train_curves - done)
+        sv = synth.survey(ncurves=m, Hs=(H,), seed=50_000 + group)
+        nrows = screen.training_rows(plan, sv.obs_off, sv.t, sv.y, sv.dy,
+                                     [(g.df, g.k0, g.nf) for g in sv.grids],
+                                     [(b.c, b.s) for b in sv.bank], sv.tpl_of_curve, H,
+                                     top_frac=0.005, neighbours=3, rand_frac=0.005,
+                                     seed=group + 1,
+                                     X_out=Xt, y_out=yt, count=nrows)
+        done += m
+        group += 1
+    rows = min(nrows, cap)
+    torch.cuda.synchronize(dev)
+    label_s = time.perf_counter() - t0
+    net = screen.Surrogate(H, seed=3, device=local)
+    losses = np.empty(args.train_steps, dtype=np.float32)
+    t0 = time.perf_counter()
+    net.train(Xt, yt, rows, steps=args.train_steps, batch=4096, lr=2e-3, seed=9, losses=losses)
+    train_s = time.perf_counter() - t0
+    del Xt, yt
+    # ---- held-out curves: exhaustive vs screened
+    sv = synth.survey(ncurves=args.heldout_curves, Hs=(H,), seed=90_001)
+    bank = [(b.c, b.s) for b in sv.bank]
+    grids = [(g.df, g.k0, g.nf) for g in sv.grids]
+    off = screen.row_offsets(grids)
+    tot = int(off[-1])
+    dt_, dy_, ds_ = (torch.from_numpy(a).to(dev) for a in (sv.t, sv.y, sv.dy))
+    ex = [torch.empty(tot, dtype=torch.float64, device=dev) for _ in range(4)]
+    sc = [torch.empty(tot, dtype=torch.float64, device=dev) for _ in range(4)]
+    fl = torch.empty(tot, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def call_ex():
+        ftp.ftp_batch(plan, sv.obs_off, dt_, dy_, ds_, grids, off[:-1], bank, sv.tpl_of_curve,
+                      *ex, None)
+
+    def call_sc():
+        ftp.ftp_batch_screened(plan, sv.obs_off, dt_, dy_, ds_, grids, off[:-1], bank,
+                               sv.tpl_of_curve, net.h, top, nbr, *sc, fl)
+
+    for _ in range(max(1, args.warmup)):
+        call_sc()
+    call_ex()
+    barrier(pg)
+    with ClockSampler(local) as clk:
+        step_ms = _timed_calls(stream, flush, args.steps, call_sc)
+    barrier(pg)
+    ex_ms = _timed_calls(stream, flush, max(1, min(3, args.steps)), call_ex)
+    clocks = clk.summary()
+    launches = ftp.ftp_plan_info(plan)["last_launches"]
+    stats = ftp.ftp_solver_stats(plan)
+    P_ex, P_sc = ex[0].cpu().numpy(), sc[0].cpu().numpy()
+    evaluated = int(np.sum(~np.isnan(P_sc)))
+    hits = []
+    for c in range(sv.ncurves):
+        a, b = P_sc[off[c]:off[c + 1]], P_ex[off[c]:off[c + 1]]
+        hits.append(bool(np.nanmax(a) >= b.max() - 1e-4))
+    recall = float(np.mean(hits))
+    inj = sv.injected
+    total_ms = max_over_ranks(pg, sum(step_ms), dev)
+    value = sum_over_ranks(pg, float(args.steps * tot), dev) / (total_ms / 1e3)
+    ex_value = tot * len(ex_ms) / (sum(ex_ms) / 1e3)
+    cfg = {"workload": SCREEN.format(n=sv.ncurves, m=args.train_curves),
+           "curves": sv.ncurves, "freqs_per_step": tot, "top_frac": top, "neighbours": nbr,
+           "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU"}
+    result = _result(args, world, value, step_ms, cfg,
+                     screening={"recall": recall,
+                                "recall_injected": float(np.mean(np.array(hits)[inj])),
+                                "recall_noise": float(np.mean(np.array(hits)[~inj])),
+                                "evaluated_frac": round(evaluated / tot, 4),
+                                "exact_evals_per_s": round(evaluated * args.steps /
+                                                           (total_ms / 1e3), 1),
+                                "exhaustive_value": round(ex_value, 1),
+                                "speedup_vs_exhaustive": round(value / ex_value, 3)},
+                     training={"curves": args.train_curves, "rows": rows,
+                               "rows_selected": nrows,
+                               "selection": "exact top 0.5% +-3 and a random 0.5% of each "
+                                            "curve's frequencies",
+                               "label_s": round(label_s, 2), "train_s": round(train_s, 2),
+                               "steps": args.train_steps, "batch": 4096,
+                               "loss_first": float(losses[:20].mean()),
+                               "loss_last": float(losses[-100:].mean())},
+                     solver={"mean_iterations": round(stats["mean_iterations"], 3),
+                             "items_last_call": stats["items"]},
+                     clocks=clocks, gpu_launches=args.steps * launches)
+    net.close()
+    ftp.ftp_destroy(plan)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, world, rank, local, pg):
     """The FP64 CPU oracle on the host cores, on the same workload and metric:
@@ -703,6 +834,8 @@ def main():
             run_survey(args, world, rank, local, pg)
         elif args.workload == "bank":
             run_bank(args, world, rank, local, pg)
+        elif args.workload == "screen":
+            run_screen(args, world, rank, local, pg)
         else:
             run_ours(args, world, rank, local, pg)
     finally:

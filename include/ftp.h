@@ -82,6 +82,8 @@ typedef enum {
 #define FTP_FLAG_NEGATIVE_AMP 8u  /* best theta1 < 0 (Section 2.1: allowed, reported) */
 #define FTP_FLAG_UNRESOLVED 16u   /* ill-conditioned but not re-solved: the batch's
                                      re-solve list was full (ftp_batch only) */
+#define FTP_FLAG_SCREENED_OUT 32u /* not evaluated: screened out by the surrogate
+                                     (ftp_batch_screened); P and theta are NaN */
 
 #define FTP_MAX_H 16
 
@@ -265,6 +267,111 @@ ftp_status ftp_periodogram_sums_noalloc(const void* sums, int64_t row_stride,
                                         double* power, double* theta1, double* theta2,
                                         double* theta3, uint8_t* flags, int device,
                                         void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned screening.  The paper has no surrogate: these entry points rank the
+ * trial frequencies of a lightcurve with a small network so that the exact
+ * solve of steps (b)-(c) runs only on the most promising ones and their
+ * neighbours.  The network reads 2 H_f + 2 features per frequency taken from
+ * the step (a) sums (so they cost no extra pass over the observations):
+ *   x[h-1]      the floating-mean Lomb-Scargle power at h*omega (the H = 1
+ *               template periodogram, Section 2.1), h = 1..H_f
+ *   x[H_f+h-1]  |Y_h|^2 / YY, h = 1..H_f
+ *   x[2 H_f]    the multi-harmonic least-squares power with H_f harmonics
+ *               (Section 2.1), an upper bound of the template power
+ *   x[2 H_f+1]  log10(N_obs)
+ * and predicts the template power P.  It is 2H_f+2 -> 128 -> 128 -> 1 with
+ * ReLU, BF16 weights and activations and FP32 accumulation on the tensor
+ * cores.  Parameters are a flat FP32 array:
+ *   W1 [128][nfeat] | b1 [128] | W2 [128][128] | b2 [128] | w3 [128] | b3
+ * (row-major, W2[j][i] maps input i to output j).
+ * ------------------------------------------------------------------------ */
+typedef struct ftp_mlp_s* ftp_mlp_t;
+
+/* Number of parameters for nfeat inputs (1 <= nfeat <= 18), or -1. */
+int64_t ftp_mlp_param_count(int nfeat);
+
+/*
+ * ftp_mlp_create - a network of nfeat inputs on `device`, with its FP32
+ * master parameters, Adam moments and gradient workspace.  params (host or
+ * device, nullable) gives the initial parameters; NULL draws each layer's
+ * weights and biases uniformly in +-1/sqrt(fan_in) from `seed`.
+ * cuda_stream: a stream of that device, or NULL for one of its own.
+ */
+ftp_status ftp_mlp_create(ftp_mlp_t* out, int nfeat, const float* params, uint64_t seed,
+                          int device, void* cuda_stream);
+void ftp_mlp_destroy(ftp_mlp_t mlp);
+/* Copy the parameters out / in (host or device arrays of
+ * ftp_mlp_param_count floats); set also resets the Adam state. */
+ftp_status ftp_mlp_get_params(ftp_mlp_t mlp, float* params);
+ftp_status ftp_mlp_set_params(ftp_mlp_t mlp, const float* params);
+
+/* Scores of n rows of X [n][nfeat] (FP32, host or device) into scores [n]. */
+ftp_status ftp_mlp_forward(ftp_mlp_t mlp, const float* X, int64_t n, float* scores);
+
+/*
+ * ftp_mlp_gradient - gradient (nullable, ftp_mlp_param_count floats, host or
+ * device) and value (loss, nullable, host or device) of the mean squared
+ * error mean_i (s(X[r_i]) - target[r_i])^2 over the n rows r_i = idx[i]
+ * (idx nullable: r_i = i) of X [rows][nfeat] / target [rows].  The error
+ * signals of the backward pass are rounded to BF16 where they enter the
+ * weight-gradient products, as the tensor cores consume them.
+ */
+ftp_status ftp_mlp_gradient(ftp_mlp_t mlp, const float* X, const float* target, int64_t rows,
+                            const int64_t* idx, int64_t n, float* grad, float* loss);
+
+/*
+ * ftp_mlp_train - `steps` Adam steps (beta = 0.9 / 0.999, eps = 1e-8, rate
+ * lr) on minibatches of `batch` rows of X / target (device arrays), drawn
+ * with replacement by a counter-based generator keyed by `seed` and the
+ * step count.  losses (host or device, nullable) receives each step's
+ * minibatch loss.
+ */
+ftp_status ftp_mlp_train(ftp_mlp_t mlp, const float* X, const float* target, int64_t rows,
+                         int64_t steps, int64_t batch, float lr, uint64_t seed, float* losses);
+
+/*
+ * ftp_batch_features - step (a) and the screening features for many curves
+ * (arguments as ftp_batch); curve c's 2 H_feat + 2 features of frequency k
+ * go to row row_off[c] + k of `features` (device, FP32 [rows][2 H_feat + 2]).
+ * row_off is a host array.  1 <= H_feat <= min(8, the plan's max_H).
+ */
+ftp_status ftp_batch_features(ftp_plan_t plan, int64_t ncurves, const int64_t* obs_off,
+                              const double* t, const double* y, const double* dy,
+                              const ftp_grid* grids, const int64_t* row_off, int H_feat,
+                              float* features);
+
+/*
+ * ftp_batch_screened - ftp_batch with screening: per curve, the features of
+ * every frequency are scored by `mlp` (H_feat = (nfeat - 2) / 2), the
+ * ceil(top_frac * nf) best scores and their +-neighbours frequencies are
+ * selected, and steps (b)-(c) run on the work units that hold a selected
+ * frequency (a unit is a few consecutive frequencies, so a little more than
+ * the selection is evaluated).  Evaluated frequencies get exact results;
+ * the others NaN with FTP_FLAG_SCREENED_OUT.  0 < top_frac <= 1.
+ */
+ftp_status ftp_batch_screened(ftp_plan_t plan, int64_t ncurves, const int64_t* obs_off,
+                              const double* t, const double* y, const double* dy,
+                              const ftp_grid* grids, const int64_t* out_off,
+                              const ftp_template* bank, int nbank, const int32_t* tpl_of_curve,
+                              ftp_mlp_t mlp, double top_frac, int neighbours, double* power,
+                              double* theta1, double* theta2, double* theta3, uint8_t* flags);
+
+/*
+ * ftp_training_rows - training rows for the surrogate from exact results:
+ * per curve (rows row_off[c] .. row_off[c+1]-1 of power [rows] and
+ * features [rows][nfeat], device arrays; row_off on the host), the rows
+ * among the ceil(top_frac * nf) largest powers and their +-neighbours, and
+ * every row whose counter-based hash (keyed by seed) falls below rand_frac,
+ * are appended in order to X_out [cap][nfeat] / y_out [cap] (device) from
+ * row *count on; *count (host) is advanced by the rows selected (rows past
+ * cap are counted, not written).
+ */
+ftp_status ftp_training_rows(const double* power, const float* features, int nfeat,
+                             int64_t ncurves, const int64_t* row_off, double top_frac,
+                             int neighbours, double rand_frac, uint64_t seed, float* X_out,
+                             float* y_out, int64_t cap, int64_t* count, int device,
+                             void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -30,9 +30,15 @@ Two things are defined here, each by its plain definition:
      loss = mean((s - target)^2)
    Gradients are taken with respect to the rounded weights (the master copy
    is FP32; rounding is treated as the identity in the backward pass), with
-   relu'(z) = [z > 0].  With bf16=False every rounding is skipped and the
-   function is an ordinary smooth network, which the tests pin by finite
-   differences.
+   relu'(z) = [z > 0].  The backward pass of the BF16 network rounds the two
+   error signals where they enter a matrix product, as the tensor cores
+   consume them:
+     r = s - target, ds = 2 r / n, dZ2 = ds w3b^T * [Z2 > 0]
+     g_w3 = A2^T ds, g_b3 = sum ds, g_b2 = column sums of dZ2
+     g_W2 = bf16(dZ2)^T A1,  dZ1 = (bf16(dZ2) W2b) * [Z1 > 0]
+     g_b1 = column sums of dZ1, g_W1 = bf16(dZ1)^T Xb
+   With bf16=False every rounding is skipped and the function is an ordinary
+   smooth network, which the tests pin by finite differences.
 
 Flat parameter layout (shared with the C ABI as an interface):
    W1 [hidden][nfeat] row-major, b1 [hidden], W2 [hidden][hidden] row-major
@@ -143,12 +149,14 @@ def loss_and_gradients(flat, X, target, nfeat: int, hidden: int = 128, bf16: boo
     g = {}
     g["w3"] = fw["A2"].T @ ds
     g["b3"] = np.array([np.sum(ds)])
+    rnd = bf16_round if bf16 else (lambda v: v)
     dZ2 = np.outer(ds, fw["w3"]) * (fw["Z2"] > 0)      # through relu
-    g["W2"] = dZ2.T @ fw["A1"]
     g["b2"] = np.sum(dZ2, axis=0)
+    dZ2 = rnd(dZ2)
+    g["W2"] = dZ2.T @ fw["A1"]
     dZ1 = (dZ2 @ fw["W2"]) * (fw["Z1"] > 0)
-    g["W1"] = dZ1.T @ fw["Xb"]
     g["b1"] = np.sum(dZ1, axis=0)
+    g["W1"] = rnd(dZ1).T @ fw["Xb"]
     return loss, flatten(g)
 
 

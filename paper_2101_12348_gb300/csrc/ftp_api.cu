@@ -12,6 +12,7 @@
 
 #include "../../include/ftp.h"
 #include "ftp_internal.cuh"
+#include "ftp_screen.cuh"
 
 namespace ftp {
 int launch_roots_mixed(const RootsArgs& a, int num_sms, cudaStream_t s);
@@ -143,6 +144,16 @@ struct ftp_plan_s {
   uint64_t eager_key = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_launches = 0;
+  // screening workspace (ftp_batch_screened; grown on demand)
+  float* d_bfeat = nullptr;     // [rows of a chunk][nfeat]
+  size_t bfeat_cap = 0;
+  float* d_bscore = nullptr;    // [rows of a chunk]
+  size_t bscore_cap = 0;
+  uint8_t* d_bsel = nullptr;    // [rows of a chunk]
+  size_t bsel_cap = 0;
+  int64_t* d_bulist = nullptr;  // listed work units of one launch
+  size_t bulist_cap = 0;
+  unsigned long long* d_bucount = nullptr;
 };
 
 namespace {
@@ -568,6 +579,7 @@ struct BCurve {
   int64_t out_off;
   double df;
   int Hc, ntc, tpl;
+  int Ht;  // template harmonics (Hc, the sums' harmonics, may be larger for features)
 };
 struct BLaunch {
   int H, ntpl, Hs;
@@ -578,6 +590,18 @@ struct BChunk {
   int64_t c0, c1, sums_elems, nf_total;
   int Hs;
   std::vector<BLaunch> launches;
+  int64_t items;  // (template, frequency) output items of the chunk's curves
+};
+
+// Optional extra work of a batch: features only (feat_out), or screening by
+// the surrogate network before the exact solve (mlp).
+struct BatchScreen {
+  int Hf = 0;                         // feature harmonics
+  float* feat_out = nullptr;          // features-only mode: device [rows][2 Hf + 2]
+  const int64_t* feat_row = nullptr;  // host: first features row of curve c
+  const ftp_mlp_s* mlp = nullptr;     // screened mode
+  double top_frac = 0.0;
+  int nbr = 0;
 };
 
 uint64_t fnv(uint64_t h, const void* p, size_t n) {
@@ -593,7 +617,9 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
                                 const std::vector<BChunk>& chunks, const RootsSeg* d_segs,
                                 const int64_t* d_units, const CurveDesc* d_curves,
                                 const int* d_cseg, double* const* o, uint8_t* of,
-                                int64_t extent, int* launches) {
+                                int64_t extent, const BatchScreen* scr,
+                                const ScreenCurve* d_scurves, const int64_t* d_rowoff,
+                                int* launches) {
   cudaStream_t s = P->stream;
   const RootsKind kind = P->mixed ? ROOTS_MIXED : ROOTS_FP64;
   const RootsKind rkind = P->mixed ? ROOTS_REDO : ROOTS_FP64;
@@ -610,6 +636,46 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       if (st != FTP_OK) return st;
     }
     if (tm) cudaEventRecord(P->bev[4 * q + 1], s);
+    const bool screened = scr && scr->mlp;
+    if (scr && scr->Hf > 0) {
+      // features of every frequency of the chunk (into the caller's array in
+      // features-only mode), then the network's scores, the selection, and
+      // the outputs of the frequencies that will not be evaluated
+      FeatArgs fa{};
+      fa.sums = P->d_bsums;
+      fa.moments = P->d_bmom;
+      fa.curves = d_scurves + ch.c0;
+      fa.ncurves = (int)(ch.c1 - ch.c0);
+      fa.Hf = scr->Hf;
+      fa.nrows = ch.nf_total;
+      fa.out = scr->feat_out ? scr->feat_out : P->d_bfeat;
+      fa.status = P->d_status;
+      const int r = launch_features(fa, !P->mixed, s);
+      if (r < 0) return FTP_ERR_UNSUPPORTED;
+      *launches += r;
+      if (!screened) {
+        if (tm) {
+          cudaEventRecord(P->bev[4 * q + 2], s);
+          cudaEventRecord(P->bev[4 * q + 3], s);
+        }
+        FTP_CK(cudaGetLastError());
+        continue;
+      }
+      if (launch_mlp_forward(mlp_params_dev(scr->mlp), mlp_nfeat(scr->mlp), P->d_bfeat,
+                             ch.nf_total, P->d_bscore, P->d_status, P->num_sms, s) < 0)
+        return FTP_ERR_CUDA;
+      SelectArgs sa{};
+      sa.ncurves = (int)(ch.c1 - ch.c0);
+      sa.row_off = d_rowoff + ch.c0 + q;
+      sa.top_frac = scr->top_frac;
+      sa.nbr = scr->nbr;
+      sa.sel = P->d_bsel;
+      sa.status = P->d_status;
+      launch_select(sa, P->d_bscore, false, s);
+      launch_fill(d_scurves + ch.c0, (int)(ch.c1 - ch.c0), ch.items, o[0], o[1], o[2], o[3], of,
+                  P->d_status, s);
+      *launches += 3;
+    }
     FTP_CK(cudaMemsetAsync(P->d_bmark, 0, sizeof(int) * (size_t)ch.nf_total, s));
     FTP_CK(cudaMemsetAsync(P->d_bcount, 0, sizeof(int), s));
     for (const BLaunch& L : ch.launches) {
@@ -644,6 +710,15 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;
       a.host_units = L.units;
+      if (screened) {
+        FTP_CK(cudaMemsetAsync(P->d_bucount, 0, sizeof(unsigned long long), s));
+        launch_unit_list(d_segs + L.seg_first, d_units + L.units_first, L.nseg, L.units,
+                         roots_items_per_unit(kind, L.H), P->d_bsel, P->d_bulist, P->d_bucount,
+                         P->d_status, s);
+        *launches += 1;
+        a.unit_list = P->d_bulist;
+        a.unit_count = P->d_bucount;
+      }
       FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), s));
       const int r = launch_roots(kind, a, P->num_sms, s);
       if (r == -1) return FTP_ERR_UNSUPPORTED;
@@ -711,16 +786,22 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
                      const double* y, const double* dy, const ftp_grid* grids,
                      const int64_t* out_off, const ftp_template* bank, int nbank,
                      const int32_t* tpl_of_curve, double* power, double* theta1, double* theta2,
-                     double* theta3, uint8_t* flags) {
-  if (!P || ncurves < 0 || !obs_off || !t || !y || !dy || !grids || !out_off || !power ||
-      !theta1 || !theta2 || !theta3)
+                     double* theta3, uint8_t* flags, const BatchScreen* scr) {
+  const bool feat_only = scr && scr->feat_out;
+  const int Hf = scr ? scr->Hf : 0;
+  if (!P || ncurves < 0 || !obs_off || !t || !y || !dy || !grids)
     return FTP_ERR_INVALID_ARG;
+  if (!feat_only && (!out_off || !power || !theta1 || !theta2 || !theta3))
+    return FTP_ERR_INVALID_ARG;
+  if (feat_only && (!scr->feat_row || !is_device_ptr(scr->feat_out))) return FTP_ERR_INVALID_ARG;
+  if (scr && (Hf < 1 || Hf > kFeatMaxH || Hf > P->max_H)) return FTP_ERR_UNSUPPORTED;
   if (ncurves == 0) return FTP_OK;
   if (ncurves > (int64_t)1 << 30) return FTP_ERR_UNSUPPORTED;
-  ftp_status st = check_templates(P, bank, nbank);
+  ftp_status st = feat_only ? FTP_OK : check_templates(P, bank, nbank);
   if (st != FTP_OK) return st;
-  int Hs = 0;
-  for (int i = 0; i < nbank; ++i) Hs = std::max(Hs, bank[i].H);
+  int Hs = Hf;
+  if (!feat_only)
+    for (int i = 0; i < nbank; ++i) Hs = std::max(Hs, bank[i].H);
   // ---- validate every curve on the host before any work is queued
   int64_t o_lo = obs_off[0], o_hi = obs_off[0], extent = 0;
   for (int64_t c = 0; c < ncurves; ++c) {
@@ -728,18 +809,19 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     if (obs_off[c] < 0 || n < 2) return FTP_ERR_INVALID_ARG;
     if (n > P->max_nobs) return FTP_ERR_UNSUPPORTED;
     const ftp_grid& g = grids[c];
-    if (!(g.df > 0.0) || !isfinite(g.df) || g.k0 < 1 || g.nf < 1 || out_off[c] < 0)
+    if (!(g.df > 0.0) || !isfinite(g.df) || g.k0 < 1 || g.nf < 1)
       return FTP_ERR_INVALID_ARG;
+    if (feat_only ? scr->feat_row[c] < 0 : out_off[c] < 0) return FTP_ERR_INVALID_ARG;
     if (g.nf > P->grid.nf) return FTP_ERR_UNSUPPORTED;
-    if (tpl_of_curve && (tpl_of_curve[c] < 0 || tpl_of_curve[c] >= nbank))
+    if (!feat_only && tpl_of_curve && (tpl_of_curve[c] < 0 || tpl_of_curve[c] >= nbank))
       return FTP_ERR_INVALID_ARG;
-    const int H = tpl_of_curve ? bank[tpl_of_curve[c]].H : Hs;
+    const int H = std::max(Hf, (!feat_only && tpl_of_curve) ? bank[tpl_of_curve[c]].H : Hs);
     int64_t nt = 0;
     if (grid_len(2 * (int64_t)H * (g.k0 + g.nf - 1), P->sigma, &nt) > P->ngrid)
       return FTP_ERR_UNSUPPORTED;
     o_lo = std::min(o_lo, obs_off[c]);
     o_hi = std::max(o_hi, obs_off[c + 1]);
-    extent = std::max(extent, out_off[c] + (tpl_of_curve ? 1 : nbank) * g.nf);
+    if (!feat_only) extent = std::max(extent, out_off[c] + (tpl_of_curve ? 1 : nbank) * g.nf);
   }
   int prev = 0;
   cudaGetDevice(&prev);
@@ -749,8 +831,9 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     ~Restore() { cudaSetDevice(d); }
   } restore{prev};
   const bool in_dev = is_device_ptr(t) && is_device_ptr(y) && is_device_ptr(dy);
-  const bool out_dev = is_device_ptr(power) && is_device_ptr(theta1) && is_device_ptr(theta2) &&
-                       is_device_ptr(theta3) && (!flags || is_device_ptr(flags));
+  const bool out_dev = feat_only ||
+                       (is_device_ptr(power) && is_device_ptr(theta1) && is_device_ptr(theta2) &&
+                        is_device_ptr(theta3) && (!flags || is_device_ptr(flags)));
 
   // ---- per-curve layout and chunks
   bool grew = false;
@@ -762,7 +845,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   std::vector<BCurve> cv((size_t)ncurves);
   std::vector<BChunk> chunks;
   {
-    BChunk cur{0, 0, 0, 0, 0, {}};
+    BChunk cur{0, 0, 0, 0, 0, {}, 0};
     for (int64_t c = 0; c < ncurves; ++c) {
       BCurve& b = cv[(size_t)c];
       const ftp_grid& g = grids[c];
@@ -775,10 +858,11 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       b.k0 = g.k0;
       b.df = g.df;
       b.nf_pad = (g.nf + 63) / 64 * 64;
-      b.tpl = tpl_of_curve ? tpl_of_curve[c] : -1;
-      b.Hc = tpl_of_curve ? bank[b.tpl].H : Hs;
-      b.ntc = tpl_of_curve ? 1 : nbank;
-      b.out_off = out_off[c];
+      b.tpl = (!feat_only && tpl_of_curve) ? tpl_of_curve[c] : -1;
+      b.Ht = b.tpl >= 0 ? bank[b.tpl].H : Hs;
+      b.Hc = std::max(b.Ht, Hf);
+      b.ntc = feat_only ? 0 : tpl_of_curve ? 1 : nbank;
+      b.out_off = feat_only ? 0 : out_off[c];
       const int64_t J = 2 * (int64_t)b.Hc * (g.k0 + g.nf - 1);
       b.ngrid = grid_len_class(J, P->sigma, &b.ntiles);
       if (b.ngrid > P->ngrid) b.ngrid = grid_len(J, P->sigma, &b.ntiles);
@@ -788,12 +872,13 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
                          cur.nf_total + b.nf > ((int64_t)1 << 30));
       if (full) {
         chunks.push_back(cur);
-        cur = BChunk{c, c, 0, 0, 0, {}};
+        cur = BChunk{c, c, 0, 0, 0, {}, 0};
       }
       b.sums_off = cur.sums_elems;
       b.redo_base = cur.nf_total;
       cur.sums_elems += elems;
       cur.nf_total += b.nf;
+      cur.items += (int64_t)b.ntc * b.nf;
       cur.Hs = std::max(cur.Hs, b.Hc);
       cur.c1 = c + 1;
     }
@@ -804,14 +889,16 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   std::vector<HGroup> groups;
   std::vector<int> pos_of;
   FTP_CK(reset_call(P));
-  st = upload_templates(P, bank, nbank, &groups, &pos_of);
-  if (st != FTP_OK) return st;
+  if (!feat_only) {
+    st = upload_templates(P, bank, nbank, &groups, &pos_of);
+    if (st != FTP_OK) return st;
+  }
   const RootsKind kind = P->mixed ? ROOTS_MIXED : ROOTS_FP64;
   std::vector<RootsSeg> segs;
   std::vector<int64_t> units;
   std::vector<int> cseg;
   size_t max_chunk_curves = 0;
-  int64_t max_sums_elems = 0, max_nf_total = 0;
+  int64_t max_sums_elems = 0, max_nf_total = 0, max_units = 0;
   for (BChunk& ch : chunks) {
     const int64_t ncc = ch.c1 - ch.c0;
     max_chunk_curves = std::max(max_chunk_curves, (size_t)ncc);
@@ -820,9 +907,11 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     // (H, first, count) of each launch: one per template group (whole bank),
     // or one per distinct H of the chunk's curves (one template per curve)
     std::vector<HGroup> lg;
-    if (tpl_of_curve) {
+    if (feat_only) {
+      // no exact solve
+    } else if (tpl_of_curve) {
       std::vector<int> hs;
-      for (int64_t c = ch.c0; c < ch.c1; ++c) hs.push_back(cv[(size_t)c].Hc);
+      for (int64_t c = ch.c0; c < ch.c1; ++c) hs.push_back(cv[(size_t)c].Ht);
       std::sort(hs.begin(), hs.end());
       hs.erase(std::unique(hs.begin(), hs.end()), hs.end());
       for (int h : hs) lg.push_back({h, 0, 1});
@@ -842,7 +931,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       int64_t acc = 0;
       for (int64_t c = ch.c0; c < ch.c1; ++c) {
         const BCurve& b = cv[(size_t)c];
-        if (tpl_of_curve && b.Hc != g.H) {
+        if (tpl_of_curve && b.Ht != g.H) {
           cseg.push_back(-1);
           continue;
         }
@@ -865,6 +954,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       units.push_back(acc);
       L.nseg = (int)(segs.size() - L.seg_first);
       L.units = acc;
+      max_units = std::max(max_units, acc);
       ch.launches.push_back(L);
     }
   }
@@ -874,12 +964,42 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     curves[(size_t)c] = CurveDesc{b.t, b.y, b.dy, b.n, b.df, b.k0, b.redo_base, b.nf,
                                   b.out_off, b.Hc, b.ntc};
   }
-  // one descriptor blob: segs | units | curves | curve -> segment maps
+  // screening / features: per-curve descriptors and, per chunk, the row
+  // offsets of its curves (chunk q's ncurves + 1 entries start at c0 + q)
+  std::vector<ScreenCurve> scurves;
+  std::vector<int64_t> rowoff;
+  if (scr) {
+    scurves.resize((size_t)ncurves);
+    for (size_t q = 0; q < chunks.size(); ++q) {
+      int64_t items = 0;
+      for (int64_t c = chunks[q].c0; c < chunks[q].c1; ++c) {
+        const BCurve& b = cv[(size_t)c];
+        ScreenCurve& sc = scurves[(size_t)c];
+        sc.sums_off = b.sums_off;
+        sc.nf_pad = b.nf_pad;
+        sc.nf = b.nf;
+        sc.row_base = b.redo_base;
+        sc.out_row = feat_only ? scr->feat_row[c] : b.redo_base;
+        sc.nobs = b.n;
+        sc.item_base = items;
+        sc.out_off = b.out_off;
+        sc.Hs = b.Hc;
+        sc.curve = (int32_t)(c - chunks[q].c0);
+        items += (int64_t)b.ntc * b.nf;
+        rowoff.push_back(b.redo_base);
+      }
+      rowoff.push_back(chunks[q].nf_total);
+    }
+  }
+  // one descriptor blob: segs | units | curves | curve -> segment maps |
+  // screening curves | row offsets
   auto al64 = [](size_t x) { return (x + 63) / 64 * 64; };
   const size_t off_units = al64(segs.size() * sizeof(RootsSeg));
   const size_t off_curves = off_units + al64(units.size() * sizeof(int64_t));
   const size_t off_cseg = off_curves + al64(curves.size() * sizeof(CurveDesc));
-  const size_t blob = off_cseg + al64(cseg.size() * sizeof(int));
+  const size_t off_scur = off_cseg + al64(cseg.size() * sizeof(int));
+  const size_t off_rowoff = off_scur + al64(scurves.size() * sizeof(ScreenCurve));
+  const size_t blob = off_rowoff + al64(rowoff.size() * sizeof(int64_t));
 
   // ---- workspace (growing it drops a captured graph)
   st = grow_dev(reinterpret_cast<unsigned char**>(&P->d_bsums), &P->bsums_cap,
@@ -893,6 +1013,17 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
         dalloc(&P->d_bslot_curve, kBatchRedoCap) != FTP_OK || dalloc(&P->d_bcount, 1) != FTP_OK ||
         dalloc(&P->d_bredo_sums, (size_t)3 * P->max_H * kBatchRedoStride) != FTP_OK)
       st = FTP_ERR_OOM;
+  }
+  if (st == FTP_OK && scr && scr->mlp) {
+    const int nfeat = 2 * Hf + 2;
+    st = grow_dev(&P->d_bfeat, &P->bfeat_cap, (size_t)max_nf_total * nfeat, &grew);
+    if (st == FTP_OK) st = grow_dev(&P->d_bscore, &P->bscore_cap, (size_t)max_nf_total, &grew);
+    if (st == FTP_OK) st = grow_dev(&P->d_bsel, &P->bsel_cap, (size_t)max_nf_total, &grew);
+    if (st == FTP_OK) st = grow_dev(&P->d_bulist, &P->bulist_cap, (size_t)max_units, &grew);
+    if (st == FTP_OK && !P->d_bucount) {
+      grew = true;
+      st = dalloc(&P->d_bucount, 1);
+    }
   }
   if (st == FTP_OK && !out_dev) {
     st = grow_dev(&P->d_bout, &P->bout_cap, (size_t)4 * extent, &grew);
@@ -910,6 +1041,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   memcpy(P->h_bdesc + off_units, units.data(), units.size() * sizeof(int64_t));
   memcpy(P->h_bdesc + off_curves, curves.data(), curves.size() * sizeof(CurveDesc));
   memcpy(P->h_bdesc + off_cseg, cseg.data(), cseg.size() * sizeof(int));
+  memcpy(P->h_bdesc + off_scur, scurves.data(), scurves.size() * sizeof(ScreenCurve));
+  memcpy(P->h_bdesc + off_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t));
   // every FFT size first: making a plan may resize (and so synchronise) the work area
   for (const BCurve& b : cv) {
     cufftHandle h;
@@ -943,6 +1076,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   const int64_t* d_units = reinterpret_cast<const int64_t*>(P->d_bdesc + off_units);
   const CurveDesc* d_curves = reinterpret_cast<const CurveDesc*>(P->d_bdesc + off_curves);
   const int* d_cseg = reinterpret_cast<const int*>(P->d_bdesc + off_cseg);
+  const ScreenCurve* d_scur = reinterpret_cast<const ScreenCurve*>(P->d_bdesc + off_scur);
+  const int64_t* d_rowoff = reinterpret_cast<const int64_t*>(P->d_bdesc + off_rowoff);
   double* o[4] = {power, theta1, theta2, theta3};
   uint8_t* of = flags;
   if (!out_dev) {
@@ -972,6 +1107,14 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     key = fnv(key, P->h_alpha, sizeof(double2) * kMaxH * nbank);
     key = fnv(key, P->h_rows, sizeof(int) * nbank);
     key = fnv(key, &P->chunk_bytes, sizeof(P->chunk_bytes));
+    if (scr) {
+      const void* sp[] = {scr->feat_out, scr->mlp};
+      key = fnv(key, sp, sizeof(sp));
+      key = fnv(key, &scr->Hf, sizeof(scr->Hf));
+      key = fnv(key, &scr->top_frac, sizeof(scr->top_frac));
+      key = fnv(key, &scr->nbr, sizeof(scr->nbr));
+      if (scr->feat_row) key = fnv(key, scr->feat_row, sizeof(int64_t) * (size_t)ncurves);
+    }
     if (key == 0) key = 1;
   }
   P->last_graph = 0;
@@ -984,7 +1127,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     cudaGraph_t graph = nullptr;
     FTP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                              &launches);
+                              scr, d_scur, d_rowoff, &launches);
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     cudaGraphExec_t exec = nullptr;
     if (st == FTP_OK && ce == cudaSuccess && graph &&
@@ -1003,12 +1146,12 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       P->eager_key = 0;  // capture failed: stay eager for this call pattern
       launches = 0;
       st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                                &launches);
+                                scr, d_scur, d_rowoff, &launches);
       if (st != FTP_OK) return st;
     }
   } else {
     st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                              &launches);
+                              scr, d_scur, d_rowoff, &launches);
     if (st != FTP_OK) return st;
     if (graphable) P->eager_key = key;
   }
@@ -1090,7 +1233,8 @@ void ftp_destroy(ftp_plan_t P) {
   for (void* p : dptrs)
     if (p) cudaFree(p);
   void* bptrs[] = {P->d_bsums, P->d_bmom, P->d_bobs, P->d_bout, P->d_bflags, P->d_bmark,
-                   P->d_blist, P->d_bslot_curve, P->d_bcount, P->d_bredo_sums, P->d_bdesc};
+                   P->d_blist, P->d_bslot_curve, P->d_bcount, P->d_bredo_sums, P->d_bdesc,
+                   P->d_bfeat, P->d_bscore, P->d_bsel, P->d_bulist, P->d_bucount};
   for (void* p : bptrs)
     if (p) cudaFree(p);
   if (P->h_bdesc) cudaFreeHost(P->h_bdesc);
@@ -1350,7 +1494,39 @@ ftp_status ftp_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
                      const int32_t* tpl_of_curve, double* power, double* theta1, double* theta2,
                      double* theta3, uint8_t* flags) {
   return run_batch(P, ncurves, obs_off, t, y, dy, grids, out_off, bank, nbank, tpl_of_curve,
-                   power, theta1, theta2, theta3, flags);
+                   power, theta1, theta2, theta3, flags, nullptr);
+}
+
+ftp_status ftp_batch_features(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off,
+                              const double* t, const double* y, const double* dy,
+                              const ftp_grid* grids, const int64_t* row_off, int H_feat,
+                              float* features) {
+  if (!features || !row_off) return FTP_ERR_INVALID_ARG;
+  BatchScreen scr;
+  scr.Hf = H_feat;
+  scr.feat_out = features;
+  scr.feat_row = row_off;
+  return run_batch(P, ncurves, obs_off, t, y, dy, grids, nullptr, nullptr, 0, nullptr, nullptr,
+                   nullptr, nullptr, nullptr, nullptr, &scr);
+}
+
+ftp_status ftp_batch_screened(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off,
+                              const double* t, const double* y, const double* dy,
+                              const ftp_grid* grids, const int64_t* out_off,
+                              const ftp_template* bank, int nbank, const int32_t* tpl_of_curve,
+                              ftp_mlp_t mlp, double top_frac, int neighbours, double* power,
+                              double* theta1, double* theta2, double* theta3, uint8_t* flags) {
+  if (!P || !mlp || !(top_frac > 0.0) || !(top_frac <= 1.0) || neighbours < 0)
+    return FTP_ERR_INVALID_ARG;
+  const int nfeat = mlp_nfeat(mlp);
+  if (nfeat % 2 != 0 || mlp_device(mlp) != P->device) return FTP_ERR_INVALID_ARG;
+  BatchScreen scr;
+  scr.Hf = (nfeat - 2) / 2;
+  scr.mlp = mlp;
+  scr.top_frac = top_frac;
+  scr.nbr = neighbours;
+  return run_batch(P, ncurves, obs_off, t, y, dy, grids, out_off, bank, nbank, tpl_of_curve,
+                   power, theta1, theta2, theta3, flags, &scr);
 }
 
 ftp_status ftp_set_batch_options(ftp_plan_t P, int64_t chunk_bytes, int use_graph) {

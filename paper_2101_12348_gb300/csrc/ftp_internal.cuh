@@ -193,6 +193,11 @@ struct RootsArgs {
   const int* curve_seg;
   int ncurves;         // entries of curve_seg
   int64_t host_units;  // upper bound of the work units (grid sizing); 0: from nf
+  // batched main pass on a subset of its units (screening): unit u of this
+  // launch is unit unit_list[u] of the batched numbering, u < *unit_count;
+  // nullable (every unit)
+  const int64_t* unit_list;
+  const unsigned long long* unit_count;
 };
 
 // Kernel variants: float2 sums + FP32 Aberth (mixed), double2 sums + FP64

@@ -296,7 +296,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
   const int64_t nf = a.nf_dev ? (int64_t)min(*a.nf_dev, a.redo_cap > 0 ? a.redo_cap : *a.nf_dev)
                               : a.nf;
   const int64_t nkb = (nf + NGW - 1) / NGW;
-  const int64_t nunits = redo_pass ? nf * a.ntpl : batched ? a.seg_units[a.nseg] : nkb * a.ntpl;
+  const bool listed = batched && !redo_pass && a.unit_list != nullptr;
+  const int64_t nunits = redo_pass ? nf * a.ntpl
+                         : listed  ? (int64_t)*a.unit_count
+                         : batched ? a.seg_units[a.nseg]
+                                   : nkb * a.ntpl;
   const double* mom = a.moments;
   W ybar = w_of<W>(mom[MO_YBAR]), YY = w_of<W>(mom[MO_YY]);
   R YYr = (R)mom[MO_YY];
@@ -319,6 +323,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
   // seg_units[s] <= u.  Units only grow along a warp's queue, so `lo` is the
   // previous answer and the first probe usually settles it.
   auto find_seg = [&](int64_t u, int lo) -> int {
+    if (u < a.seg_units[lo]) lo = 0;  // listed units need not ascend
     if (u < a.seg_units[lo + 1]) return lo;
     int hi = a.nseg;
     while (hi - lo > 1) {
@@ -340,6 +345,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
       r.tl = (int)(u / nkb);
       r.kfirst = (u % nkb) * NGW;
     } else if (!redo_pass) {
+      if (listed) u = a.unit_list[u];
       r.seg = find_seg(u, hint);
       const int64_t local = u - a.seg_units[r.seg];
       const int64_t nkb_s = (a.segs[r.seg].nf + NGW - 1) / NGW;

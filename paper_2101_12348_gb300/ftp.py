@@ -27,6 +27,8 @@ FLAG_NONCONVERGED = 1
 FLAG_DEGENERATE_MM = 2
 FLAG_CONSTANT_P = 4
 FLAG_NEGATIVE_AMP = 8
+FLAG_UNRESOLVED = 16
+FLAG_SCREENED_OUT = 32
 
 STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE",
                 3: "FTP_ERR_MIXED_ZERO_SIGMA", 4: "FTP_ERR_NONFINITE", 5: "FTP_ERR_OOM",
@@ -36,7 +38,9 @@ STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE
 EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy",
            "ftp_status_string", "ftp_plan_info", "ftp_solver_stats", "ftp_set_timing",
            "ftp_stage_times", "ftp_periodogram_sums_noalloc", "ftp_set_batch_options",
-           "ftp_batch_info")
+           "ftp_batch_info", "ftp_mlp_param_count", "ftp_mlp_create", "ftp_mlp_destroy",
+           "ftp_mlp_get_params", "ftp_mlp_set_params", "ftp_mlp_forward", "ftp_mlp_gradient",
+           "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows")
 
 
 class FtpGrid(C.Structure):
@@ -88,9 +92,25 @@ def load(path: str | None = None) -> C.CDLL:
     lib.ftp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
     lib.ftp_set_batch_options.argtypes = [vp, i64, i32]
     lib.ftp_batch_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
+    u64, f32 = C.c_uint64, C.c_float
+    lib.ftp_mlp_param_count.argtypes = [i32]
+    lib.ftp_mlp_create.argtypes = [C.POINTER(vp), i32, vp, u64, i32, vp]
+    lib.ftp_mlp_destroy.argtypes = [vp]
+    lib.ftp_mlp_destroy.restype = None
+    lib.ftp_mlp_get_params.argtypes = [vp, vp]
+    lib.ftp_mlp_set_params.argtypes = [vp, vp]
+    lib.ftp_mlp_forward.argtypes = [vp, vp, i64, vp]
+    lib.ftp_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp]
+    lib.ftp_mlp_train.argtypes = [vp, vp, vp, i64, i64, i64, f32, u64, vp]
+    lib.ftp_batch_features.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(FtpGrid), vp, i32, vp]
+    lib.ftp_batch_screened.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(FtpGrid), vp,
+                                       C.POINTER(FtpTemplate), i32, vp, vp, dbl, i32, vp, vp, vp,
+                                       vp, vp]
+    lib.ftp_training_rows.argtypes = [vp, vp, i32, i64, vp, dbl, i32, dbl, u64, vp, vp, i64,
+                                      C.POINTER(i64), i32, vp]
     for name in EXPORTS:
-        if name not in ("ftp_destroy", "ftp_status_string"):
-            getattr(lib, name).restype = i32
+        if name not in ("ftp_destroy", "ftp_status_string", "ftp_mlp_destroy"):
+            getattr(lib, name).restype = i64 if name == "ftp_mlp_param_count" else i32
     if path is None:
         _lib = lib
     return lib
@@ -173,14 +193,101 @@ def ftp_batch(plan: int, obs_off, t, y, dy, grids, out_off, bank, tpl_of_curve, 
     bank: sequence of (c, s); tpl_of_curve: int32 host array or None."""
     obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
     out_off = np.ascontiguousarray(out_off, dtype=np.int64)
-    g = (FtpGrid * len(grids))()
-    for i, (df, k0, nf) in enumerate(grids):
-        g[i] = FtpGrid(float(df), int(k0), int(nf))
+    g = _grids(grids)
     arr, keep = _templates(bank)
     tpc = None if tpl_of_curve is None else np.ascontiguousarray(tpl_of_curve, dtype=np.int32)
     _check(load().ftp_batch(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t), _ptr(y), _ptr(dy),
                             g, _ptr(out_off), arr, len(keep) // 2, _ptr(tpc), _ptr(power),
                             _ptr(theta1), _ptr(theta2), _ptr(theta3), _ptr(flags)), "ftp_batch")
+
+
+def _grids(grids):
+    g = (FtpGrid * len(grids))()
+    for i, (df, k0, nf) in enumerate(grids):
+        g[i] = FtpGrid(float(df), int(k0), int(nf))
+    return g
+
+
+def ftp_batch_features(plan: int, obs_off, t, y, dy, grids, row_off, H_feat: int,
+                       features) -> None:
+    """Screening features of every frequency of every curve; features is a
+    device tensor [rows][2 H_feat + 2] (float32); row_off an int64 host array."""
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    row_off = np.ascontiguousarray(row_off, dtype=np.int64)
+    _check(load().ftp_batch_features(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t), _ptr(y),
+                                     _ptr(dy), _grids(grids), _ptr(row_off), int(H_feat),
+                                     _ptr(features)), "ftp_batch_features")
+
+
+def ftp_batch_screened(plan: int, obs_off, t, y, dy, grids, out_off, bank, tpl_of_curve,
+                       mlp: int, top_frac: float, neighbours: int, power, theta1, theta2, theta3,
+                       flags=None) -> None:
+    """ftp_batch with surrogate screening (arguments as ftp_batch plus the
+    network handle, the selected fraction and the neighbour half-width)."""
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    out_off = np.ascontiguousarray(out_off, dtype=np.int64)
+    arr, keep = _templates(bank)
+    tpc = None if tpl_of_curve is None else np.ascontiguousarray(tpl_of_curve, dtype=np.int32)
+    _check(load().ftp_batch_screened(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t), _ptr(y),
+                                     _ptr(dy), _grids(grids), _ptr(out_off), arr, len(keep) // 2,
+                                     _ptr(tpc), mlp, float(top_frac), int(neighbours),
+                                     _ptr(power), _ptr(theta1), _ptr(theta2), _ptr(theta3),
+                                     _ptr(flags)), "ftp_batch_screened")
+
+
+def ftp_mlp_param_count(nfeat: int) -> int:
+    return int(load().ftp_mlp_param_count(int(nfeat)))
+
+
+def ftp_mlp_create(nfeat: int, params=None, seed: int = 0, device: int = 0,
+                   stream: int | None = None) -> int:
+    h = C.c_void_p()
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().ftp_mlp_create(C.byref(h), int(nfeat), _ptr(p), int(seed) & (2**64 - 1),
+                                 int(device), stream), "ftp_mlp_create")
+    return h.value
+
+
+def ftp_mlp_destroy(mlp: int) -> None:
+    load().ftp_mlp_destroy(mlp)
+
+
+def ftp_mlp_get_params(mlp: int, out) -> None:
+    _check(load().ftp_mlp_get_params(mlp, _ptr(out)), "ftp_mlp_get_params")
+
+
+def ftp_mlp_set_params(mlp: int, params) -> None:
+    _check(load().ftp_mlp_set_params(mlp, _ptr(params)), "ftp_mlp_set_params")
+
+
+def ftp_mlp_forward(mlp: int, X, n: int, scores) -> None:
+    _check(load().ftp_mlp_forward(mlp, _ptr(X), int(n), _ptr(scores)), "ftp_mlp_forward")
+
+
+def ftp_mlp_gradient(mlp: int, X, target, rows: int, idx, n: int, grad=None, loss=None) -> None:
+    _check(load().ftp_mlp_gradient(mlp, _ptr(X), _ptr(target), int(rows), _ptr(idx), int(n),
+                                   _ptr(grad), _ptr(loss)), "ftp_mlp_gradient")
+
+
+def ftp_mlp_train(mlp: int, X, target, rows: int, steps: int, batch: int, lr: float, seed: int,
+                  losses=None) -> None:
+    _check(load().ftp_mlp_train(mlp, _ptr(X), _ptr(target), int(rows), int(steps), int(batch),
+                                float(lr), int(seed) & (2**64 - 1), _ptr(losses)),
+           "ftp_mlp_train")
+
+
+def ftp_training_rows(power, features, nfeat: int, row_off, top_frac: float, neighbours: int,
+                      rand_frac: float, seed: int, X_out, y_out, cap: int, count: int,
+                      device: int = 0, stream: int | None = None) -> int:
+    """Appends training rows (see include/ftp.h); returns the new row count."""
+    row_off = np.ascontiguousarray(row_off, dtype=np.int64)
+    c = C.c_int64(int(count))
+    _check(load().ftp_training_rows(_ptr(power), _ptr(features), int(nfeat), row_off.shape[0] - 1,
+                                    _ptr(row_off), float(top_frac), int(neighbours),
+                                    float(rand_frac), int(seed) & (2**64 - 1), _ptr(X_out),
+                                    _ptr(y_out), int(cap), C.byref(c), int(device), stream),
+           "ftp_training_rows")
+    return c.value
 
 
 def ftp_set_batch_options(plan: int, chunk_bytes: int = 0, use_graph: bool = True) -> None:

@@ -171,3 +171,20 @@ def test_bf16_network_stays_close_to_the_exact_one():
     s_x = so.forward(p, X, nfeat, bf16=False)["s"]
     assert np.max(np.abs(s_b - s_x)) < 0.05 * (1 + np.max(np.abs(s_x)))
     assert np.max(np.abs(s_b - s_x)) > 0  # the rounding points are really applied
+
+
+def test_bf16_gradient_stays_close_to_the_exact_one():
+    """The BF16 network's gradient (rounded forward values and rounded error
+    signals into the weight-gradient products) differs from the exact
+    network's by rounding only: each rounding perturbs one factor by at most
+    2^-8 relative, so the difference is a small fraction of the gradient, yet
+    non-zero (the rounding points are really applied)."""
+    nfeat = 10
+    rng = np.random.default_rng(11)
+    p = so.init_params(nfeat, seed=4)
+    X = rng.uniform(0, 1, (256, nfeat))
+    tgt = rng.uniform(0, 1, 256)
+    _, gb = so.loss_and_gradients(p, X, tgt, nfeat, bf16=True)
+    _, gx = so.loss_and_gradients(p, X, tgt, nfeat, bf16=False)
+    rel = np.linalg.norm(gb - gx) / np.linalg.norm(gx)
+    assert 0 < rel < 0.03
