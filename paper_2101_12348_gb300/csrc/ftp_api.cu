@@ -51,6 +51,30 @@ struct FftEntry {
   size_t work = 0;
 };
 
+// Workspace of one step (a) pipeline: ftp_batch runs the step (a) of
+// several curves at once, one lane each, on their own streams.  Lane 0 is the
+// plan's own workspace and stream; extra lanes own their buffers.
+struct SumLane {
+  cudaStream_t s = nullptr;
+  bool owned = false;  // buffers (and the stream) belong to this lane
+  unsigned char* mom_scratch = nullptr;
+  int* tile_count = nullptr;
+  int* tile_off = nullptr;
+  int* cursor = nullptr;
+  int* cell = nullptr;
+  int* cell_s = nullptr;
+  void* frac = nullptr;
+  void* frac_s = nullptr;
+  void* coef = nullptr;
+  void* coef_s = nullptr;
+  void* grid = nullptr;
+  void* fftwork = nullptr;
+  size_t fftwork_bytes = 0;
+  std::map<int64_t, FftEntry> ffts;
+  cudaEvent_t done = nullptr;  // end of the lane's share of a chunk
+};
+constexpr int kSumLanes = 4;
+
 }  // namespace
 
 struct ftp_plan_s {
@@ -97,9 +121,9 @@ struct ftp_plan_s {
   int* d_row0 = nullptr;    // a single 0: output row of one-template launches
   double* d_out = nullptr;  // staged outputs [4][max_templates][nf]
   uint8_t* d_flags = nullptr;
-  void* d_fftwork = nullptr;
-  size_t fftwork_bytes = 0;
-  std::map<int64_t, FftEntry> ffts;
+  SumLane l0;                     // step (a) on the plan's own workspace
+  std::vector<SumLane*> xlanes;   // extra step (a) lanes of ftp_batch (grown on demand)
+  cudaEvent_t fork = nullptr;     // start of a chunk's step (a), for the extra lanes
   // pinned host staging
   int* h_status = nullptr;
   unsigned long long* h_counters = nullptr;
@@ -211,9 +235,9 @@ ftp_status dalloc(T** p, size_t count) {
   return cuda_err(cudaMalloc((void**)p, count * sizeof(T)));
 }
 
-ftp_status get_fft(ftp_plan_t P, int64_t n, cufftHandle* out) {
-  auto it = P->ffts.find(n);
-  if (it != P->ffts.end()) {
+ftp_status get_fft(ftp_plan_t P, SumLane& L, int64_t n, cufftHandle* out) {
+  auto it = L.ffts.find(n);
+  if (it != L.ffts.end()) {
     *out = it->second.h;
     return FTP_OK;
   }
@@ -225,86 +249,84 @@ ftp_status get_fft(ftp_plan_t P, int64_t n, cufftHandle* out) {
     cufftDestroy(e.h);
     return FTP_ERR_CUDA;
   }
-  if (e.work > P->fftwork_bytes) {
+  if (e.work > L.fftwork_bytes) {
     // queued transforms may still use the old work area
-    if (P->stream) cudaStreamSynchronize(P->stream);
-    if (P->d_fftwork) cudaFree(P->d_fftwork);
-    P->d_fftwork = nullptr;
-    P->fftwork_bytes = 0;
-    if (cudaMalloc(&P->d_fftwork, e.work) != cudaSuccess) {
+    if (L.s) cudaStreamSynchronize(L.s);
+    if (L.fftwork) cudaFree(L.fftwork);
+    L.fftwork = nullptr;
+    L.fftwork_bytes = 0;
+    if (cudaMalloc(&L.fftwork, e.work) != cudaSuccess) {
       cufftDestroy(e.h);
       return FTP_ERR_OOM;
     }
-    P->fftwork_bytes = e.work;
-    for (auto& kv : P->ffts) cufftSetWorkArea(kv.second.h, P->d_fftwork);
+    L.fftwork_bytes = e.work;
+    for (auto& kv : L.ffts) cufftSetWorkArea(kv.second.h, L.fftwork);
   }
-  cufftSetWorkArea(e.h, P->d_fftwork);
-  P->ffts[n] = e;
+  cufftSetWorkArea(e.h, L.fftwork);
+  L.ffts[n] = e;
   *out = e.h;
   return FTP_OK;
 }
+ftp_status get_fft(ftp_plan_t P, int64_t n, cufftHandle* out) { return get_fft(P, P->l0, n, out); }
 
 void ev_rec(ftp_plan_t P, int i) {
   if (P->timing && !P->in_batch) cudaEventRecord(P->ev[i], P->stream);
 }
 
-// Step (a) for one curve: moments, binning, spreading, FFT, gather into the
-// sum tiles `sums` (layout [3 Hs][nf_pad]) and the moments block `moments`.
-// t, y, dy are device pointers; ngrid/ntiles give the NFFT grid (at most the
-// plan's).
-ftp_status run_sums(ftp_plan_t P, const double* t, const double* y, const double* dy,
+// Step (a) for one curve on lane L: moments, binning, spreading, FFT, gather
+// into the sum tiles `sums` (layout [3 Hs][nf_pad]) and the moments block
+// `moments`.  t, y, dy are device pointers; ngrid/ntiles give the NFFT grid
+// (at most the plan's).
+ftp_status run_sums(ftp_plan_t P, SumLane& L, const double* t, const double* y, const double* dy,
                     int64_t nobs, double df, int64_t k0, int64_t nf, int Hs, int64_t ngrid,
                     int64_t ntiles, double* moments, void* sums, int64_t nf_pad, int* launches) {
   if (ngrid > P->ngrid || ntiles > P->ntiles) return FTP_ERR_UNSUPPORTED;
   cufftHandle fft;
-  ftp_status st = get_fft(P, ngrid, &fft);
+  ftp_status st = get_fft(P, L, ngrid, &fft);
   if (st != FTP_OK) return st;
-  cudaStream_t s = P->stream;
+  cudaStream_t s = L.s;
   ev_rec(P, 0);
-  FTP_CK(cudaMemsetAsync(P->d_tile_count, 0, sizeof(int) * ntiles, s));
-  launch_moments(t, y, dy, nobs, moments, P->d_status, P->d_mom_scratch, s);
+  FTP_CK(cudaMemsetAsync(L.tile_count, 0, sizeof(int) * ntiles, s));
+  launch_moments(t, y, dy, nobs, moments, P->d_status, L.mom_scratch, s);
   if (P->mixed) {
-    launch_points<float>(t, y, dy, nobs, moments, P->d_status, df, ngrid, P->d_tile_count,
-                         P->d_cell, (float*)P->d_frac, (float2*)P->d_coef, s);
+    launch_points<float>(t, y, dy, nobs, moments, P->d_status, df, ngrid, L.tile_count, L.cell,
+                         (float*)L.frac, (float2*)L.coef, s);
   } else {
-    launch_points<double>(t, y, dy, nobs, moments, P->d_status, df, ngrid, P->d_tile_count,
-                          P->d_cell, (double*)P->d_frac, (double2*)P->d_coef, s);
+    launch_points<double>(t, y, dy, nobs, moments, P->d_status, df, ngrid, L.tile_count, L.cell,
+                          (double*)L.frac, (double2*)L.coef, s);
   }
-  launch_scan(P->d_tile_count, ntiles, P->d_tile_off, P->d_cursor, P->d_status, s);
+  launch_scan(L.tile_count, ntiles, L.tile_off, L.cursor, P->d_status, s);
   if (P->mixed) {
-    launch_scatter<float>(nobs, P->d_tile_off, P->d_cursor, P->d_cell, (float*)P->d_frac,
-                          (float2*)P->d_coef, P->d_cell_s, (float*)P->d_frac_s,
-                          (float2*)P->d_coef_s, P->d_status, s);
+    launch_scatter<float>(nobs, L.tile_off, L.cursor, L.cell, (float*)L.frac, (float2*)L.coef,
+                          L.cell_s, (float*)L.frac_s, (float2*)L.coef_s, P->d_status, s);
   } else {
-    launch_scatter<double>(nobs, P->d_tile_off, P->d_cursor, P->d_cell, (double*)P->d_frac,
-                           (double2*)P->d_coef, P->d_cell_s, (double*)P->d_frac_s,
-                           (double2*)P->d_coef_s, P->d_status, s);
+    launch_scatter<double>(nobs, L.tile_off, L.cursor, L.cell, (double*)L.frac, (double2*)L.coef,
+                           L.cell_s, (double*)L.frac_s, (double2*)L.coef_s, P->d_status, s);
   }
   ev_rec(P, 1);
   if (P->mixed) {
-    launch_spread<float>(P->d_tile_off, P->d_cell_s, (float*)P->d_frac_s, (float2*)P->d_coef_s,
-                         ngrid, ntiles, P->m, P->beta, (float2*)P->d_grid, P->d_status, s);
+    launch_spread<float>(L.tile_off, L.cell_s, (float*)L.frac_s, (float2*)L.coef_s, ngrid, ntiles,
+                         P->m, P->beta, (float2*)L.grid, P->d_status, s);
   } else {
-    launch_spread<double>(P->d_tile_off, P->d_cell_s, (double*)P->d_frac_s,
-                          (double2*)P->d_coef_s, ngrid, ntiles, P->m, P->beta,
-                          (double2*)P->d_grid, P->d_status, s);
+    launch_spread<double>(L.tile_off, L.cell_s, (double*)L.frac_s, (double2*)L.coef_s, ngrid,
+                          ntiles, P->m, P->beta, (double2*)L.grid, P->d_status, s);
   }
   ev_rec(P, 2);
   if (cufftSetStream(fft, s) != CUFFT_SUCCESS) return FTP_ERR_CUDA;
   cufftResult fr;
   if (P->mixed) {
-    fr = cufftExecC2C(fft, (cufftComplex*)P->d_grid, (cufftComplex*)P->d_grid, CUFFT_INVERSE);
+    fr = cufftExecC2C(fft, (cufftComplex*)L.grid, (cufftComplex*)L.grid, CUFFT_INVERSE);
   } else {
-    fr = cufftExecZ2Z(fft, (cufftDoubleComplex*)P->d_grid, (cufftDoubleComplex*)P->d_grid,
+    fr = cufftExecZ2Z(fft, (cufftDoubleComplex*)L.grid, (cufftDoubleComplex*)L.grid,
                       CUFFT_INVERSE);
   }
   if (fr != CUFFT_SUCCESS) return FTP_ERR_CUDA;
   ev_rec(P, 3);
   if (P->mixed) {
-    launch_gather<float>((const float2*)P->d_grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
+    launch_gather<float>((const float2*)L.grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
                          (float2*)sums, P->d_status, s);
   } else {
-    launch_gather<double>((const double2*)P->d_grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
+    launch_gather<double>((const double2*)L.grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
                           (double2*)sums, P->d_status, s);
   }
   ev_rec(P, 4);
@@ -319,7 +341,7 @@ ftp_status run_sums_plan(ftp_plan_t P, const double* t, const double* y, const d
   const int64_t J = 2 * (int64_t)Hs * (P->grid.k0 + P->grid.nf - 1);
   int64_t ntiles = 0;
   const int64_t ngrid = grid_len(J, P->sigma, &ntiles);
-  return run_sums(P, t, y, dy, nobs, P->grid.df, P->grid.k0, P->grid.nf, Hs, ngrid, ntiles,
+  return run_sums(P, P->l0, t, y, dy, nobs, P->grid.df, P->grid.k0, P->grid.nf, Hs, ngrid, ntiles,
                   P->d_moments, P->d_sums, P->nf_pad, launches);
 }
 
@@ -569,6 +591,59 @@ ftp_status grow_dev(T** p, size_t* cap, size_t count, bool* grew) {
   return FTP_OK;
 }
 
+void free_lane(SumLane* L) {
+  if (L->s) cudaStreamSynchronize(L->s);
+  for (auto& kv : L->ffts) cufftDestroy(kv.second.h);
+  L->ffts.clear();
+  if (L->fftwork) cudaFree(L->fftwork);
+  L->fftwork = nullptr;
+  if (!L->owned) return;
+  void* bufs[] = {L->mom_scratch, L->tile_count, L->tile_off, L->cursor, L->cell, L->cell_s,
+                  L->frac, L->frac_s, L->coef, L->coef_s, L->grid};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (L->done) cudaEventDestroy(L->done);
+  if (L->s) cudaStreamDestroy(L->s);
+}
+
+// Extra step (a) lanes up to `want` lanes in all (lane 0 is the plan's own),
+// each sized like the plan's workspace.  *grew is set when one is created.
+ftp_status ensure_lanes(ftp_plan_t P, int want, bool* grew) {
+  if (!P->fork && cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess)
+    return FTP_ERR_CUDA;
+  while ((int)P->xlanes.size() + 1 < want) {
+    SumLane* L = new SumLane();
+    L->owned = true;
+    const size_t nobs = (size_t)P->max_nobs;
+    bool ok = cudaStreamCreateWithFlags(&L->s, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming) == cudaSuccess &&
+              dalloc(&L->mom_scratch, kMomentScratchBytes) == FTP_OK &&
+              dalloc(&L->tile_count, (size_t)P->ntiles) == FTP_OK &&
+              dalloc(&L->tile_off, (size_t)P->ntiles + 1) == FTP_OK &&
+              dalloc(&L->cursor, (size_t)P->ntiles) == FTP_OK &&
+              dalloc(&L->cell, nobs) == FTP_OK && dalloc(&L->cell_s, nobs) == FTP_OK;
+    unsigned char* b[5] = {};
+    const size_t sizes[5] = {nobs * P->rsz, nobs * P->rsz, nobs * P->csz, nobs * P->csz,
+                             (size_t)P->ngrid * P->csz};
+    for (int i = 0; i < 5 && ok; ++i) ok = dalloc(&b[i], sizes[i]) == FTP_OK;
+    L->frac = b[0];
+    L->frac_s = b[1];
+    L->coef = b[2];
+    L->coef_s = b[3];
+    L->grid = b[4];
+    if (ok) ok = cudaMemset(L->mom_scratch, 0, kMomentScratchBytes) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      free_lane(L);
+      delete L;
+      return FTP_ERR_OOM;
+    }
+    P->xlanes.push_back(L);
+    *grew = true;
+  }
+  return FTP_OK;
+}
+
 struct BCurve {
   const double* t;  // device
   const double* y;
@@ -627,13 +702,27 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
   for (size_t q = 0; q < chunks.size(); ++q) {
     const BChunk& ch = chunks[q];
     if (tm) cudaEventRecord(P->bev[4 * q + 0], s);
+    // step (a) of the chunk's curves, round-robin over the lanes (fork/join
+    // through events, so a captured graph holds parallel branches)
+    const int used = (int)std::min<int64_t>(1 + (int64_t)P->xlanes.size(), ch.c1 - ch.c0);
+    if (used > 1) {
+      FTP_CK(cudaEventRecord(P->fork, s));
+      for (int l = 1; l < used; ++l) FTP_CK(cudaStreamWaitEvent(P->xlanes[l - 1]->s, P->fork, 0));
+    }
     for (int64_t c = ch.c0; c < ch.c1; ++c) {
       const BCurve& b = cv[(size_t)c];
-      ftp_status st = run_sums(P, b.t, b.y, b.dy, b.n, b.df, b.k0, b.nf, b.Hc, b.ngrid, b.ntiles,
-                               P->d_bmom + (size_t)(c - ch.c0) * MO_WORDS,
+      const int l = (int)((c - ch.c0) % used);
+      SumLane& L = l == 0 ? P->l0 : *P->xlanes[l - 1];
+      ftp_status st = run_sums(P, L, b.t, b.y, b.dy, b.n, b.df, b.k0, b.nf, b.Hc, b.ngrid,
+                               b.ntiles, P->d_bmom + (size_t)(c - ch.c0) * MO_WORDS,
                                (unsigned char*)P->d_bsums + (size_t)b.sums_off * P->csz,
                                b.nf_pad, launches);
       if (st != FTP_OK) return st;
+    }
+    for (int l = 1; l < used; ++l) {
+      SumLane& L = *P->xlanes[l - 1];
+      FTP_CK(cudaEventRecord(L.done, L.s));
+      FTP_CK(cudaStreamWaitEvent(s, L.done, 0));
     }
     if (tm) cudaEventRecord(P->bev[4 * q + 1], s);
     const bool screened = scr && scr->mlp;
@@ -1043,11 +1132,22 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   memcpy(P->h_bdesc + off_cseg, cseg.data(), cseg.size() * sizeof(int));
   memcpy(P->h_bdesc + off_scur, scurves.data(), scurves.size() * sizeof(ScreenCurve));
   memcpy(P->h_bdesc + off_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t));
-  // every FFT size first: making a plan may resize (and so synchronise) the work area
-  for (const BCurve& b : cv) {
-    cufftHandle h;
-    st = get_fft(P, b.ngrid, &h);
+  // step (a) lanes, then every FFT size on every lane that runs one: making a
+  // plan may resize (and so synchronise) a work area
+  {
+    int64_t most = 0;
+    for (const BChunk& ch : chunks) most = std::max(most, ch.c1 - ch.c0);
+    st = ensure_lanes(P, (int)std::min<int64_t>(kSumLanes, most), &grew);
     if (st != FTP_OK) return st;
+  }
+  for (const BChunk& ch : chunks) {
+    const int used = (int)std::min<int64_t>(1 + (int64_t)P->xlanes.size(), ch.c1 - ch.c0);
+    for (int64_t c = ch.c0; c < ch.c1; ++c) {
+      const int l = (int)((c - ch.c0) % used);
+      cufftHandle h;
+      st = get_fft(P, l == 0 ? P->l0 : *P->xlanes[l - 1], cv[(size_t)c].ngrid, &h);
+      if (st != FTP_OK) return st;
+    }
   }
   if (P->timing) {
     while (P->bev.size() < 4 * chunks.size()) {
@@ -1224,12 +1324,18 @@ void ftp_destroy(ftp_plan_t P) {
   cudaGetDevice(&prev);
   cudaSetDevice(P->device);
   if (P->stream) cudaStreamSynchronize(P->stream);
-  for (auto& kv : P->ffts) cufftDestroy(kv.second.h);
+  for (SumLane* L : P->xlanes) {
+    free_lane(L);
+    delete L;
+  }
+  P->xlanes.clear();
+  free_lane(&P->l0);
+  if (P->fork) cudaEventDestroy(P->fork);
   void* dptrs[] = {P->d_in, P->d_moments, P->d_mom_scratch, P->d_status, P->d_counters, P->d_queue, P->d_redo_list,
                    P->d_redo_mark, P->d_redo_count, P->d_redo_sums, P->d_tile_count, P->d_tile_off,
                    P->d_cursor, P->d_cell, P->d_cell_s, P->d_frac, P->d_frac_s, P->d_coef,
                    P->d_coef_s, P->d_grid, P->d_sums, P->d_alpha, P->d_rows, P->d_row0, P->d_out,
-                   P->d_flags, P->d_fftwork};
+                   P->d_flags};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   void* bptrs[] = {P->d_bsums, P->d_bmom, P->d_bobs, P->d_bout, P->d_bflags, P->d_bmark,
@@ -1361,6 +1467,18 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
     return fail(FTP_ERR_OOM);
   for (auto& e : P->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(FTP_ERR_CUDA);
+  P->l0.s = P->stream;
+  P->l0.mom_scratch = P->d_mom_scratch;
+  P->l0.tile_count = P->d_tile_count;
+  P->l0.tile_off = P->d_tile_off;
+  P->l0.cursor = P->d_cursor;
+  P->l0.cell = P->d_cell;
+  P->l0.cell_s = P->d_cell_s;
+  P->l0.frac = P->d_frac;
+  P->l0.frac_s = P->d_frac_s;
+  P->l0.coef = P->d_coef;
+  P->l0.coef_s = P->d_coef_s;
+  P->l0.grid = P->d_grid;
   cufftHandle h;
   st = get_fft(P, P->ngrid, &h);
   if (st != FTP_OK) return fail(st);

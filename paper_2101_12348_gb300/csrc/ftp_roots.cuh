@@ -238,6 +238,18 @@ template <int G, typename W> __device__ __forceinline__ W wsum(W v) {
   return v;
 }
 
+// An increasing function of arg(p) on [0, 2 pi) for |p| = 1 (values in [0, 4)):
+// orders candidate phases without an arctangent.
+template <typename T2>
+__device__ __forceinline__ auto pseudo_angle(T2 p) -> decltype(p.x) {
+  using T = decltype(p.x);
+  const T ax = p.x < T(0) ? -p.x : p.x, ay = p.y < T(0) ? -p.y : p.y;
+  const T q = ay / (ax + ay + T(1e-30));  // in [0, 1]
+  // quadrants I..IV map to [0,1), [1,2), [2,3), [3,4)
+  if (p.y >= T(0)) return p.x >= T(0) ? q : T(2) - q;
+  return p.x < T(0) ? T(2) + q : T(4) - q;
+}
+
 // Real trigonometric polynomial in the working precision, |psi| = 1:
 //   v0 + 2 Re sum_{e=1..n} c_e psi^e  (Horner in psi).
 template <typename T2, typename T>
@@ -249,7 +261,7 @@ __device__ __forceinline__ T trig_eval(const T2* c, int n, T2 psi, T v0) {
 }
 
 template <typename S2, typename R, int H, int G>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(const RootsArgs a) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(const RootsArgs a) {
   using namespace wide;
   using C = Cfg<S2, R, H, G>;
   using R2 = typename C::R2;
@@ -677,9 +689,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
         const R ym = trig_eval(Bw, H, ps[r], R(0));
         sc[r] = (mm > R(1e-9) * a0w) ? ym * ym / mm : R(0);
         pos[r] = ym > R(0);
-        R t2 = atan2(ps[r].y, ps[r].x);
-        if (t2 < R(0)) t2 += kTwoPi;
-        th[r] = t2;
+        th[r] = pseudo_angle(ps[r]);
         lmax = fmax(lmax, sc[r]);
       }
     }
@@ -708,7 +718,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 3) roots_kernel(cons
         bpsi = mk<R2>(ox, oy);
       }
     }
-    const R theta_w = (bkey < R(1e29)) ? (bkey >= R(16) ? bkey - R(16) : bkey) : R(0);
+    R theta_w = atan2(bpsi.y, bpsi.x);
+    if (theta_w < R(0)) theta_w += kTwoPi;
     // psi in wide precision, one Newton step onto |psi| = 1
     WC psi;
     if constexpr (C::kDD) {
