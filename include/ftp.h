@@ -153,7 +153,8 @@ ftp_status ftp_periodogram(ftp_plan_t plan, const double* t, const double* y, co
  *
  * Execution: the curves are cut into chunks whose sum tiles fit the plan's
  * chunk budget (ftp_set_batch_options; 8 GiB by default).  Per chunk, step
- * (a) runs curve by curve into the chunk's sum tiles, then steps (b)-(c) run
+ * (a) runs curve by curve, several curves at once on concurrent streams
+ * (ftp_set_batch_tuning), into the chunk's sum tiles, then steps (b)-(c) run
  * as one persistent kernel launch per harmonic count H over every
  * (frequency, template) item of every curve of the chunk, and the chunk's
  * ill-conditioned frequencies are re-solved from direct FP64 sums in one more
@@ -182,6 +183,34 @@ ftp_status ftp_batch(ftp_plan_t plan, int64_t ncurves, const int64_t* obs_off, c
  */
 ftp_status ftp_set_batch_options(ftp_plan_t plan, int64_t chunk_bytes, int use_graph);
 ftp_status ftp_batch_info(ftp_plan_t plan, int64_t* chunks, int* graph);
+
+/*
+ * Batch tuning.  Two choices of ftp_batch depend on the GPU and the shape of
+ * the batch: how many curves run step (a) at once (sum_lanes, 1..8: each lane
+ * has its own stream, workspace and FFT plans; default 4) and how many CTAs
+ * per SM the persistent root-finding launches use (roots_ctas_per_sm; 0 = as
+ * many as fit, the default).  ftp_set_batch_tuning / ftp_get_batch_tuning
+ * set and read them.
+ *
+ * ftp_batch_autotune - picks both by timing them on the given batch
+ * (arguments as ftp_batch; the outputs are used as scratch and overwritten):
+ * each lane count in {1, 2, 4, 8} by the device time of step (a), then each
+ * CTA count in {all that fit, 4, 3, 2} by the time of the root stage; the
+ * fastest (a later candidate must win by 3 % / 2 %) is kept for the plan.
+ * cache_path (nullable) names a JSON file of earlier results keyed by the
+ * device, precision, largest H, template mode and log2 classes of the curve
+ * count, median N_obs and median N_f: a cached class is applied without
+ * timing (*from_cache = 1), a new one is timed and added.  Costs about ten
+ * ftp_batch calls when it times.
+ */
+ftp_status ftp_set_batch_tuning(ftp_plan_t plan, int sum_lanes, int roots_ctas_per_sm);
+ftp_status ftp_get_batch_tuning(ftp_plan_t plan, int* sum_lanes, int* roots_ctas_per_sm);
+ftp_status ftp_batch_autotune(ftp_plan_t plan, int64_t ncurves, const int64_t* obs_off,
+                              const double* t, const double* y, const double* dy,
+                              const ftp_grid* grids, const int64_t* out_off,
+                              const ftp_template* bank, int nbank, const int32_t* tpl_of_curve,
+                              double* power, double* theta1, double* theta2, double* theta3,
+                              const char* cache_path, int* from_cache);
 
 /* Release the plan's device memory, cuFFT plan and owned stream.  NULL is a no-op. */
 void ftp_destroy(ftp_plan_t plan);

@@ -6,8 +6,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <fstream>
 #include <map>
 #include <new>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include "../../include/ftp.h"
@@ -73,7 +76,8 @@ struct SumLane {
   std::map<int64_t, FftEntry> ffts;
   cudaEvent_t done = nullptr;  // end of the lane's share of a chunk
 };
-constexpr int kSumLanes = 4;
+constexpr int kSumLanes = 4;     // default concurrent step (a) lanes of ftp_batch
+constexpr int kMaxSumLanes = 8;
 
 }  // namespace
 
@@ -124,6 +128,10 @@ struct ftp_plan_s {
   SumLane l0;                     // step (a) on the plan's own workspace
   std::vector<SumLane*> xlanes;   // extra step (a) lanes of ftp_batch (grown on demand)
   cudaEvent_t fork = nullptr;     // start of a chunk's step (a), for the extra lanes
+  // batch tuning knobs (ftp_batch_autotune): concurrent step (a) lanes and
+  // CTAs per SM of the persistent roots launches (0: as many as fit)
+  int sum_lanes = kSumLanes;
+  int roots_ctas_per_sm = 0;
   // pinned host staging
   int* h_status = nullptr;
   unsigned long long* h_counters = nullptr;
@@ -485,6 +493,7 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
   }
   a.maxit = P->maxit;
   a.polish_steps = P->polish_steps;
+  a.ctas_per_sm = P->roots_ctas_per_sm;
   FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), P->stream));
   const int r = launch_roots(kind, a, P->num_sms, P->stream);
   if (r == -1) return FTP_ERR_UNSUPPORTED;
@@ -704,7 +713,8 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
     if (tm) cudaEventRecord(P->bev[4 * q + 0], s);
     // step (a) of the chunk's curves, round-robin over the lanes (fork/join
     // through events, so a captured graph holds parallel branches)
-    const int used = (int)std::min<int64_t>(1 + (int64_t)P->xlanes.size(), ch.c1 - ch.c0);
+    const int used = (int)std::min<int64_t>(
+        std::min<int64_t>(1 + (int64_t)P->xlanes.size(), P->sum_lanes), ch.c1 - ch.c0);
     if (used > 1) {
       FTP_CK(cudaEventRecord(P->fork, s));
       for (int l = 1; l < used; ++l) FTP_CK(cudaStreamWaitEvent(P->xlanes[l - 1]->s, P->fork, 0));
@@ -795,6 +805,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.redo_tol = P->mixed ? kRedoTolF32 : kRedoTolF64;
       a.maxit = P->maxit;
       a.polish_steps = P->polish_steps;
+      a.ctas_per_sm = P->roots_ctas_per_sm;
       a.segs = d_segs + L.seg_first;
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;
@@ -848,6 +859,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.redo_cap = kBatchRedoCap;
       a.maxit = P->maxit;
       a.polish_steps = P->polish_steps;
+      a.ctas_per_sm = P->roots_ctas_per_sm;
       a.segs = d_segs + L.seg_first;
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;
@@ -1137,11 +1149,12 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   {
     int64_t most = 0;
     for (const BChunk& ch : chunks) most = std::max(most, ch.c1 - ch.c0);
-    st = ensure_lanes(P, (int)std::min<int64_t>(kSumLanes, most), &grew);
+    st = ensure_lanes(P, (int)std::min<int64_t>(P->sum_lanes, most), &grew);
     if (st != FTP_OK) return st;
   }
   for (const BChunk& ch : chunks) {
-    const int used = (int)std::min<int64_t>(1 + (int64_t)P->xlanes.size(), ch.c1 - ch.c0);
+    const int used = (int)std::min<int64_t>(
+        std::min<int64_t>(1 + (int64_t)P->xlanes.size(), P->sum_lanes), ch.c1 - ch.c0);
     for (int64_t c = ch.c0; c < ch.c1; ++c) {
       const int l = (int)((c - ch.c0) % used);
       cufftHandle h;
@@ -1207,6 +1220,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     key = fnv(key, P->h_alpha, sizeof(double2) * kMaxH * nbank);
     key = fnv(key, P->h_rows, sizeof(int) * nbank);
     key = fnv(key, &P->chunk_bytes, sizeof(P->chunk_bytes));
+    key = fnv(key, &P->sum_lanes, sizeof(P->sum_lanes));
+    key = fnv(key, &P->roots_ctas_per_sm, sizeof(P->roots_ctas_per_sm));
     if (scr) {
       const void* sp[] = {scr->feat_out, scr->mlp};
       key = fnv(key, sp, sizeof(sp));
@@ -1645,6 +1660,157 @@ ftp_status ftp_batch_screened(ftp_plan_t P, int64_t ncurves, const int64_t* obs_
   scr.nbr = neighbours;
   return run_batch(P, ncurves, obs_off, t, y, dy, grids, out_off, bank, nbank, tpl_of_curve,
                    power, theta1, theta2, theta3, flags, &scr);
+}
+
+ftp_status ftp_set_batch_tuning(ftp_plan_t P, int sum_lanes, int roots_ctas_per_sm) {
+  if (!P || sum_lanes < 1 || sum_lanes > kMaxSumLanes || roots_ctas_per_sm < 0)
+    return FTP_ERR_INVALID_ARG;
+  P->sum_lanes = sum_lanes;
+  P->roots_ctas_per_sm = roots_ctas_per_sm;
+  return FTP_OK;
+}
+
+ftp_status ftp_get_batch_tuning(ftp_plan_t P, int* sum_lanes, int* roots_ctas_per_sm) {
+  if (!P) return FTP_ERR_INVALID_ARG;
+  if (sum_lanes) *sum_lanes = P->sum_lanes;
+  if (roots_ctas_per_sm) *roots_ctas_per_sm = P->roots_ctas_per_sm;
+  return FTP_OK;
+}
+
+ftp_status ftp_batch_autotune(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off,
+                              const double* t, const double* y, const double* dy,
+                              const ftp_grid* grids, const int64_t* out_off,
+                              const ftp_template* bank, int nbank, const int32_t* tpl_of_curve,
+                              double* power, double* theta1, double* theta2, double* theta3,
+                              const char* cache_path, int* from_cache) {
+  if (!P || ncurves < 1 || !obs_off || !grids || !bank || nbank < 1) return FTP_ERR_INVALID_ARG;
+  // shape class of the batch: device, precision, harmonics, and log2 buckets
+  // of the curve count, the median observation count and the median grid size
+  std::vector<int64_t> nobs((size_t)ncurves), nfs((size_t)ncurves);
+  for (int64_t c = 0; c < ncurves; ++c) {
+    nobs[(size_t)c] = obs_off[c + 1] - obs_off[c];
+    nfs[(size_t)c] = grids[c].nf;
+  }
+  std::nth_element(nobs.begin(), nobs.begin() + ncurves / 2, nobs.end());
+  std::nth_element(nfs.begin(), nfs.begin() + ncurves / 2, nfs.end());
+  auto lg = [](int64_t v) {
+    int b = 0;
+    while (v > 1) {
+      v >>= 1;
+      ++b;
+    }
+    return b;
+  };
+  int Hmax = 0;
+  for (int i = 0; i < nbank; ++i) Hmax = std::max(Hmax, bank[i].H);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, P->device);
+  std::string dev(prop.name);
+  for (char& ch : dev)
+    if (ch == '"' || ch == '\\' || ch == '\n') ch = '_';
+  std::ostringstream ks;
+  ks << dev << "/sm" << prop.multiProcessorCount << "/" << (P->mixed ? "mixed" : "fp64") << "/H"
+     << Hmax << "/" << (tpl_of_curve ? "per-curve" : "bank") << "/c" << lg(ncurves) << "/n"
+     << lg(nobs[(size_t)ncurves / 2]) << "/f" << lg(nfs[(size_t)ncurves / 2]);
+  const std::string key = ks.str();
+  if (from_cache) *from_cache = 0;
+  // cache: one entry per line, "key": {"sum_lanes": L, "roots_ctas_per_sm": C, ...}
+  std::vector<std::string> lines;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      const size_t q0 = line.find('"'), q1 = q0 == std::string::npos ? q0 : line.find('"', q0 + 1);
+      if (q1 == std::string::npos) continue;
+      const std::string k = line.substr(q0 + 1, q1 - q0 - 1);
+      int L = 0, Cc = -1;
+      const size_t pl = line.find("\"sum_lanes\":"), pc = line.find("\"roots_ctas_per_sm\":");
+      if (pl == std::string::npos || pc == std::string::npos) continue;
+      if (sscanf(line.c_str() + pl + 12, " %d", &L) != 1 ||
+          sscanf(line.c_str() + pc + 20, " %d", &Cc) != 1)
+        continue;
+      if (k == key && L >= 1 && L <= kMaxSumLanes && Cc >= 0) {
+        P->sum_lanes = L;
+        P->roots_ctas_per_sm = Cc;
+        if (from_cache) *from_cache = 1;
+        return FTP_OK;
+      }
+      if (k != key) lines.push_back(line);
+    }
+  }
+  // time the choices on this batch (eager calls with stage events)
+  const bool timing0 = P->timing;
+  const int lanes0 = P->sum_lanes, ctas0 = P->roots_ctas_per_sm;
+  P->timing = true;
+  auto once = [&](float* sa, float* sr) -> ftp_status {
+    ftp_status st = run_batch(P, ncurves, obs_off, t, y, dy, grids, out_off, bank, nbank,
+                              tpl_of_curve, power, theta1, theta2, theta3, nullptr, nullptr);
+    if (st == FTP_OK) {
+      *sa = P->stage_ms[0];
+      *sr = P->stage_ms[4];
+    }
+    return st;
+  };
+  float sa = 0.f, sr = 0.f;
+  std::ostringstream rec;
+  ftp_status st = FTP_OK;
+  int best_l = lanes0;
+  float best_a = 3e38f;
+  rec << "\"step_a_ms\": {";
+  for (int L : {1, 2, 4, 8}) {
+    P->sum_lanes = L;
+    st = once(&sa, &sr);  // warm-up: lanes and FFT plans
+    if (st == FTP_OK) st = once(&sa, &sr);
+    if (st != FTP_OK) break;
+    rec << (L == 1 ? "" : ", ") << "\"" << L << "\": " << sa;
+    if (sa < 0.97f * best_a) {
+      best_a = sa;
+      best_l = L;
+    }
+  }
+  rec << "}, \"roots_ms\": {";
+  int best_c = ctas0;
+  float best_r = 3e38f;
+  if (st == FTP_OK) {
+    P->sum_lanes = best_l;
+    for (int Cc : {0, 4, 3, 2}) {
+      P->roots_ctas_per_sm = Cc;
+      st = once(&sa, &sr);
+      if (st != FTP_OK) break;
+      rec << (Cc == 0 ? "" : ", ") << "\"" << Cc << "\": " << sr;
+      if (sr < 0.98f * best_r) {
+        best_r = sr;
+        best_c = Cc;
+      }
+    }
+  }
+  rec << "}";
+  P->timing = timing0;
+  if (st != FTP_OK) {
+    P->sum_lanes = lanes0;
+    P->roots_ctas_per_sm = ctas0;
+    return st;
+  }
+  P->sum_lanes = best_l;
+  P->roots_ctas_per_sm = best_c;
+  if (cache_path) {
+    std::ostringstream e;
+    e << "  \"" << key << "\": {\"sum_lanes\": " << best_l << ", \"roots_ctas_per_sm\": " << best_c
+      << ", " << rec.str() << "}";
+    std::vector<std::string> keep;
+    for (const std::string& l : lines) {
+      std::string x = l;
+      while (!x.empty() && (x.back() == ',' || x.back() == ' ')) x.pop_back();
+      if (x.find("\"sum_lanes\":") != std::string::npos) keep.push_back(x);
+    }
+    keep.push_back(e.str());
+    std::ofstream out(cache_path, std::ios::trunc);
+    if (!out) return FTP_ERR_INVALID_ARG;
+    out << "{\n";
+    for (size_t i = 0; i < keep.size(); ++i) out << keep[i] << (i + 1 < keep.size() ? ",\n" : "\n");
+    out << "}\n";
+  }
+  return FTP_OK;
 }
 
 ftp_status ftp_set_batch_options(ftp_plan_t P, int64_t chunk_bytes, int use_graph) {

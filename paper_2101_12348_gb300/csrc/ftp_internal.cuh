@@ -198,6 +198,7 @@ struct RootsArgs {
   // nullable (every unit)
   const int64_t* unit_list;
   const unsigned long long* unit_count;
+  int ctas_per_sm;  // persistent grid: CTAs per SM (0 or more than fit: as many as fit)
 };
 
 // Kernel variants: float2 sums + FP32 Aberth (mixed), double2 sums + FP64

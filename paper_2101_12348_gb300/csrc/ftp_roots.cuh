@@ -939,7 +939,9 @@ int launch_h(const RootsArgs& a, int num_sms, cudaStream_t s) {
   }
   const int64_t nf = a.nf;  // upper bound when the count lives on the device
   const int64_t nunits = a.host_units > 0 ? a.host_units : (nf + C::NGW - 1) / C::NGW * a.ntpl;
-  int64_t grid = (int64_t)num_sms * blocks_per_sm;
+  const int bps = (a.ctas_per_sm > 0 && a.ctas_per_sm < blocks_per_sm) ? a.ctas_per_sm
+                                                                       : blocks_per_sm;
+  int64_t grid = (int64_t)num_sms * bps;
   const int64_t need = (nunits + C::WARPS - 1) / C::WARPS;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;

@@ -40,7 +40,8 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_stage_times", "ftp_periodogram_sums_noalloc", "ftp_set_batch_options",
            "ftp_batch_info", "ftp_mlp_param_count", "ftp_mlp_create", "ftp_mlp_destroy",
            "ftp_mlp_get_params", "ftp_mlp_set_params", "ftp_mlp_forward", "ftp_mlp_gradient",
-           "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows")
+           "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows",
+           "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune")
 
 
 class FtpGrid(C.Structure):
@@ -108,6 +109,11 @@ def load(path: str | None = None) -> C.CDLL:
                                        vp, vp]
     lib.ftp_training_rows.argtypes = [vp, vp, i32, i64, vp, dbl, i32, dbl, u64, vp, vp, i64,
                                       C.POINTER(i64), i32, vp]
+    lib.ftp_set_batch_tuning.argtypes = [vp, i32, i32]
+    lib.ftp_get_batch_tuning.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    lib.ftp_batch_autotune.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(FtpGrid), vp,
+                                       C.POINTER(FtpTemplate), i32, vp, vp, vp, vp, vp,
+                                       C.c_char_p, C.POINTER(i32)]
     for name in EXPORTS:
         if name not in ("ftp_destroy", "ftp_status_string", "ftp_mlp_destroy"):
             getattr(lib, name).restype = i64 if name == "ftp_mlp_param_count" else i32
@@ -288,6 +294,37 @@ def ftp_training_rows(power, features, nfeat: int, row_off, top_frac: float, nei
                                     _ptr(y_out), int(cap), C.byref(c), int(device), stream),
            "ftp_training_rows")
     return c.value
+
+
+def ftp_set_batch_tuning(plan: int, sum_lanes: int, roots_ctas_per_sm: int = 0) -> None:
+    _check(load().ftp_set_batch_tuning(plan, int(sum_lanes), int(roots_ctas_per_sm)),
+           "ftp_set_batch_tuning")
+
+
+def ftp_get_batch_tuning(plan: int) -> dict:
+    a, b = C.c_int(), C.c_int()
+    _check(load().ftp_get_batch_tuning(plan, C.byref(a), C.byref(b)), "ftp_get_batch_tuning")
+    return {"sum_lanes": a.value, "roots_ctas_per_sm": b.value}
+
+
+def ftp_batch_autotune(plan: int, obs_off, t, y, dy, grids, out_off, bank, tpl_of_curve, power,
+                       theta1, theta2, theta3, cache_path: str | None = None) -> dict:
+    """Times the batch tuning choices on this batch (outputs are scratch) or
+    applies a cached result; returns the chosen settings and whether they
+    came from the cache."""
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    out_off = np.ascontiguousarray(out_off, dtype=np.int64)
+    arr, keep = _templates(bank)
+    tpc = None if tpl_of_curve is None else np.ascontiguousarray(tpl_of_curve, dtype=np.int32)
+    fc = C.c_int()
+    _check(load().ftp_batch_autotune(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t), _ptr(y),
+                                     _ptr(dy), _grids(grids), _ptr(out_off), arr, len(keep) // 2,
+                                     _ptr(tpc), _ptr(power), _ptr(theta1), _ptr(theta2),
+                                     _ptr(theta3), None if cache_path is None else
+                                     os.fsencode(cache_path), C.byref(fc)), "ftp_batch_autotune")
+    r = ftp_get_batch_tuning(plan)
+    r["from_cache"] = bool(fc.value)
+    return r
 
 
 def ftp_set_batch_options(plan: int, chunk_bytes: int = 0, use_graph: bool = True) -> None:

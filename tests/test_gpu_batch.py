@@ -202,3 +202,45 @@ def test_batch_survey_scale_sampled(ftp):
                                         np.argsort(-pc)[:5]]))
         ref = oracle.periodogram(lc.t, lc.y, lc.dy, g.freqs()[sel], tp.c, tp.s)
         assert np.max(np.abs(pc[sel] - ref["power"])) <= TOL_P["mixed"]
+
+
+def test_batch_autotune_and_tuning_knobs(ftp, tmp_path):
+    """ftp_batch_autotune times the step (a) lane count and the roots grid on
+    the batch, keeps the fastest, writes them to the JSON cache, and a second
+    plan applies the cached choice without timing; every setting gives results
+    within the parity tolerance."""
+    import json
+    off, t, y, dy, grids, bank, tpc = mixed_survey()
+    grid_t = [(g.df, g.k0, g.nf) for g in grids]
+    out_off = np.zeros(len(grids) + 1, dtype=np.int64)
+    out_off[1:] = np.cumsum([g.nf for g in grids])
+    tot = int(out_off[-1])
+    bk = [(b.c, b.s) for b in bank]
+    cache = str(tmp_path / "ftp_tuning.json")
+    outs = [np.empty(tot) for _ in range(4)]
+    with plan_for(ftp, off, grids, bank, "mixed") as plan:
+        assert ftp.ftp_get_batch_tuning(plan.h) == {"sum_lanes": 4, "roots_ctas_per_sm": 0}
+        r1 = ftp.ftp_batch_autotune(plan.h, off, t, y, dy, grid_t, out_off[:-1], bk, tpc, *outs,
+                                    cache_path=cache)
+        assert not r1["from_cache"]
+        assert r1["sum_lanes"] in (1, 2, 4, 8) and r1["roots_ctas_per_sm"] in (0, 2, 3, 4)
+        entries = json.load(open(cache))
+        assert len(entries) == 1
+        (rec,) = entries.values()
+        assert rec["sum_lanes"] == r1["sum_lanes"]
+        assert set(rec["step_a_ms"]) == {"1", "2", "4", "8"}
+        ftp.ftp_batch(plan.h, off, t, y, dy, grid_t, out_off[:-1], bk, tpc, *outs)
+        check_curves(off, t, y, dy, grids, bank, tpc, outs[0], out_off, "mixed", theta2=outs[2])
+        for lanes, ctas in ((1, 2), (8, 3)):
+            ftp.ftp_set_batch_tuning(plan.h, lanes, ctas)
+            o2 = [np.empty(tot) for _ in range(4)]
+            ftp.ftp_batch(plan.h, off, t, y, dy, grid_t, out_off[:-1], bk, tpc, *o2)
+            check_curves(off, t, y, dy, grids, bank, tpc, o2[0], out_off, "mixed", theta2=o2[2])
+        with pytest.raises(ftp.FtpError):
+            ftp.ftp_set_batch_tuning(plan.h, 9, 0)
+    with plan_for(ftp, off, grids, bank, "mixed") as plan2:
+        r2 = ftp.ftp_batch_autotune(plan2.h, off, t, y, dy, grid_t, out_off[:-1], bk, tpc, *outs,
+                                    cache_path=cache)
+        assert r2["from_cache"]
+        assert (r2["sum_lanes"], r2["roots_ctas_per_sm"]) == (r1["sum_lanes"],
+                                                              r1["roots_ctas_per_sm"])
