@@ -390,41 +390,78 @@ __global__ void __launch_bounds__(256) spread_kernel(const int* __restrict__ off
 //   Gw[j] = (X[j] + conj X[n-j]) / 2,  Gy[j] = (X[j] - conj X[n-j]) / (2 i),
 // each divided by the Kaiser-Bessel transform
 //   phihat(nu) = 2 m sinh(sqrt(beta^2 - (2 pi m nu)^2)) / sqrt(...), nu = j/n.
+// Tiled by grid index: a CTA reads a tile of T consecutive j (and the mirrored
+// n - j) once, coalesced, deconvolves it into shared memory, then for each
+// harmonic h writes Z_h(k) (and Y_h(k), h <= Hs) for the consecutive K with
+// h K inside the tile - coalesced writes, strided reads from shared memory.
+// Every grid value is read once instead of once per harmonic that needs it.
+template <typename R> struct GatherTile;
+template <> struct GatherTile<float> { static constexpr int T = 2048; };
+template <> struct GatherTile<double> { static constexpr int T = 1024; };
+
 template <typename R>
-__global__ void gather_kernel(const typename C2<R>::type* __restrict__ X, int64_t ngrid,
-                              int64_t k0, int64_t nf, int64_t nf_pad, int Hs, int m, double beta,
-                              typename C2<R>::type* __restrict__ sums,
-                              const int* __restrict__ status) {
+__global__ void __launch_bounds__(256) gather_kernel(const typename C2<R>::type* __restrict__ X,
+                                                     int64_t ngrid, int64_t k0, int64_t nf,
+                                                     int64_t nf_pad, int Hs, int m, double beta,
+                                                     typename C2<R>::type* __restrict__ sums,
+                                                     const int* __restrict__ status) {
   using Cx = typename C2<R>::type;
+  constexpr int T = GatherTile<R>::T;
+  __shared__ Cx sw[T], sy[T];
+  __shared__ int64_t kb[2 * kMaxH][2];  // K range of each harmonic in the tile
   if (status[ST_CODE] != DEV_OK) return;
-  const int h = blockIdx.y + 1;
-  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nf_pad) return;
-  if (k >= nf) {  // row padding read by whole work units: zeros
+  const int H2 = 2 * Hs;
+  const int64_t K1 = k0 + nf - 1;  // largest K
+  const int64_t jlo = k0, jhi = (int64_t)H2 * K1;
+  const int64_t ntiles = (jhi - jlo) / T + 1;
+  // row padding [nf, nf_pad) read by whole work units: zeros
+  const int64_t npad = nf_pad - nf;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)3 * Hs * npad;
+       q += (int64_t)gridDim.x * blockDim.x) {
     Cx zero;
     zero.x = R(0);
     zero.y = R(0);
-    sums[(int64_t)(h - 1) * nf_pad + k] = zero;
-    if (h <= Hs) sums[(int64_t)(2 * Hs + h - 1) * nf_pad + k] = zero;
-    return;
+    sums[(q / npad) * nf_pad + nf + q % npad] = zero;
   }
-  const int64_t j = (int64_t)h * (k0 + k);
-  const Cx xp = X[j];
-  const Cx xm = X[ngrid - j];
-  // nu = j/n and the window transform in the working precision: its relative
-  // error is at the rounding level of the sums themselves
-  const R nu = (R)j / (R)ngrid;
-  const R a = R(6.283185307179586476925286766559) * (R)m * nu;
   const R bt = (R)beta;
-  const R z = sqrt(bt * bt - a * a);
-  const R inv = z / (R(2 * m) * sinh(z));
-  Cx gw, gy;
-  gw.x = R(0.5) * (xp.x + xm.x) * inv;
-  gw.y = R(0.5) * (xp.y - xm.y) * inv;
-  gy.x = R(0.5) * (xp.y + xm.y) * inv;
-  gy.y = -R(0.5) * (xp.x - xm.x) * inv;
-  sums[(int64_t)(h - 1) * nf_pad + k] = gw;
-  if (h <= Hs) sums[(int64_t)(2 * Hs + h - 1) * nf_pad + k] = gy;
+  const R c2m = R(6.283185307179586476925286766559) * (R)m / (R)ngrid;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t J0 = jlo + tile * T;
+    const int64_t J1 = J0 + T - 1 < jhi ? J0 + T - 1 : jhi;  // inclusive
+    __syncthreads();  // the previous tile's shared values are consumed
+    if ((int)threadIdx.x < H2) {
+      const int64_t h = threadIdx.x + 1;
+      const int64_t lo = (J0 + h - 1) / h, hi = J1 / h;
+      kb[threadIdx.x][0] = lo > k0 ? lo : k0;
+      kb[threadIdx.x][1] = hi < K1 ? hi : K1;
+    }
+    for (int i = threadIdx.x; i <= (int)(J1 - J0); i += blockDim.x) {
+      const int64_t j = J0 + i;
+      const Cx xp = X[j];
+      const Cx xm = X[ngrid - j];
+      // the window transform in the working precision: its relative error is
+      // at the rounding level of the sums themselves
+      const R a = c2m * (R)j;
+      const R z = sqrt(bt * bt - a * a);
+      const R inv = z / (R(2 * m) * sinh(z));
+      Cx gw, gy;
+      gw.x = R(0.5) * (xp.x + xm.x) * inv;
+      gw.y = R(0.5) * (xp.y - xm.y) * inv;
+      gy.x = R(0.5) * (xp.y + xm.y) * inv;
+      gy.y = -R(0.5) * (xp.x - xm.x) * inv;
+      sw[i] = gw;
+      sy[i] = gy;
+    }
+    __syncthreads();
+    for (int h = 1; h <= H2; ++h) {
+      const int64_t lo = kb[h - 1][0], hi = kb[h - 1][1];
+      for (int64_t K = lo + threadIdx.x; K <= hi; K += blockDim.x) {
+        const int i = (int)(h * K - J0);
+        sums[(int64_t)(h - 1) * nf_pad + (K - k0)] = sw[i];
+        if (h <= Hs) sums[(int64_t)(H2 + h - 1) * nf_pad + (K - k0)] = sy[i];
+      }
+    }
+  }
 }
 
 
@@ -649,8 +686,11 @@ template <typename R>
 void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int64_t nf,
                    int64_t nf_pad, int Hs, int m, double beta, typename C2<R>::type* sums,
                    const int* status, cudaStream_t s) {
-  dim3 g((unsigned)((nf_pad + 255) / 256), (unsigned)(2 * Hs));
-  gather_kernel<R><<<g, 256, 0, s>>>(X, ngrid, k0, nf, nf_pad, Hs, m, beta, sums, status);
+  const int64_t ntiles = ((int64_t)2 * Hs * (k0 + nf - 1) - k0) / GatherTile<R>::T + 1;
+  int64_t blocks = ntiles < 152 * 6 ? ntiles : 152 * 6;
+  if (blocks < 1) blocks = 1;
+  gather_kernel<R><<<(unsigned)blocks, 256, 0, s>>>(X, ngrid, k0, nf, nf_pad, Hs, m, beta, sums,
+                                                    status);
 }
 
 #define FTP_INST(R)                                                                            \
