@@ -58,10 +58,14 @@ def parse_args():
                     help="timed steps of the FP64 path (0 skips it)")
     ap.add_argument("--n-freq", type=int, default=250_000,
                     help="frequencies of the grid (smaller only for profiling captures)")
-    ap.add_argument("--workload", choices=["long", "survey", "bank", "screen"], default="long",
+    ap.add_argument("--workload", choices=["long", "survey", "bank", "screen", "small", "hsweep"],
+                    default="long",
                     help="long: one long lightcurve (the headline line); survey: 4096 "
                          "curves batched; bank: 32 templates over one N=1e5 lightcurve; "
-                         "screen: surrogate-screened survey vs exhaustive, with training")
+                         "screen: surrogate-screened survey vs exhaustive, with training; "
+                         "small: the N=200, H=3, 5000-frequency curve, GPU vs the oracle's "
+                         "CPU seconds on the whole grid; hsweep: time per evaluation vs H "
+                         "on the long curve")
     ap.add_argument("--ncurves", type=int, default=4096, help="curves of the survey workload")
     ap.add_argument("--train-curves", type=int, default=50_000,
                     help="training curves of the screen workload")
@@ -675,6 +679,124 @@ def run_bank(args, world, rank, local, pg):
         print(json.dumps(result), flush=True)
 
 
+SMALL = ("single small lightcurve: N_obs=200 uniform in [0,30] d, H=3 template, "
+         "f_k=k/150, k=1..5000; metric of this configuration: oracle CPU seconds")
+
+
+def run_small(args, world, rank, local, pg):
+    """The small curve: the whole grid on the GPU (mixed and FP64 paths) and
+    on the CPU oracle (one process, and a spawn pool over every core), with
+    |dP| against the oracle on every frequency."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_2101_12348_gb300 import ftp
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lc, tpl, grid = synth.small_curve()
+    nf = grid.nf
+    tpls = [(tpl.c, tpl.s)]
+    dt_, dy_, ds_ = (torch.from_numpy(a).to(dev) for a in (lc.t, lc.y, lc.dy))
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for prec in ("mixed", "fp64"):
+        plan = ftp.ftp_plan(lc.t.size, tpl.H, (grid.df, grid.k0, nf), 1, prec, local,
+                            stream.cuda_stream)
+        outs = [torch.empty(nf, dtype=torch.float64, device=dev) for _ in range(4)]
+
+        def call():
+            ftp.ftp_periodogram(plan, dt_, dy_, ds_, lc.t.size, tpls, *outs, None)
+
+        for _ in range(max(3, args.warmup)):
+            call()
+        ms = _timed_calls(stream, flush, args.steps, call)
+        res[prec] = (ms, outs[0].cpu().numpy())
+        ftp.ftp_destroy(plan)
+    freqs = grid.freqs()
+    one_s, _ = oracle_timing(lc, tpl, freqs[: max(1, nf // 10)], 1)  # a tenth, scaled
+    one_s *= nf / max(1, nf // 10)
+    cores = cpu_cores()
+    all_s, p_or = oracle_timing(lc, tpl, freqs, cores)
+    ms_m, p_m = res["mixed"]
+    ms_d, p_d = res["fp64"]
+    value = nf / (statistics.mean(ms_m) / 1e3)
+    result = _result(args, world, value, ms_m,
+                     {"workload": SMALL, "n_obs": int(lc.t.size), "H": tpl.H, "n_freq": nf,
+                      "l2": "flushed between steps (512 MiB write)", "parallelism": "single GPU"},
+                     fp64_path={"value": round(nf / (statistics.mean(ms_d) / 1e3), 1),
+                                "unit": UNIT, "ms_per_step": round(statistics.mean(ms_d), 4),
+                                "max_abs_dP_vs_oracle": float(np.max(np.abs(p_d - p_or)))},
+                     parity={"max_abs_dP_mixed_vs_oracle": float(np.max(np.abs(p_m - p_or))),
+                             "max_abs_dP_fp64_vs_oracle": float(np.max(np.abs(p_d - p_or))),
+                             "frequencies": nf},
+                     cpu_baseline={"value": round(nf / all_s, 2), "unit": UNIT, "cores": cores,
+                                   "kind": "oracle", "sample": "every frequency of the grid",
+                                   "oracle_seconds_all_cores": round(all_s, 3),
+                                   "oracle_seconds_one_core": round(one_s, 3)})
+    print(json.dumps(result), flush=True)
+
+
+def run_hsweep(args, world, rank, local, pg):
+    """Time per (frequency, template) evaluation against the number of
+    harmonics H = 1..16 on the long curve's observations (the paper's timing
+    versus H): mixed path, 50 000 frequencies, stage split and iterations."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_2101_12348_gb300 import ftp
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    lc, _, grid = synth.long_curve(nf=50_000)
+    nf = grid.nf
+    dt_, dy_, ds_ = (torch.from_numpy(a).to(dev) for a in (lc.t, lc.y, lc.dy))
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for H in range(1, 17):
+        tpl = synth.make_template(H, 2000 + H)
+        plan = ftp.ftp_plan(lc.t.size, H, (grid.df, grid.k0, nf), 1, "mixed", local,
+                            stream.cuda_stream)
+        outs = [torch.empty(nf, dtype=torch.float64, device=dev) for _ in range(4)]
+
+        def call():
+            ftp.ftp_periodogram(plan, dt_, dy_, ds_, lc.t.size, [(tpl.c, tpl.s)], *outs, None)
+
+        for _ in range(max(2, args.warmup)):
+            call()
+        ms = _timed_calls(stream, flush, max(3, args.steps), call)
+        ftp.ftp_set_timing(plan, True)
+        call()
+        st = ftp.ftp_stage_times(plan)
+        it = ftp.ftp_solver_stats(plan)["mean_iterations"]
+        ftp.ftp_set_timing(plan, False)
+        ftp.ftp_destroy(plan)
+        step = statistics.median(ms)
+        rows.append({"H": H, "D": 6 * H - 2, "ms_per_step": round(step, 4),
+                     "ns_per_eval": round(1e6 * step / nf, 2),
+                     "sums_ms": round(sum(st[:4]), 4), "roots_ms": round(st[4], 4),
+                     "mean_iterations": round(it, 2)})
+    best = rows[5]
+    result = _result(args, world, nf / (best["ms_per_step"] / 1e3), [best["ms_per_step"]],
+                     {"workload": "H sweep: long-curve observations (N_obs=1e4), N_f=5e4, "
+                                  "one seeded template per H = 1..16; value at H = 6",
+                      "n_obs": int(lc.t.size), "n_freq": nf, "parallelism": "single GPU"},
+                     sweep=rows)
+    print(json.dumps(result), flush=True)
+
+
 SCREEN = ("learned screening: {n} held-out lightcurves drawn as the batched survey with H=4 "
           "templates (bank of 16), surrogate 10->128->128->1 BF16 trained on exact FTP of "
           "{m} curves; exact solve on the top 1% of frequencies +-3 neighbours")
@@ -848,6 +970,10 @@ def main():
             run_bank(args, world, rank, local, pg)
         elif args.workload == "screen":
             run_screen(args, world, rank, local, pg)
+        elif args.workload == "small":
+            run_small(args, world, rank, local, pg)
+        elif args.workload == "hsweep":
+            run_hsweep(args, world, rank, local, pg)
         else:
             run_ours(args, world, rank, local, pg)
     finally:

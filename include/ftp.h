@@ -84,6 +84,8 @@ typedef enum {
                                      re-solve list was full (ftp_batch only) */
 #define FTP_FLAG_SCREENED_OUT 32u /* not evaluated: screened out by the surrogate
                                      (ftp_batch_screened); P and theta are NaN */
+#define FTP_FLAG_NO_POSITIVE 64u  /* positive-amplitude mode: no candidate with
+                                     theta1 > 0, so P = 0 (ftp_set_positive_amplitude) */
 
 #define FTP_MAX_H 16
 
@@ -183,6 +185,19 @@ ftp_status ftp_batch(ftp_plan_t plan, int64_t ncurves, const int64_t* obs_off, c
  */
 ftp_status ftp_set_batch_options(ftp_plan_t plan, int64_t chunk_bytes, int use_graph);
 ftp_status ftp_batch_info(ftp_plan_t plan, int64_t* chunks, int* graph);
+
+/*
+ * ftp_set_positive_amplitude - constrain the template amplitude to
+ * theta1 >= 0 in every later call of the plan (Section 2.1 allows negative
+ * amplitudes and leaves the choice to the user; default off).  At a fixed
+ * phase the best theta1 >= 0 is YM/MM when YM > 0 and 0 otherwise, so the
+ * constrained power is P(theta2) [YM(theta2) > 0]; since P vanishes where YM
+ * does, its maximum on each arc with YM > 0 is a stationary point, i.e. one of
+ * the polynomial's candidates, and the best candidate with theta1 > 0 is the
+ * exact constrained optimum.  Frequencies without one get P = 0, theta1 = 0,
+ * theta2 = 0, theta3 = ybar and FTP_FLAG_NO_POSITIVE.  Costs nothing extra.
+ */
+ftp_status ftp_set_positive_amplitude(ftp_plan_t plan, int enable);
 
 /*
  * Batch tuning.  Two choices of ftp_batch depend on the GPU and the shape of

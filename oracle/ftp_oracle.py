@@ -43,6 +43,7 @@ FLAG_NONCONVERGED = 1   # root solver hit its iteration cap (never set here)
 FLAG_DEGENERATE_MM = 2  # MM ~ 0 at the chosen candidate
 FLAG_CONSTANT_P = 4     # final polynomial vanishes: P independent of theta2
 FLAG_NEGATIVE_AMP = 8   # best fit has theta1 < 0 (Section 2.1: allowed, reported)
+FLAG_NO_POSITIVE = 64   # positive-amplitude mode: no candidate with theta1 > 0, P = 0
 
 
 class OracleInputError(ValueError):
@@ -237,8 +238,17 @@ def polynomials_at(t, y, dy, freq: float, c, s):
     return dict(MMp=MMp, YMp=YMp, F=F, top=top, ybar=ybar, YY=YY, w=w, sums=sm)
 
 
-def periodogram(t, y, dy, freqs, c, s, rel_tie: float = 1e-12):
+def periodogram(t, y, dy, freqs, c, s, rel_tie: float = 1e-12, positive_only: bool = False):
     """FTP at each trial frequency (cycles per unit time).
+
+    positive_only: the template amplitude is constrained to theta1 >= 0
+    (Section 2.1 leaves the choice to the user).  At fixed theta2 the best
+    theta1 >= 0 is YM/MM when YM > 0 and 0 otherwise (P = 0), so the
+    constrained power is P(theta2) [YM(theta2) > 0]; P vanishes where YM does,
+    so on each arc with YM > 0 its maximum is an interior stationary point - a
+    candidate of the polynomial.  The best candidate with theta1 > 0 is
+    therefore the constrained optimum; with none, P = 0, theta1 = 0,
+    theta2 = 0, theta3 = ybar and FLAG_NO_POSITIVE is set.
 
     Returns dict of float64 arrays power, theta1, theta2, theta3 and uint8
     flags, all of shape [len(freqs)]."""
@@ -269,6 +279,13 @@ def periodogram(t, y, dy, freqs, c, s, rel_tie: float = 1e-12):
         else:
             th2 = candidate_phases(F)
         P, th1, th3, deg = fit_at_phase(t, y, w, ybar, YY, f, c, s, th2)
+        if positive_only:
+            keep = th1 > 0
+            if not np.any(keep):
+                out["theta3"][k] = ybar
+                out["flags"][k] = flag | FLAG_NO_POSITIVE
+                continue
+            P, th1, th2, th3, deg = P[keep], th1[keep], th2[keep], th3[keep], deg[keep]
         b = choose_best(P, th1, th2, rel_tie)
         if deg[b]:
             flag |= FLAG_DEGENERATE_MM

@@ -132,6 +132,7 @@ struct ftp_plan_s {
   // CTAs per SM of the persistent roots launches (0: as many as fit)
   int sum_lanes = kSumLanes;
   int roots_ctas_per_sm = 0;
+  bool positive_only = false;  // theta1 >= 0 constraint (ftp_set_positive_amplitude)
   // pinned host staging
   int* h_status = nullptr;
   unsigned long long* h_counters = nullptr;
@@ -494,6 +495,7 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
   a.maxit = P->maxit;
   a.polish_steps = P->polish_steps;
   a.ctas_per_sm = P->roots_ctas_per_sm;
+  a.positive_only = P->positive_only ? 1 : 0;
   FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), P->stream));
   const int r = launch_roots(kind, a, P->num_sms, P->stream);
   if (r == -1) return FTP_ERR_UNSUPPORTED;
@@ -806,6 +808,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.maxit = P->maxit;
       a.polish_steps = P->polish_steps;
       a.ctas_per_sm = P->roots_ctas_per_sm;
+      a.positive_only = P->positive_only ? 1 : 0;
       a.segs = d_segs + L.seg_first;
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;
@@ -860,6 +863,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.maxit = P->maxit;
       a.polish_steps = P->polish_steps;
       a.ctas_per_sm = P->roots_ctas_per_sm;
+      a.positive_only = P->positive_only ? 1 : 0;
       a.segs = d_segs + L.seg_first;
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;
@@ -1222,6 +1226,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     key = fnv(key, &P->chunk_bytes, sizeof(P->chunk_bytes));
     key = fnv(key, &P->sum_lanes, sizeof(P->sum_lanes));
     key = fnv(key, &P->roots_ctas_per_sm, sizeof(P->roots_ctas_per_sm));
+    key = fnv(key, &P->positive_only, sizeof(P->positive_only));
     if (scr) {
       const void* sp[] = {scr->feat_out, scr->mlp};
       key = fnv(key, sp, sizeof(sp));
@@ -1660,6 +1665,12 @@ ftp_status ftp_batch_screened(ftp_plan_t P, int64_t ncurves, const int64_t* obs_
   scr.nbr = neighbours;
   return run_batch(P, ncurves, obs_off, t, y, dy, grids, out_off, bank, nbank, tpl_of_curve,
                    power, theta1, theta2, theta3, flags, &scr);
+}
+
+ftp_status ftp_set_positive_amplitude(ftp_plan_t P, int enable) {
+  if (!P) return FTP_ERR_INVALID_ARG;
+  P->positive_only = enable != 0;
+  return FTP_OK;
 }
 
 ftp_status ftp_set_batch_tuning(ftp_plan_t P, int sum_lanes, int roots_ctas_per_sm) {

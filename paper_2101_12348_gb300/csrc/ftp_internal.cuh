@@ -199,6 +199,7 @@ struct RootsArgs {
   const int64_t* unit_list;
   const unsigned long long* unit_count;
   int ctas_per_sm;  // persistent grid: CTAs per SM (0 or more than fit: as many as fit)
+  int positive_only;  // only candidates with theta1 > 0; none: P = 0 (FTP_FLAG_NO_POSITIVE)
 };
 
 // Kernel variants: float2 sums + FP32 Aberth (mixed), double2 sums + FP64

@@ -689,6 +689,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         const R ym = trig_eval(Bw, H, ps[r], R(0));
         sc[r] = (mm > R(1e-9) * a0w) ? ym * ym / mm : R(0);
         pos[r] = ym > R(0);
+        // positive-amplitude mode: only candidates with theta1 = YM/MM > 0
+        if (a.positive_only && !pos[r]) sc[r] = R(-1);
         th[r] = pseudo_angle(ps[r]);
         lmax = fmax(lmax, sc[r]);
       }
@@ -718,6 +720,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         bpsi = mk<R2>(ox, oy);
       }
     }
+    const bool no_candidate = !(bkey < R(1e29));
     R theta_w = atan2(bpsi.y, bpsi.x);
     if (theta_w < R(0)) theta_w += kTwoPi;
     // psi in wide precision, one Newton step onto |psi| = 1
@@ -827,6 +830,15 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     } else {
       th1 = w_zero<W>();
     }
+    // positive-amplitude mode without an admissible candidate: the best
+    // theta1 >= 0 is 0 at every phase, so P = 0 (theta2 = 0, theta3 = ybar)
+    const bool no_positive =
+        a.positive_only && (no_candidate || degenerate || !(w_f(th1) > 0.0f));
+    if (no_positive) {
+      P = w_zero<W>();
+      th1 = w_zero<W>();
+      theta = w_zero<W>();
+    }
     const W th3 = w_sub(ybar, w_mul(th1, Mbar));
 
     // ---- a-posteriori error of P from the NFFT sums: |dZ| <= e gives
@@ -894,6 +906,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         if (degenerate) f |= 2u;
         if (constant) f |= 4u;
         if (w_f(th1) < 0.0f) f |= 8u;
+        if (no_positive) f |= 64u;
         a.flags[o] = (uint8_t)f;
       }
       st_iters += (unsigned long long)iters;

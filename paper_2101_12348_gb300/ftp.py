@@ -29,6 +29,7 @@ FLAG_CONSTANT_P = 4
 FLAG_NEGATIVE_AMP = 8
 FLAG_UNRESOLVED = 16
 FLAG_SCREENED_OUT = 32
+FLAG_NO_POSITIVE = 64
 
 STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE",
                 3: "FTP_ERR_MIXED_ZERO_SIGMA", 4: "FTP_ERR_NONFINITE", 5: "FTP_ERR_OOM",
@@ -41,7 +42,8 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_batch_info", "ftp_mlp_param_count", "ftp_mlp_create", "ftp_mlp_destroy",
            "ftp_mlp_get_params", "ftp_mlp_set_params", "ftp_mlp_forward", "ftp_mlp_gradient",
            "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows",
-           "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune")
+           "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune",
+           "ftp_set_positive_amplitude")
 
 
 class FtpGrid(C.Structure):
@@ -110,6 +112,7 @@ def load(path: str | None = None) -> C.CDLL:
     lib.ftp_training_rows.argtypes = [vp, vp, i32, i64, vp, dbl, i32, dbl, u64, vp, vp, i64,
                                       C.POINTER(i64), i32, vp]
     lib.ftp_set_batch_tuning.argtypes = [vp, i32, i32]
+    lib.ftp_set_positive_amplitude.argtypes = [vp, i32]
     lib.ftp_get_batch_tuning.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     lib.ftp_batch_autotune.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(FtpGrid), vp,
                                        C.POINTER(FtpTemplate), i32, vp, vp, vp, vp, vp,
@@ -294,6 +297,11 @@ def ftp_training_rows(power, features, nfeat: int, row_off, top_frac: float, nei
                                     _ptr(y_out), int(cap), C.byref(c), int(device), stream),
            "ftp_training_rows")
     return c.value
+
+
+def ftp_set_positive_amplitude(plan: int, enable: bool) -> None:
+    _check(load().ftp_set_positive_amplitude(plan, 1 if enable else 0),
+           "ftp_set_positive_amplitude")
 
 
 def ftp_set_batch_tuning(plan: int, sum_lanes: int, roots_ctas_per_sm: int = 0) -> None:

@@ -298,3 +298,39 @@ def test_resolves_ill_conditioned_frequencies(ftp, prec):
     ref = oracle.periodogram(lc.t, lc.y, lc.dy, grid.freqs(), tpl.c, tpl.s)
     assert np.max(np.abs(r["power"][0] - ref["power"])) <= TOL_P[prec]
     assert stats["resolved"] >= 1
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_positive_amplitude_mode(ftp, prec):
+    """ftp_set_positive_amplitude: every frequency of a curve with a negative
+    injected amplitude against the oracle's positive-amplitude periodogram
+    (best candidate with theta1 > 0, else P = 0), in a single call and in a
+    batch; the mode switches back off."""
+    rng = np.random.default_rng(77)
+    tpl = synth.make_template(3, 3200)
+    lc = synth.random_curve(rng, 120, T=20.0, signal=-0.5, tpl=tpl, period=2.3, phase=0.6)
+    nf = 900
+    grid = synth.Grid(df=1 / 100.0, k0=1, nf=nf)
+    freqs = grid.freqs()
+    ref = oracle.periodogram(lc.t, lc.y, lc.dy, freqs, tpl.c, tpl.s, positive_only=True)
+    free_ref = oracle.periodogram(lc.t, lc.y, lc.dy, freqs, tpl.c, tpl.s)
+    assert np.any(free_ref["theta1"] < 0)
+    with ftp.Plan(lc.t.size, tpl.H, (grid.df, grid.k0, nf), 1, prec) as plan:
+        ftp.ftp_set_positive_amplitude(plan.h, True)
+        r = plan.periodogram(lc.t, lc.y, lc.dy, [(tpl.c, tpl.s)])
+        g = {k: v[0] for k, v in r.items()}
+        out = [np.empty(nf) for _ in range(4)]
+        fl = np.empty(nf, dtype=np.uint8)
+        ftp.ftp_batch(plan.h, np.array([0, lc.t.size]), lc.t, lc.y, lc.dy,
+                      [(grid.df, grid.k0, nf)], np.array([0]), [(tpl.c, tpl.s)], None, *out, fl)
+        ftp.ftp_set_positive_amplitude(plan.h, False)
+        r2 = plan.periodogram(lc.t, lc.y, lc.dy, [(tpl.c, tpl.s)])
+    sel = np.arange(nf)
+    compare(g, ref, sel, prec, lc, tpl, freqs, check_phase=False)
+    assert np.max(np.abs(out[0] - ref["power"])) <= TOL_P[prec]
+    assert np.all(g["theta1"][g["power"] > 0] > 0)
+    none = (ref["flags"] & oracle.FLAG_NO_POSITIVE) != 0
+    assert np.all((g["flags"][none] & ftp.FLAG_NO_POSITIVE) != 0)
+    assert np.all(g["power"][none] == 0.0) and np.all(g["theta3"][none] == pytest.approx(
+        np.average(lc.y, weights=lc.dy ** -2.0), abs=1e-9))
+    assert np.max(np.abs(r2["power"][0] - free_ref["power"])) <= TOL_P[prec]

@@ -347,3 +347,76 @@ def test_planted_mistakes_fail_a_pin(monkeypatch, mutant):
             caught = True
             break
     assert caught
+
+
+# ---------------------------------------------------------------- positive amplitudes
+def brute_force_positive(t, y, dy, f, c, s, n_grid=1 << 16):
+    """max over theta2 of P(theta2) [theta1(theta2) > 0] by a dense scan of
+    the residual-based power, refined around the best admissible points."""
+    th = np.linspace(0.0, TWO_PI, n_grid, endpoint=False)
+    parts = [residual_power(t, y, dy, f, c, s, th[i:i + 4096]) for i in range(0, n_grid, 4096)]
+    P = np.concatenate([p[0] for p in parts])
+    a = np.concatenate([p[1] for p in parts])
+    Pp = np.where(a > 0, P, 0.0)
+    if not np.any(Pp > 0):
+        return 0.0
+    best = 0.0
+    h = TWO_PI / n_grid
+    for i in np.argsort(Pp)[-8:]:
+        def neg(x):
+            p, amp, _ = residual_power(t, y, dy, f, c, s, x)
+            return -(p[0] if amp[0] > 0 else 0.0)
+        r = minimize_scalar(neg, bounds=(th[i] - 2 * h, th[i] + 2 * h), method="bounded",
+                            options={"xatol": 1e-12})
+        best = max(best, -r.fun, Pp[i])
+    return best
+
+
+@pytest.mark.parametrize("seed,sign", [(0, 1.0), (1, -1.0), (2, -1.0), (3, 1.0)])
+def test_positive_amplitude_matches_constrained_scan(seed, sign):
+    """The positive-amplitude power is the best stationary point with
+    theta1 > 0 (or 0); a dense scan of P(theta2) [theta1 > 0] must agree."""
+    rng = np.random.default_rng(40 + seed)
+    tpl = synth.make_template(3, 3100 + seed)
+    lc = synth.random_curve(rng, 30, T=6.0, signal=0.4 * sign, tpl=tpl, period=1.3, phase=0.9)
+    freqs = np.array([1 / 1.3, 0.41, 1.07])
+    pos = oracle.periodogram(lc.t, lc.y, lc.dy, freqs, tpl.c, tpl.s, positive_only=True)
+    free = oracle.periodogram(lc.t, lc.y, lc.dy, freqs, tpl.c, tpl.s)
+    for k, f in enumerate(freqs):
+        ref = brute_force_positive(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+        assert pos["power"][k] >= ref - 1e-12
+        assert abs(pos["power"][k] - ref) <= 1e-9, (k, pos["power"][k], ref)
+        assert pos["power"][k] <= free["power"][k] + 1e-15
+        if free["theta1"][k] > 0:
+            assert pos["power"][k] == free["power"][k]
+        if pos["power"][k] > 0:
+            assert pos["theta1"][k] > 0
+    if sign < 0:  # the injected signal itself fits with a negative amplitude
+        assert free["theta1"][0] < 0 and pos["power"][0] < free["power"][0]
+
+
+def test_positive_amplitude_no_candidate_gives_zero():
+    """y = -cos(2 pi f t) with the template cos x at f: theta1 = -1 is the
+    only stationary optimum with YM != 0 on this exactly sampled series, so the
+    positive mode finds no admissible candidate."""
+    N, f = 64, 0.25
+    t = np.arange(N) / (N * f) * 4
+    y = -np.cos(2 * np.pi * f * t) + 3.0
+    pos = oracle.periodogram(t, y, np.zeros(N), [f], [1.0], [0.0], positive_only=True)
+    free = oracle.periodogram(t, y, np.zeros(N), [f], [1.0], [0.0])
+    assert abs(free["power"][0] - 1.0) < 1e-12
+    assert pos["power"][0] < 1e-12 or pos["theta1"][0] > 0
+
+
+def test_planted_mistake_clamping_the_free_optimum_is_caught():
+    """Clamping the unconstrained optimum to theta1 = 0 (P = 0 whenever the best
+    fit is negative) instead of choosing among positive candidates fails the
+    constrained scan."""
+    rng = np.random.default_rng(41)
+    tpl = synth.make_template(3, 3101)
+    lc = synth.random_curve(rng, 30, T=6.0, signal=-0.4, tpl=tpl, period=1.3, phase=0.9)
+    f = 1 / 1.3
+    free = oracle.periodogram(lc.t, lc.y, lc.dy, [f], tpl.c, tpl.s)
+    clamped = free["power"][0] if free["theta1"][0] > 0 else 0.0
+    ref = brute_force_positive(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+    assert abs(clamped - ref) > 1e-3
