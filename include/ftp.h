@@ -187,6 +187,27 @@ ftp_status ftp_set_batch_options(ftp_plan_t plan, int64_t chunk_bytes, int use_g
 ftp_status ftp_batch_info(ftp_plan_t plan, int64_t* chunks, int* graph);
 
 /*
+ * ftp_multiband_periodogram - the multi-phase multi-band periodogram (Section
+ * 2.2, Eq. multibandmultiphase): band b owns observations [obs_off[b],
+ * obs_off[b+1]) of t, y, dy and its own amplitude, phase and offset at a
+ * shared trial frequency (the plan's grid), fitted with template
+ * bank[tpl_of_band[b]] (NULL: template 0 for every band).  The combined
+ * power is P = sum_b chi2_0,b P_b / sum_b chi2_0,b with chi2_0,b the weighted
+ * sum of squared deviations of band b from its weighted mean (raw weights
+ * sigma^-2, unit weights when a band's sigma are all zero).  power [nf] and
+ * the nullable per-band outputs [nbands][nf] may be host or device memory;
+ * obs_off, bank and tpl_of_band are host arrays.  The bands run as one
+ * ftp_batch over the plan's grid (same validation and errors).
+ */
+ftp_status ftp_multiband_periodogram(ftp_plan_t plan, int nbands, const int64_t* obs_off,
+                                     const double* t, const double* y, const double* dy,
+                                     const ftp_template* bank, int nbank,
+                                     const int32_t* tpl_of_band, double* power,
+                                     double* band_power, double* band_theta1,
+                                     double* band_theta2, double* band_theta3,
+                                     uint8_t* band_flags);
+
+/*
  * ftp_set_positive_amplitude - constrain the template amplitude to
  * theta1 >= 0 in every later call of the plan (Section 2.1 allows negative
  * amplitudes and leaves the choice to the user; default off).  At a fixed

@@ -319,3 +319,30 @@ def best_candidate_margin(t, y, dy, freq: float, c, s, theta2_best: float,
     twin = (np.sign(th1) != np.sign(th1b[0])) & (np.abs(P - Pbest) <= rel_tie * max(Pbest, 1e-300))
     far = P[(d > sep) & ~twin]
     return float(Pbest - (far.max() if far.size else 0.0))
+
+
+# ---------------------------------------------------------------------------
+# Multi-band, multi-phase model (Section 2.2, Eq. multibandmultiphase)
+# ---------------------------------------------------------------------------
+def chi2_0(y, dy) -> float:
+    """Weighted sum of squared residuals about the weighted mean, with the
+    raw weights sigma^-2 (unit weights when every sigma is zero)."""
+    y = np.asarray(y, dtype=np.float64)
+    dy = np.asarray(dy, dtype=np.float64)
+    wr = np.ones_like(dy) if np.all(dy == 0) else dy ** -2.0
+    ybar = np.sum(wr * y) / np.sum(wr)
+    return float(np.sum(wr * (y - ybar) ** 2))
+
+
+def multiband_periodogram(bands, freqs, rel_tie: float = 1e-12):
+    """Multi-phase multi-band template periodogram: every band k has its own
+    amplitude, phase and offset (and template) at a shared frequency, and
+    P = sum_k chi2_0,k P_k / sum_k chi2_0,k (Eq. multibandmultiphase).
+
+    bands: sequence of (t, y, dy, c, s).  Returns dict(power [nf],
+    band_power [K][nf], chi2_0 [K], bands: the per-band periodogram dicts)."""
+    per = [periodogram(t, y, dy, freqs, c, s, rel_tie) for (t, y, dy, c, s) in bands]
+    w = np.array([chi2_0(y, dy) for (_, y, dy, _, _) in bands])
+    bp = np.array([p["power"] for p in per])
+    return dict(power=(w[:, None] * bp).sum(axis=0) / w.sum(), band_power=bp, chi2_0=w,
+                bands=per)

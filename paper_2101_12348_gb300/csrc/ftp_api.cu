@@ -187,6 +187,13 @@ struct ftp_plan_s {
   int64_t* d_bulist = nullptr;  // listed work units of one launch
   size_t bulist_cap = 0;
   unsigned long long* d_bucount = nullptr;
+  // multi-band workspace (ftp_multiband_periodogram; grown on demand)
+  double* d_mb = nullptr;       // [4][bands][nf] per-band outputs, then [bands][MO_WORDS] moments
+  size_t mb_cap = 0;
+  uint8_t* d_mbflags = nullptr;  // [bands][nf]
+  size_t mbflags_cap = 0;
+  double* d_mbpow = nullptr;     // [nf] combined power
+  size_t mbpow_cap = 0;
 };
 
 namespace {
@@ -602,6 +609,30 @@ ftp_status grow_dev(T** p, size_t* cap, size_t count, bool* grew) {
   return FTP_OK;
 }
 
+// Multi-phase combination (Section 2.2, Eq. multibandmultiphase): per
+// frequency, P = sum_b chi2_0,b P_b / sum_b chi2_0,b with chi2_0,b = YY_b W_b
+// (YY is the variance under normalised weights, W the sum of the raw ones).
+__global__ void __launch_bounds__(256) multiband_combine_kernel(const double* __restrict__ bp,
+                                                                const double* __restrict__ mom,
+                                                                int nbands, int64_t nf,
+                                                                double* __restrict__ power) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nf) return;
+  double num = 0.0, den = 0.0;
+  for (int b = 0; b < nbands; ++b) {
+    const double c = mom[(size_t)b * MO_WORDS + MO_YY] * mom[(size_t)b * MO_WORDS + MO_WSUM];
+    num += c * bp[(size_t)b * nf + k];
+    den += c;
+  }
+  power[k] = num / den;
+}
+
+void launch_multiband_combine(const double* bp, const double* mom, int nbands, int64_t nf,
+                              double* power, cudaStream_t s) {
+  multiband_combine_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(bp, mom, nbands, nf,
+                                                                         power);
+}
+
 void free_lane(SumLane* L) {
   if (L->s) cudaStreamSynchronize(L->s);
   for (auto& kv : L->ffts) cufftDestroy(kv.second.h);
@@ -688,6 +719,7 @@ struct BatchScreen {
   const ftp_mlp_s* mlp = nullptr;     // screened mode
   double top_frac = 0.0;
   int nbr = 0;
+  double* moments_out = nullptr;      // device [ncurves][MO_WORDS]: each curve's moments
 };
 
 uint64_t fnv(uint64_t h, const void* p, size_t n) {
@@ -737,6 +769,10 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       FTP_CK(cudaStreamWaitEvent(s, L.done, 0));
     }
     if (tm) cudaEventRecord(P->bev[4 * q + 1], s);
+    if (scr && scr->moments_out)
+      FTP_CK(cudaMemcpyAsync(scr->moments_out + (size_t)ch.c0 * MO_WORDS, P->d_bmom,
+                             sizeof(double) * MO_WORDS * (size_t)(ch.c1 - ch.c0),
+                             cudaMemcpyDeviceToDevice, s));
     const bool screened = scr && scr->mlp;
     if (scr && scr->Hf > 0) {
       // features of every frequency of the chunk (into the caller's array in
@@ -899,7 +935,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   if (!feat_only && (!out_off || !power || !theta1 || !theta2 || !theta3))
     return FTP_ERR_INVALID_ARG;
   if (feat_only && (!scr->feat_row || !is_device_ptr(scr->feat_out))) return FTP_ERR_INVALID_ARG;
-  if (scr && (Hf < 1 || Hf > kFeatMaxH || Hf > P->max_H)) return FTP_ERR_UNSUPPORTED;
+  if (scr && (scr->feat_out || scr->mlp) && (Hf < 1 || Hf > kFeatMaxH || Hf > P->max_H))
+    return FTP_ERR_UNSUPPORTED;
   if (ncurves == 0) return FTP_OK;
   if (ncurves > (int64_t)1 << 30) return FTP_ERR_UNSUPPORTED;
   ftp_status st = feat_only ? FTP_OK : check_templates(P, bank, nbank);
@@ -1228,7 +1265,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     key = fnv(key, &P->roots_ctas_per_sm, sizeof(P->roots_ctas_per_sm));
     key = fnv(key, &P->positive_only, sizeof(P->positive_only));
     if (scr) {
-      const void* sp[] = {scr->feat_out, scr->mlp};
+      const void* sp[] = {scr->feat_out, scr->mlp, scr->moments_out};
       key = fnv(key, sp, sizeof(sp));
       key = fnv(key, &scr->Hf, sizeof(scr->Hf));
       key = fnv(key, &scr->top_frac, sizeof(scr->top_frac));
@@ -1360,7 +1397,8 @@ void ftp_destroy(ftp_plan_t P) {
     if (p) cudaFree(p);
   void* bptrs[] = {P->d_bsums, P->d_bmom, P->d_bobs, P->d_bout, P->d_bflags, P->d_bmark,
                    P->d_blist, P->d_bslot_curve, P->d_bcount, P->d_bredo_sums, P->d_bdesc,
-                   P->d_bfeat, P->d_bscore, P->d_bsel, P->d_bulist, P->d_bucount};
+                   P->d_bfeat, P->d_bscore, P->d_bsel, P->d_bulist, P->d_bucount,
+                   P->d_mb, P->d_mbflags, P->d_mbpow};
   for (void* p : bptrs)
     if (p) cudaFree(p);
   if (P->h_bdesc) cudaFreeHost(P->h_bdesc);
@@ -1665,6 +1703,62 @@ ftp_status ftp_batch_screened(ftp_plan_t P, int64_t ncurves, const int64_t* obs_
   scr.nbr = neighbours;
   return run_batch(P, ncurves, obs_off, t, y, dy, grids, out_off, bank, nbank, tpl_of_curve,
                    power, theta1, theta2, theta3, flags, &scr);
+}
+
+ftp_status ftp_multiband_periodogram(ftp_plan_t P, int nbands, const int64_t* obs_off,
+                                     const double* t, const double* y, const double* dy,
+                                     const ftp_template* bank, int nbank,
+                                     const int32_t* tpl_of_band, double* power,
+                                     double* band_power, double* band_theta1,
+                                     double* band_theta2, double* band_theta3,
+                                     uint8_t* band_flags) {
+  if (!P || nbands < 1 || !obs_off || !power || !bank || nbank < 1) return FTP_ERR_INVALID_ARG;
+  if (nbands > (1 << 20)) return FTP_ERR_UNSUPPORTED;
+  const int64_t nf = P->grid.nf, items = (int64_t)nbands * nf;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->device);
+  struct Restore {
+    int d;
+    ~Restore() { cudaSetDevice(d); }
+  } restore{prev};
+  bool grew = false;
+  ftp_status st = grow_dev(&P->d_mb, &P->mb_cap, (size_t)4 * items + (size_t)MO_WORDS * nbands,
+                           &grew);
+  if (st == FTP_OK) st = grow_dev(&P->d_mbflags, &P->mbflags_cap, (size_t)items, &grew);
+  if (st == FTP_OK) st = grow_dev(&P->d_mbpow, &P->mbpow_cap, (size_t)nf, &grew);
+  if (st != FTP_OK) return st;
+  if (grew && P->graph_exec) {
+    cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
+    P->graph_key = 0;
+  }
+  std::vector<ftp_grid> grids((size_t)nbands, P->grid);
+  std::vector<int64_t> out_off((size_t)nbands);
+  std::vector<int32_t> tob((size_t)nbands, 0);
+  for (int b = 0; b < nbands; ++b) {
+    out_off[(size_t)b] = (int64_t)b * nf;
+    if (tpl_of_band) tob[(size_t)b] = tpl_of_band[b];
+  }
+  double* o[4];
+  for (int i = 0; i < 4; ++i) o[i] = P->d_mb + (size_t)i * items;
+  double* mom = P->d_mb + (size_t)4 * items;
+  BatchScreen scr;
+  scr.moments_out = mom;
+  st = run_batch(P, nbands, obs_off, t, y, dy, grids.data(), out_off.data(), bank, nbank,
+                 tob.data(), o[0], o[1], o[2], o[3], P->d_mbflags, &scr);
+  if (st != FTP_OK) return st;
+  launch_multiband_combine(o[0], mom, nbands, nf, P->d_mbpow, P->stream);
+  FTP_CK(cudaGetLastError());
+  FTP_CK(cudaMemcpyAsync(power, P->d_mbpow, sizeof(double) * nf, cudaMemcpyDefault, P->stream));
+  double* bo[4] = {band_power, band_theta1, band_theta2, band_theta3};
+  for (int i = 0; i < 4; ++i)
+    if (bo[i])
+      FTP_CK(cudaMemcpyAsync(bo[i], o[i], sizeof(double) * items, cudaMemcpyDefault, P->stream));
+  if (band_flags)
+    FTP_CK(cudaMemcpyAsync(band_flags, P->d_mbflags, (size_t)items, cudaMemcpyDefault, P->stream));
+  FTP_CK(cudaStreamSynchronize(P->stream));
+  return FTP_OK;
 }
 
 ftp_status ftp_set_positive_amplitude(ftp_plan_t P, int enable) {

@@ -43,7 +43,7 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_mlp_get_params", "ftp_mlp_set_params", "ftp_mlp_forward", "ftp_mlp_gradient",
            "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows",
            "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune",
-           "ftp_set_positive_amplitude")
+           "ftp_set_positive_amplitude", "ftp_multiband_periodogram")
 
 
 class FtpGrid(C.Structure):
@@ -113,6 +113,8 @@ def load(path: str | None = None) -> C.CDLL:
                                       C.POINTER(i64), i32, vp]
     lib.ftp_set_batch_tuning.argtypes = [vp, i32, i32]
     lib.ftp_set_positive_amplitude.argtypes = [vp, i32]
+    lib.ftp_multiband_periodogram.argtypes = [vp, i32, vp, vp, vp, vp, C.POINTER(FtpTemplate),
+                                              i32, vp, vp, vp, vp, vp, vp, vp]
     lib.ftp_get_batch_tuning.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     lib.ftp_batch_autotune.argtypes = [vp, i64, vp, vp, vp, vp, C.POINTER(FtpGrid), vp,
                                        C.POINTER(FtpTemplate), i32, vp, vp, vp, vp, vp,
@@ -297,6 +299,20 @@ def ftp_training_rows(power, features, nfeat: int, row_off, top_frac: float, nei
                                     _ptr(y_out), int(cap), C.byref(c), int(device), stream),
            "ftp_training_rows")
     return c.value
+
+
+def ftp_multiband_periodogram(plan: int, obs_off, t, y, dy, bank, tpl_of_band, power,
+                              band_power=None, band_theta1=None, band_theta2=None,
+                              band_theta3=None, band_flags=None) -> None:
+    """Multi-phase multi-band periodogram over the plan's grid (see include/ftp.h)."""
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    arr, keep = _templates(bank)
+    tob = None if tpl_of_band is None else np.ascontiguousarray(tpl_of_band, dtype=np.int32)
+    _check(load().ftp_multiband_periodogram(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t),
+                                            _ptr(y), _ptr(dy), arr, len(keep) // 2, _ptr(tob),
+                                            _ptr(power), _ptr(band_power), _ptr(band_theta1),
+                                            _ptr(band_theta2), _ptr(band_theta3),
+                                            _ptr(band_flags)), "ftp_multiband_periodogram")
 
 
 def ftp_set_positive_amplitude(plan: int, enable: bool) -> None:

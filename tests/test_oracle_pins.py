@@ -420,3 +420,80 @@ def test_planted_mistake_clamping_the_free_optimum_is_caught():
     clamped = free["power"][0] if free["theta1"][0] > 0 else 0.0
     ref = brute_force_positive(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
     assert abs(clamped - ref) > 1e-3
+
+
+# ---------------------------------------------------------------- multi-band
+def raw_chi2_best(t, y, dy, f, c, s, n_grid=1 << 15):
+    """min over (theta1, theta2, theta3) of sum sigma^-2 (y - theta1 M - theta3)^2
+    by a dense theta2 scan refined with Brent, residuals computed directly."""
+    wr = dy ** -2.0
+
+    def chi2(th):
+        th = np.atleast_1d(th)
+        M = template_values(c, s, TWO_PI * f * t[None, :] - th[:, None])
+        sw, sm, smm = wr.sum(), M @ wr, (M * M) @ wr
+        sy, smy = wr @ y, M @ (wr * y)
+        det = sw * smm - sm * sm
+        a = (sw * smy - sm * sy) / det
+        b = (smm * sy - sm * smy) / det
+        return ((y[None, :] - a[:, None] * M - b[:, None]) ** 2) @ wr
+
+    th = np.linspace(0.0, TWO_PI, n_grid, endpoint=False)
+    v = np.concatenate([chi2(th[i:i + 4096]) for i in range(0, n_grid, 4096)])
+    best = np.inf
+    h = TWO_PI / n_grid
+    for i in np.argsort(v)[:6]:
+        r = minimize_scalar(lambda x: chi2(x)[0], bounds=(th[i] - 2 * h, th[i] + 2 * h),
+                            method="bounded", options={"xatol": 1e-12})
+        best = min(best, r.fun, v[i])
+    return best
+
+
+def three_bands(seed=60):
+    rng = np.random.default_rng(seed)
+    out = []
+    for b, (n, sig, H) in enumerate([(35, (0.05, 0.1), 3), (22, (0.1, 0.3), 2), (50, (0.02, 0.05), 4)]):
+        tpl = synth.make_template(H, 3300 + b)
+        lc = synth.random_curve(rng, n, T=9.0, signal=0.3 + 0.2 * b, tpl=tpl, period=1.9,
+                                phase=0.3 * b, sigma=sig)
+        out.append((lc.t, lc.y + 2.0 * b, lc.dy, tpl.c, tpl.s))
+    return out
+
+
+def test_multiband_is_the_joint_multiphase_fit():
+    """Eq. multibandmultiphase equals 1 - sum_k chi2_min,k / sum_k chi2_0,k of
+    the joint model with independent per-band amplitude, phase and offset,
+    each chi2_min,k found by brute force from raw residuals."""
+    bands = three_bands()
+    freqs = np.array([1 / 1.9, 0.77, 0.31])
+    mb = oracle.multiband_periodogram(bands, freqs)
+    for k, f in enumerate(freqs):
+        num = sum(raw_chi2_best(t, y, dy, f, c, s) for (t, y, dy, c, s) in bands)
+        den = sum(oracle.chi2_0(y, dy) for (_, y, dy, _, _) in bands)
+        assert abs(mb["power"][k] - (1.0 - num / den)) <= 1e-9, (k, mb["power"][k], 1 - num / den)
+
+
+def test_multiband_single_band_and_invariances():
+    bands = three_bands(61)
+    freqs = np.linspace(0.2, 1.2, 9)
+    one = oracle.multiband_periodogram(bands[:1], freqs)
+    ref = oracle.periodogram(*bands[0][:3], freqs, bands[0][3], bands[0][4])
+    np.testing.assert_array_equal(one["power"], ref["power"])
+    mb = oracle.multiband_periodogram(bands, freqs)
+    rev = oracle.multiband_periodogram(bands[::-1], freqs)
+    np.testing.assert_allclose(mb["power"], rev["power"], atol=1e-15)
+    dup = oracle.multiband_periodogram([bands[1], bands[1]], freqs)
+    single = oracle.multiband_periodogram([bands[1]], freqs)
+    np.testing.assert_allclose(dup["power"], single["power"], atol=1e-15)
+    assert np.all(mb["power"] >= mb["band_power"].min(axis=0) - 1e-15)
+    assert np.all(mb["power"] <= mb["band_power"].max(axis=0) + 1e-15)
+
+
+def test_planted_mistake_unweighted_band_average_is_caught():
+    bands = three_bands()
+    f = 1 / 1.9
+    mb = oracle.multiband_periodogram(bands, [f])
+    wrong = mb["band_power"][:, 0].mean()
+    num = sum(raw_chi2_best(t, y, dy, f, c, s) for (t, y, dy, c, s) in bands)
+    den = sum(oracle.chi2_0(y, dy) for (_, y, dy, _, _) in bands)
+    assert abs(wrong - (1.0 - num / den)) > 1e-3
