@@ -8,5 +8,5 @@ from .ftp_oracle import (FLAG_CONSTANT_P, FLAG_DEGENERATE_MM, FLAG_NEGATIVE_AMP,
                          final_poly, fit_at_phase, harmonic_phases, mm_poly,
                          normalized_weights, periodogram, polynomials_at, template_alpha,
                          ym_poly)
-from .ftp_oracle import chi2_0, multiband_periodogram
+from .ftp_oracle import chi2_0, multiband_periodogram, shared_phase_multiband
 from . import screen_oracle

@@ -346,3 +346,97 @@ def multiband_periodogram(bands, freqs, rel_tie: float = 1e-12):
     bp = np.array([p["power"] for p in per])
     return dict(power=(w[:, None] * bp).sum(axis=0) / w.sum(), band_power=bp, chi2_0=w,
                 bands=per)
+
+
+# ---------------------------------------------------------------------------
+# Shared-phase multi-band template (Appendix A)
+# ---------------------------------------------------------------------------
+def shared_phase_multiband(bands, freqs, offsets=None, rel_tie: float = 1e-12):
+    """Multi-band model with one amplitude, phase and offset shared by every
+    band and a template per band (Appendix A):
+        y_i^(k) ~ theta1 M^(k)(omega t_i - theta2) + theta3 + lambda_k,
+    the fixed band offsets lambda_k subtracted from the data first.  Weights
+    are normalised over all observations (sum_k W_k = 1, W_k the band's share).
+    The polynomials pool the single-band ones:
+        MM' = sum_k W_k <M^(k)2>' - (sum_k W_k Mbar^(k)')^2,
+        YM' = sum_k W_k YM^(k)' with y centred on the pooled mean,
+    and the candidates are evaluated directly from the pooled data.
+
+    bands: sequence of (t, y, dy, c, s); templates shorter than the longest
+    are padded with zero harmonics.  Returns dict of power, theta1, theta2,
+    theta3, flags (as periodogram)."""
+    K = len(bands)
+    H = max(len(b[3]) for b in bands)
+    lam = np.zeros(K) if offsets is None else np.asarray(offsets, dtype=np.float64)
+    tb, yb, cb, sb, kb = [], [], [], [], []
+    for k, (t, y, dy, c, s) in enumerate(bands):
+        tb.append(np.asarray(t, dtype=np.float64))
+        yb.append(np.asarray(y, dtype=np.float64) - lam[k])
+        cp = np.zeros(H)
+        sp = np.zeros(H)
+        cp[:len(c)] = c
+        sp[:len(s)] = s
+        cb.append(cp)
+        sb.append(sp)
+        kb.append(np.full(len(t), k))
+    t_all = np.concatenate(tb)
+    y_all = np.concatenate(yb)
+    k_all = np.concatenate(kb)
+    w = normalized_weights(np.concatenate([np.asarray(b[2], dtype=np.float64) for b in bands]))
+    ybar, YY = data_moments(y_all, w)
+    Wk = np.array([w[k_all == k].sum() for k in range(K)])
+    alphas = [template_alpha(cb[k], sb[k]) for k in range(K)]
+    freqs = np.atleast_1d(np.asarray(freqs, dtype=np.float64))
+    out = {n: np.zeros(freqs.size) for n in ("power", "theta1", "theta2", "theta3")}
+    out["flags"] = np.zeros(freqs.size, dtype=np.uint8)
+
+    def fit(f, th2):
+        th2 = np.atleast_1d(th2)
+        M = np.zeros((th2.size, t_all.size))
+        for k in range(K):
+            sel = k_all == k
+            ph = harmonic_phases(t_all[sel], f, H)
+            n = np.arange(1, H + 1, dtype=np.float64)[:, None, None]
+            x = ph[:, None, :] - n * th2[None, :, None]
+            M[:, sel] = np.tensordot(cb[k], np.cos(x), axes=(0, 0)) + \
+                np.tensordot(sb[k], np.sin(x), axes=(0, 0))
+        Mbar = M @ w
+        MMhat = (M * M) @ w
+        MM = MMhat - Mbar ** 2
+        YMv = M @ (w * (y_all - ybar))
+        deg = ~(MM > 1e-14 * MMhat)
+        safe = np.where(deg, 1.0, MM)
+        P = np.where(deg, 0.0, YMv * YMv / (YY * safe))
+        th1 = np.where(deg, 0.0, YMv / safe)
+        return P, th1, ybar - th1 * Mbar, deg
+
+    for q, f in enumerate(freqs):
+        MMhat = np.zeros(4 * H + 1, dtype=np.complex128)
+        Mbar = np.zeros(2 * H + 1, dtype=np.complex128)
+        YMp = np.zeros(2 * H + 1, dtype=np.complex128)
+        for k in range(K):
+            sel = k_all == k
+            sm = direct_sums(t_all[sel], y_all[sel], w[sel] / Wk[k], ybar, f, H)
+            C, S = sm["C"], sm["S"]
+            MMhat += Wk[k] * mm_poly(alphas[k], sm["CC"] + np.outer(C, C),
+                                     sm["CS"] + np.outer(C, S), sm["SS"] + np.outer(S, S))
+            Mbar += Wk[k] * ym_poly(alphas[k], C, S)
+            YMp += Wk[k] * ym_poly(alphas[k], sm["YC"], sm["YS"])
+        MMp = MMhat - npoly.polymul(Mbar, Mbar)
+        F, _ = final_poly(MMp, YMp)
+        flag = 0
+        if np.max(np.abs(F)) <= 1e-14 * max(np.max(np.abs(MMp)) * np.max(np.abs(YMp)), 1e-300) * H:
+            th2 = np.zeros(1)
+            flag |= FLAG_CONSTANT_P
+        else:
+            th2 = candidate_phases(F)
+        P, th1, th3, deg = fit(f, th2)
+        b = choose_best(P, th1, th2, rel_tie)
+        if deg[b]:
+            flag |= FLAG_DEGENERATE_MM
+        if th1[b] < 0:
+            flag |= FLAG_NEGATIVE_AMP
+        out["power"][q], out["theta1"][q] = P[b], th1[b]
+        out["theta2"][q], out["theta3"][q] = th2[b], th3[b]
+        out["flags"][q] = flag
+    return out
