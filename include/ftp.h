@@ -208,6 +208,29 @@ ftp_status ftp_multiband_periodogram(ftp_plan_t plan, int nbands, const int64_t*
                                      uint8_t* band_flags);
 
 /*
+ * ftp_shared_multiband - the shared-phase multi-band template periodogram
+ * (Appendix A, the model of Sesar et al. 2016): band b owns observations
+ * [obs_off[b], obs_off[b+1]) of t, y, dy and a template
+ * bank[tpl_of_band[b]] (NULL: template 0 for every band); one amplitude
+ * theta1, phase theta2 and offset theta3 are shared by all bands,
+ *     y^(b) ~ theta1 M^(b)(omega t - theta2) + theta3 + offsets[b],
+ * with the fixed band offsets (host array, nullable = 0) subtracted first.
+ * Weights are normalised over all observations, so the polynomials MM', YM'
+ * are band-weighted sums of the single-band ones (y centred on the pooled
+ * mean) and the root stage is the single-band one.  Step (a) runs per band on
+ * the plan's grid; the pooled polynomial coefficients are formed in FP64 and
+ * the roots found with FP64 polish on both precision paths.  Outputs are [nf]
+ * arrays (host or device, flags nullable) of the combined fit.  Every band
+ * must fit the plan (N_obs <= max_nobs, H <= max_H); mixing bands with and
+ * without uncertainties returns FTP_ERR_MIXED_ZERO_SIGMA.
+ */
+ftp_status ftp_shared_multiband(ftp_plan_t plan, int nbands, const int64_t* obs_off,
+                                const double* t, const double* y, const double* dy,
+                                const double* offsets, const ftp_template* bank, int nbank,
+                                const int32_t* tpl_of_band, double* power, double* theta1,
+                                double* theta2, double* theta3, uint8_t* flags);
+
+/*
  * ftp_set_positive_amplitude - constrain the template amplitude to
  * theta1 >= 0 in every later call of the plan (Section 2.1 allows negative
  * amplitudes and leaves the choice to the user; default off).  At a fixed

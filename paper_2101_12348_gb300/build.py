@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libftp_gb300.so")
 SOURCES = ["ftp_api.cu", "ftp_nfft.cu", "ftp_roots_mixed.cu", "ftp_roots_fp64.cu",
            "ftp_roots_redo.cu", "ftp_noalloc.cu", "ftp_screen.cu", "ftp_mlp.cu",
-           "ftp_mlp_api.cu"]
+           "ftp_mlp_api.cu", "ftp_shared.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -18,6 +18,12 @@
 #include "ftp_screen.cuh"
 
 namespace ftp {
+void launch_shared_moments(const double* mom, const double* lam, int nbands, double* share,
+                           double* dyb, double* pooled, int* status, cudaStream_t s);
+void launch_shared_assembly(const void* sums, bool fp64, int64_t band_stride, int Hs, int nbands,
+                            int64_t nf, int64_t nf_pad, int H, const double2* alpha,
+                            const double* share, const double* dyb, double2* coef,
+                            const int* status, cudaStream_t s);
 int launch_roots_mixed(const RootsArgs& a, int num_sms, cudaStream_t s);
 int launch_roots_fp64(const RootsArgs& a, int num_sms, cudaStream_t s);
 int launch_roots_redo(const RootsArgs& a, int num_sms, cudaStream_t s);
@@ -194,6 +200,15 @@ struct ftp_plan_s {
   size_t mbflags_cap = 0;
   double* d_mbpow = nullptr;     // [nf] combined power
   size_t mbpow_cap = 0;
+  // shared-phase multi-band workspace (ftp_shared_multiband; grown on demand)
+  unsigned char* d_shsums = nullptr;  // [bands][3H][nf_pad] sums
+  size_t shsums_cap = 0;
+  double* d_shmisc = nullptr;  // moments [bands][MO_WORDS] | share | dyb | lambda | pooled
+  size_t shmisc_cap = 0;
+  double2* d_shalpha = nullptr;  // [bands][kMaxH]
+  size_t shalpha_cap = 0;
+  double2* d_shcoef = nullptr;   // [4H+1][nf_pad] pooled coefficients
+  size_t shcoef_cap = 0;
 };
 
 namespace {
@@ -1398,7 +1413,8 @@ void ftp_destroy(ftp_plan_t P) {
   void* bptrs[] = {P->d_bsums, P->d_bmom, P->d_bobs, P->d_bout, P->d_bflags, P->d_bmark,
                    P->d_blist, P->d_bslot_curve, P->d_bcount, P->d_bredo_sums, P->d_bdesc,
                    P->d_bfeat, P->d_bscore, P->d_bsel, P->d_bulist, P->d_bucount,
-                   P->d_mb, P->d_mbflags, P->d_mbpow};
+                   P->d_mb, P->d_mbflags, P->d_mbpow, P->d_shsums, P->d_shmisc,
+                   P->d_shalpha, P->d_shcoef};
   for (void* p : bptrs)
     if (p) cudaFree(p);
   if (P->h_bdesc) cudaFreeHost(P->h_bdesc);
@@ -1759,6 +1775,135 @@ ftp_status ftp_multiband_periodogram(ftp_plan_t P, int nbands, const int64_t* ob
     FTP_CK(cudaMemcpyAsync(band_flags, P->d_mbflags, (size_t)items, cudaMemcpyDefault, P->stream));
   FTP_CK(cudaStreamSynchronize(P->stream));
   return FTP_OK;
+}
+
+ftp_status ftp_shared_multiband(ftp_plan_t P, int nbands, const int64_t* obs_off,
+                                const double* t, const double* y, const double* dy,
+                                const double* offsets, const ftp_template* bank, int nbank,
+                                const int32_t* tpl_of_band, double* power, double* theta1,
+                                double* theta2, double* theta3, uint8_t* flags) {
+  if (!P || nbands < 1 || !obs_off || !t || !y || !dy || !bank || nbank < 1 || !power ||
+      !theta1 || !theta2 || !theta3)
+    return FTP_ERR_INVALID_ARG;
+  if (nbands > 4096) return FTP_ERR_UNSUPPORTED;
+  ftp_status st = check_templates(P, bank, nbank);
+  if (st != FTP_OK) return st;
+  int H = 0;
+  for (int b = 0; b < nbands; ++b) {
+    const int q = tpl_of_band ? tpl_of_band[b] : 0;
+    if (q < 0 || q >= nbank) return FTP_ERR_INVALID_ARG;
+    const int64_t n = obs_off[b + 1] - obs_off[b];
+    if (obs_off[b] < 0 || n < 2) return FTP_ERR_INVALID_ARG;
+    if (n > P->max_nobs) return FTP_ERR_UNSUPPORTED;
+    H = std::max(H, bank[q].H);
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(P->device);
+  struct Restore {
+    int d;
+    ~Restore() { cudaSetDevice(d); }
+  } restore{prev};
+  const int64_t nf = P->grid.nf, nf_pad = P->nf_pad;
+  const int64_t band_elems = (int64_t)3 * H * nf_pad;
+  bool grew = false;
+  st = grow_dev(&P->d_shsums, &P->shsums_cap, (size_t)nbands * band_elems * P->csz, &grew);
+  if (st == FTP_OK)
+    st = grow_dev(&P->d_shmisc, &P->shmisc_cap, (size_t)nbands * (MO_WORDS + 3) + MO_WORDS, &grew);
+  if (st == FTP_OK) st = grow_dev(&P->d_shalpha, &P->shalpha_cap, (size_t)nbands * kMaxH, &grew);
+  if (st == FTP_OK)
+    st = grow_dev(&P->d_shcoef, &P->shcoef_cap, (size_t)(4 * H + 1) * nf_pad, &grew);
+  if (st != FTP_OK) return st;
+  double* mom = P->d_shmisc;
+  double* share = mom + (size_t)nbands * MO_WORDS;
+  double* dyb = share + nbands;
+  double* lam = dyb + nbands;
+  double* pooled = lam + nbands;
+  // band templates (zero-padded to H harmonics) and offsets
+  std::vector<double2> al((size_t)nbands * kMaxH, make_double2(0.0, 0.0));
+  for (int b = 0; b < nbands; ++b) {
+    const ftp_template& tp = bank[tpl_of_band ? tpl_of_band[b] : 0];
+    for (int n = 0; n < tp.H; ++n)
+      al[(size_t)b * kMaxH + n] = make_double2(0.5 * tp.c[n], 0.5 * tp.s[n]);
+  }
+  std::vector<double> lamh((size_t)nbands, 0.0);
+  if (offsets)
+    for (int b = 0; b < nbands; ++b) {
+      if (!isfinite(offsets[b])) return FTP_ERR_INVALID_ARG;
+      lamh[(size_t)b] = offsets[b];
+    }
+  cudaStream_t s = P->stream;
+  FTP_CK(reset_call(P));
+  FTP_CK(cudaMemcpyAsync(P->d_shalpha, al.data(), sizeof(double2) * al.size(),
+                         cudaMemcpyHostToDevice, s));
+  FTP_CK(cudaMemcpyAsync(lam, lamh.data(), sizeof(double) * nbands, cudaMemcpyHostToDevice, s));
+  FTP_CK(cudaStreamSynchronize(s));  // the host vectors go out of scope below
+  int launches = 0;
+  const int64_t J = 2 * (int64_t)H * (P->grid.k0 + nf - 1);
+  int64_t ntiles = 0;
+  const int64_t ngrid = grid_len(J, P->sigma, &ntiles);
+  for (int b = 0; b < nbands; ++b) {
+    const int64_t o = obs_off[b], n = obs_off[b + 1] - obs_off[b];
+    const double *dt, *dyv, *ddy;
+    st = stage_obs(P, t + o, y + o, dy + o, n, &dt, &dyv, &ddy);
+    if (st != FTP_OK) return st;
+    st = run_sums(P, P->l0, dt, dyv, ddy, n, P->grid.df, P->grid.k0, nf, H, ngrid, ntiles,
+                  mom + (size_t)b * MO_WORDS, P->d_shsums + (size_t)b * band_elems * P->csz,
+                  nf_pad, &launches);
+    if (st != FTP_OK) return st;
+  }
+  launch_shared_moments(mom, lam, nbands, share, dyb, pooled, P->d_status, s);
+  launch_shared_assembly(P->d_shsums, !P->mixed, band_elems, H, nbands, nf, nf_pad, H,
+                         P->d_shalpha, share, dyb, P->d_shcoef, P->d_status, s);
+  launches += 2;
+  const bool direct = is_device_ptr(power) && is_device_ptr(theta1) && is_device_ptr(theta2) &&
+                      is_device_ptr(theta3) && (!flags || is_device_ptr(flags));
+  double* o[4] = {power, theta1, theta2, theta3};
+  uint8_t* of = flags;
+  if (!direct) {
+    for (int i = 0; i < 4; ++i) o[i] = P->d_out + (size_t)i * P->max_templates * nf;
+    of = flags ? P->d_flags : nullptr;
+  }
+  RootsArgs a{};
+  a.sums = P->d_shcoef;
+  a.sums_elems = (int64_t)(4 * H + 1) * nf_pad;
+  a.out_elems = direct ? nf : (int64_t)P->max_templates * nf;
+  a.nf = nf;
+  a.nf_pad = nf_pad;
+  a.Hs = H;
+  a.H = H;
+  a.ntpl = 1;
+  a.alpha = P->d_shalpha;
+  a.rows = P->d_row0;
+  a.moments = pooled;
+  a.power = o[0];
+  a.theta1 = o[1];
+  a.theta2 = o[2];
+  a.theta3 = o[3];
+  a.flags = of;
+  a.out_stride = nf;
+  a.status = P->d_status;
+  a.counters = P->d_counters;
+  a.queue = P->d_queue;
+  a.maxit = P->maxit;
+  a.polish_steps = P->polish_steps;
+  a.ctas_per_sm = P->roots_ctas_per_sm;
+  a.positive_only = P->positive_only ? 1 : 0;
+  a.coef_mode = 1;
+  FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), s));
+  const int r = launch_roots(P->mixed ? ROOTS_REDO : ROOTS_FP64, a, P->num_sms, s);
+  if (r == -1) return FTP_ERR_UNSUPPORTED;
+  if (r < 0) return FTP_ERR_CUDA;
+  launches += r;
+  FTP_CK(cudaGetLastError());
+  if (!direct) {
+    double* dsto[4] = {power, theta1, theta2, theta3};
+    for (int i = 0; i < 4; ++i)
+      FTP_CK(cudaMemcpyAsync(dsto[i], o[i], sizeof(double) * nf, cudaMemcpyDefault, s));
+    if (flags) FTP_CK(cudaMemcpyAsync(flags, P->d_flags, nf, cudaMemcpyDefault, s));
+  }
+  P->last_launches = launches;
+  return finish(P);
 }
 
 ftp_status ftp_set_positive_amplitude(ftp_plan_t P, int enable) {

@@ -200,6 +200,9 @@ struct RootsArgs {
   const unsigned long long* unit_count;
   int ctas_per_sm;  // persistent grid: CTAs per SM (0 or more than fit: as many as fit)
   int positive_only;  // only candidates with theta1 > 0; none: P = 0 (FTP_FLAG_NO_POSITIVE)
+  // `sums` holds pre-assembled coefficients instead of sums: rows a_0..a_2H,
+  // b_1..b_H, c_1..c_H (4H+1 rows of nf_pad, pooled multi-band assembly)
+  int coef_mode;
 };
 
 // Kernel variants: float2 sums + FP32 Aberth (mixed), double2 sums + FP64

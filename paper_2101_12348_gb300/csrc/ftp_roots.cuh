@@ -68,6 +68,7 @@ struct Cfg {
   static constexpr int NGW = 32 / G;              // items per warp unit
   static constexpr int WARPS = 4;                 // warps per CTA
   static constexpr int ROWS = 3 * H;              // staged sum rows
+  static constexpr int CROWS = 4 * H + 1;         // staged coefficient rows (coef_mode)
   static constexpr int NA = 2 * H + 1;            // a_0..a_2H, Z_0..Z_2H
   static constexpr int NB = H + 1;                // b_0..b_H, c_0..c_H, Y_0..Y_H
   static constexpr int NF = 3 * H;                // F_0..F_{3H-1}
@@ -88,7 +89,7 @@ struct Cfg {
   static constexpr size_t GROUP_BYTES = rup(G_END, 16);
   // per-warp shared memory
   static constexpr size_t ROW_BYTES = NGW * sizeof(S2);
-  static constexpr size_t STAGE_BYTES = ROWS * ROW_BYTES;
+  static constexpr size_t STAGE_BYTES = (ROWS > CROWS ? ROWS : CROWS) * ROW_BYTES;
   static constexpr size_t W_STAGE = 0;                                   // 2 buffers
   static constexpr size_t W_MBAR = rup(2 * STAGE_BYTES, 16);             // 2 mbarriers
   static constexpr size_t W_KE = W_MBAR + 16;                            // K_e, e = 0..2H
@@ -385,11 +386,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     }
     S2* dst = stage + (size_t)buf * (C::STAGE_BYTES / sizeof(S2));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&mbar[buf], (unsigned)C::STAGE_BYTES);
+    const int nrows = a.coef_mode ? C::CROWS : C::ROWS;
+    mbar_expect_tx(&mbar[buf], (unsigned)(nrows * C::ROW_BYTES));
     const S2* sums = reinterpret_cast<const S2*>(a.sums);
 #pragma unroll 1
-    for (int r2 = 0; r2 < C::ROWS; ++r2) {
-      const int src_row = (r2 < 2 * H) ? r2 : 2 * Hs + (r2 - 2 * H);
+    for (int r2 = 0; r2 < nrows; ++r2) {
+      const int src_row = a.coef_mode ? r2 : (r2 < 2 * H) ? r2 : 2 * Hs + (r2 - 2 * H);
       const int64_t off = (int64_t)src_row * stride + base;
       if (!FTP_DCHECK(a.status, off >= 0 && off + NGW <= a.sums_elems, 11, off, a.sums_elems) ||
           !FTP_DCHECK(a.status, (gaddr(sums + off) & 15) == 0, 12, gaddr(sums + off) & 15, 16) ||
@@ -468,65 +470,95 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     const int64_t k = redo_pass ? cu.kfirst : cu.kfirst + gi;
     const bool valid = unit_ok && (redo_pass ? gi == 0 : k < seg_nf);
 
-    // ---- sums of this item into wide shared memory (one conversion each)
-    for (int q = gl; q < C::ROWS; q += G) {
-      const S2 v = st[q * NGW + gi];
-      WC wv;
-      if constexpr (C::kDD) {
-        wv = mkc(w_off<W>((float)v.x), w_off<W>((float)v.y));
-      } else {
-        wv = mkc((double)v.x, (double)v.y);
-      }
-      if (q < 2 * H) Z64[q + 1] = wv;
-      else Y64[q - 2 * H + 1] = wv;
-    }
-    if (gl == 0) {
-      Z64[0] = mkc(w_of<W>(1.0), w_zero<W>());
-      Y64[0] = c_zero<W>();
-    }
-    __syncwarp();
-
-    // ---- (b) assembly (FP64-class).  b_k = alpha_k conj(Y_k), c_n = alpha_n conj(Z_n)
     R amax2 = R(0), bmax2 = R(0);
-    for (int kk = gl; kk <= H; kk += G) {
-      WC bv = c_zero<W>(), cv = c_zero<W>();
-      if (kk > 0) {
-        bv = c_mul<W>(AL[kk - 1], c_conj<W>(Y64[kk]));
-        cv = c_mul<W>(AL[kk - 1], c_conj<W>(Z64[kk]));
-      }
-      B64[kk] = bv;
-      C64[kk] = cv;
-      const R2 bw = mk<R2>((R)w_f(re(bv)), (R)w_f(im(bv)));
-      Bw[kk] = bw;
-      bmax2 = fmax(bmax2, cabs2(bw));
-    }
-    __syncwarp();
-    // a_e = conj(Z_e) K_e - S_e over slots {0}, {e, 2H+1-e}
-    for (int s = gl; s < C::NSLOT; s += G) {
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        if (s == 0 && half == 1) break;
-        const int e = (s == 0) ? 0 : (half == 0 ? s : 2 * H + 1 - s);
-        WC acc;
-        if (e == 0) {
-          W q = w_zero<W>();
-          for (int n = 1; n <= H; ++n) q = w_add(q, c_abs2<W>(C64[n]));
-          acc = mkc(w_sub(re(KE[0]), w_mulf(q, 2.0f)), w_zero<W>());
+    if (a.coef_mode) {
+      // pre-assembled coefficients (a_0..a_2H, b_1..b_H, c_1..c_H) of this item
+      for (int q = gl; q < C::CROWS; q += G) {
+        const S2 v = st[q * NGW + gi];
+        WC wv;
+        if constexpr (C::kDD) {
+          wv = mkc(w_off<W>((float)v.x), w_off<W>((float)v.y));
         } else {
-          WC S = c_zero<W>();
-          const int nlo = e - H > 1 ? e - H : 1;
-          for (int n = nlo; 2 * n <= e; ++n) {  // sum_{n+m=e} c_n c_m, symmetric
-            const WC t = c_mul<W>(C64[n], C64[e - n]);
-            S = c_add<W>(S, (2 * n == e) ? t : c_mulf<W>(t, 2.0f));
-          }
-          for (int n = e + 1; n <= H; ++n)  // 2 sum_{n-m=e} c_n conj(c_m)
-            S = c_add<W>(S, c_mulf<W>(c_mul<W>(C64[n], c_conj<W>(C64[n - e])), 2.0f));
-          acc = c_sub<W>(c_mul<W>(c_conj<W>(Z64[e]), KE[e]), S);
+          wv = mkc((double)v.x, (double)v.y);
         }
-        A64[e] = acc;
-        const R2 aw = mk<R2>((R)w_f(re(acc)), (R)w_f(im(acc)));
-        Aw[e] = aw;
-        amax2 = fmax(amax2, cabs2(aw));
+        const R2 rw = mk<R2>((R)v.x, (R)v.y);
+        if (q <= 2 * H) {
+          A64[q] = wv;
+          Aw[q] = rw;
+          amax2 = fmax(amax2, cabs2(rw));
+        } else if (q <= 3 * H) {
+          B64[q - 2 * H] = wv;
+          Bw[q - 2 * H] = rw;
+          bmax2 = fmax(bmax2, cabs2(rw));
+        } else {
+          C64[q - 3 * H] = wv;
+        }
+      }
+      if (gl == 0) {
+        B64[0] = c_zero<W>();
+        C64[0] = c_zero<W>();
+        Bw[0] = mk<R2>(0, 0);
+      }
+    } else {
+      // ---- sums of this item into wide shared memory (one conversion each)
+      for (int q = gl; q < C::ROWS; q += G) {
+        const S2 v = st[q * NGW + gi];
+        WC wv;
+        if constexpr (C::kDD) {
+          wv = mkc(w_off<W>((float)v.x), w_off<W>((float)v.y));
+        } else {
+          wv = mkc((double)v.x, (double)v.y);
+        }
+        if (q < 2 * H) Z64[q + 1] = wv;
+        else Y64[q - 2 * H + 1] = wv;
+      }
+      if (gl == 0) {
+        Z64[0] = mkc(w_of<W>(1.0), w_zero<W>());
+        Y64[0] = c_zero<W>();
+      }
+      __syncwarp();
+
+      // ---- (b) assembly (FP64-class).  b_k = alpha_k conj(Y_k), c_n = alpha_n conj(Z_n)
+      for (int kk = gl; kk <= H; kk += G) {
+        WC bv = c_zero<W>(), cv = c_zero<W>();
+        if (kk > 0) {
+          bv = c_mul<W>(AL[kk - 1], c_conj<W>(Y64[kk]));
+          cv = c_mul<W>(AL[kk - 1], c_conj<W>(Z64[kk]));
+        }
+        B64[kk] = bv;
+        C64[kk] = cv;
+        const R2 bw = mk<R2>((R)w_f(re(bv)), (R)w_f(im(bv)));
+        Bw[kk] = bw;
+        bmax2 = fmax(bmax2, cabs2(bw));
+      }
+      __syncwarp();
+      // a_e = conj(Z_e) K_e - S_e over slots {0}, {e, 2H+1-e}
+      for (int s = gl; s < C::NSLOT; s += G) {
+  #pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          if (s == 0 && half == 1) break;
+          const int e = (s == 0) ? 0 : (half == 0 ? s : 2 * H + 1 - s);
+          WC acc;
+          if (e == 0) {
+            W q = w_zero<W>();
+            for (int n = 1; n <= H; ++n) q = w_add(q, c_abs2<W>(C64[n]));
+            acc = mkc(w_sub(re(KE[0]), w_mulf(q, 2.0f)), w_zero<W>());
+          } else {
+            WC S = c_zero<W>();
+            const int nlo = e - H > 1 ? e - H : 1;
+            for (int n = nlo; 2 * n <= e; ++n) {  // sum_{n+m=e} c_n c_m, symmetric
+              const WC t = c_mul<W>(C64[n], C64[e - n]);
+              S = c_add<W>(S, (2 * n == e) ? t : c_mulf<W>(t, 2.0f));
+            }
+            for (int n = e + 1; n <= H; ++n)  // 2 sum_{n-m=e} c_n conj(c_m)
+              S = c_add<W>(S, c_mulf<W>(c_mul<W>(C64[n], c_conj<W>(C64[n - e])), 2.0f));
+            acc = c_sub<W>(c_mul<W>(c_conj<W>(Z64[e]), KE[e]), S);
+          }
+          A64[e] = acc;
+          const R2 aw = mk<R2>((R)w_f(re(acc)), (R)w_f(im(acc)));
+          Aw[e] = aw;
+          amax2 = fmax(amax2, cabs2(aw));
+        }
       }
     }
     __syncwarp();

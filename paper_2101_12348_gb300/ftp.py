@@ -43,7 +43,8 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_mlp_get_params", "ftp_mlp_set_params", "ftp_mlp_forward", "ftp_mlp_gradient",
            "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows",
            "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune",
-           "ftp_set_positive_amplitude", "ftp_multiband_periodogram")
+           "ftp_set_positive_amplitude", "ftp_multiband_periodogram",
+           "ftp_shared_multiband")
 
 
 class FtpGrid(C.Structure):
@@ -113,6 +114,8 @@ def load(path: str | None = None) -> C.CDLL:
                                       C.POINTER(i64), i32, vp]
     lib.ftp_set_batch_tuning.argtypes = [vp, i32, i32]
     lib.ftp_set_positive_amplitude.argtypes = [vp, i32]
+    lib.ftp_shared_multiband.argtypes = [vp, i32, vp, vp, vp, vp, vp, C.POINTER(FtpTemplate), i32,
+                                         vp, vp, vp, vp, vp, vp]
     lib.ftp_multiband_periodogram.argtypes = [vp, i32, vp, vp, vp, vp, C.POINTER(FtpTemplate),
                                               i32, vp, vp, vp, vp, vp, vp, vp]
     lib.ftp_get_batch_tuning.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
@@ -313,6 +316,19 @@ def ftp_multiband_periodogram(plan: int, obs_off, t, y, dy, bank, tpl_of_band, p
                                             _ptr(power), _ptr(band_power), _ptr(band_theta1),
                                             _ptr(band_theta2), _ptr(band_theta3),
                                             _ptr(band_flags)), "ftp_multiband_periodogram")
+
+
+def ftp_shared_multiband(plan: int, obs_off, t, y, dy, offsets, bank, tpl_of_band, power,
+                         theta1, theta2, theta3, flags=None) -> None:
+    """Shared-phase multi-band template periodogram (see include/ftp.h)."""
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    lam = None if offsets is None else np.ascontiguousarray(offsets, dtype=np.float64)
+    arr, keep = _templates(bank)
+    tob = None if tpl_of_band is None else np.ascontiguousarray(tpl_of_band, dtype=np.int32)
+    _check(load().ftp_shared_multiband(plan, obs_off.shape[0] - 1, _ptr(obs_off), _ptr(t), _ptr(y),
+                                       _ptr(dy), _ptr(lam), arr, len(keep) // 2, _ptr(tob),
+                                       _ptr(power), _ptr(theta1), _ptr(theta2), _ptr(theta3),
+                                       _ptr(flags)), "ftp_shared_multiband")
 
 
 def ftp_set_positive_amplitude(plan: int, enable: bool) -> None:

@@ -371,3 +371,48 @@ def test_multiband_periodogram(ftp, prec):
     assert np.max(np.abs(bp - ref["band_power"])) <= TOL_P[prec]
     assert np.max(np.abs(pd.cpu().numpy() - p)) <= 2 * TOL_P[prec]
     assert np.all(p >= bp.min(axis=0) - 1e-12) and np.all(p <= bp.max(axis=0) + 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_shared_phase_multiband(ftp, prec):
+    """ftp_shared_multiband: three bands with their own templates (H = 2, 3, 3)
+    and fixed offsets sharing one amplitude, phase and offset, every frequency
+    against the oracle's pooled Appendix A periodogram; host and device
+    arrays agree; a single band reproduces ftp_periodogram."""
+    rng = np.random.default_rng(99)
+    bands, lam = [], np.array([0.0, 1.1, -0.6])
+    for b, (n, H) in enumerate([(80, 3), (50, 2), (120, 3)]):
+        tpl = synth.make_template(H, 3600 + b)
+        t = np.sort(rng.uniform(0, 30.0, n))
+        dy = rng.uniform(0.05, 0.15, n)
+        y = 0.5 * tpl(2 * np.pi * t / 2.9 - 0.4) + 0.1 + lam[b] + dy * rng.standard_normal(n)
+        bands.append((t, y, dy, tpl))
+    nf = 800
+    grid = synth.Grid(df=1 / 150.0, k0=1, nf=nf)
+    freqs = grid.freqs()
+    ref = oracle.shared_phase_multiband([(t, y, dy, tp.c, tp.s) for t, y, dy, tp in bands], freqs,
+                                        lam)
+    off = np.cumsum([0] + [b[0].size for b in bands]).astype(np.int64)
+    t = np.concatenate([b[0] for b in bands])
+    y = np.concatenate([b[1] for b in bands])
+    dy = np.concatenate([b[2] for b in bands])
+    bank = [(tp.c, tp.s) for *_, tp in bands]
+    with ftp.Plan(int(np.max(np.diff(off))), 3, (grid.df, grid.k0, nf), 3, prec) as plan:
+        out = [np.empty(nf) for _ in range(4)]
+        fl = np.empty(nf, dtype=np.uint8)
+        ftp.ftp_shared_multiband(plan.h, off, t, y, dy, lam, bank, np.arange(3), *out, fl)
+        dev = [torch.empty(nf, dtype=torch.float64, device="cuda") for _ in range(4)]
+        ftp.ftp_shared_multiband(plan.h, off, *(torch.from_numpy(a).cuda() for a in (t, y, dy)),
+                                 lam, bank, np.arange(3), *dev)
+        one = [np.empty(nf) for _ in range(4)]
+        ftp.ftp_shared_multiband(plan.h, off[:2], t, y, dy, None, bank, None, *one)
+        single = plan.periodogram(bands[0][0], bands[0][1], bands[0][2], [bank[0]])
+    dP = np.abs(out[0] - ref["power"])
+    assert dP.max() <= TOL_P[prec], dP.max()
+    g = {"power": out[0], "theta1": out[1], "theta2": out[2], "theta3": out[3]}
+    k = int(np.argmax(ref["power"]))
+    assert phase_err(g["theta2"][k], ref["theta2"][k]) <= TOL_PHASE[prec]
+    assert abs(g["theta1"][k] - ref["theta1"][k]) <= TOL_AMP[prec] * max(1, abs(ref["theta1"][k]))
+    assert abs(g["theta3"][k] - ref["theta3"][k]) <= TOL_AMP[prec] * max(1, abs(ref["theta3"][k]))
+    assert np.max(np.abs(dev[0].cpu().numpy() - out[0])) <= 2 * TOL_P[prec]
+    assert np.max(np.abs(one[0] - single["power"][0])) <= 2 * TOL_P[prec]
