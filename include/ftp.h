@@ -314,6 +314,20 @@ ftp_status ftp_set_timing(ftp_plan_t plan, int enable);
 ftp_status ftp_stage_times(ftp_plan_t plan, float* ms6);
 
 /*
+ * ftp_roots_first_phase_ms - device time (milliseconds, CUDA events on the
+ * plan's stream) of the first of the two root-stage kernels in the last
+ * timed ftp_periodogram call, summed over its template groups: assembly of
+ * the polynomial of Section 2, the Aberth-Ehrlich iterations and the choice of
+ * the best candidate root (Section 2, final polynomial and its roots).  The
+ * second kernel (FP64-class polish and evaluation at that root, outputs)
+ * takes the rest of stage [4] of ftp_stage_times.  The re-solve pass is not
+ * included.  Zero unless timing was enabled with ftp_set_timing(plan, 1);
+ * not recorded by ftp_batch.  Errors: FTP_ERR_INVALID_ARG for a null plan or
+ * pointer.
+ */
+ftp_status ftp_roots_first_phase_ms(ftp_plan_t plan, float* ms);
+
+/*
  * ftp_periodogram_sums_noalloc - steps (b)-(c) on sums the caller already
  * holds, allocating nothing.  The paper has no counterpart: this is an entry
  * point for callers that cannot call cudaMalloc - a process whose device

@@ -110,7 +110,7 @@ struct ftp_plan_s {
   unsigned char* d_mom_scratch = nullptr;  // moment partials + ticket
   int* d_status = nullptr;
   unsigned long long* d_counters = nullptr;
-  unsigned long long* d_queue = nullptr;  // work-unit counter of the roots kernel
+  unsigned long long* d_queue = nullptr;  // work-unit counters of the two roots kernels
   int* d_redo_list = nullptr;            // frequencies to re-solve from direct FP64 sums
   int* d_redo_mark = nullptr;
   int* d_redo_count = nullptr;
@@ -149,6 +149,10 @@ struct ftp_plan_s {
   bool timing = false;
   cudaEvent_t ev[7] = {};
   float stage_ms[6] = {};
+  // first roots kernel of each template group (timing only)
+  cudaEvent_t fev[2 * kMaxH] = {};
+  int fev_used = 0;
+  float first_phase_ms = 0.f;
   int maxit = 60;
   int polish_steps = 1;
   // ---- batch workspace (grown on demand by ftp_batch; never shrinks)
@@ -426,6 +430,11 @@ ftp_status finish(ftp_plan_t P) {
     float ms;
     for (int i = 0; i < 6; ++i)
       if (cudaEventElapsedTime(&ms, P->ev[i], P->ev[i + 1]) == cudaSuccess) P->stage_ms[i] = ms;
+    P->first_phase_ms = 0.f;
+    for (int g = 0; g < P->fev_used; ++g)
+      if (cudaEventElapsedTime(&ms, P->fev[2 * g], P->fev[2 * g + 1]) == cudaSuccess)
+        P->first_phase_ms += ms;
+    P->fev_used = 0;
     cudaGetLastError();
   }
   return (ftp_status)P->h_status[ST_CODE];
@@ -481,8 +490,14 @@ ftp_status upload_templates(ftp_plan_t P, const ftp_template* tpl, int ntpl,
 ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int Hs, int64_t nf,
                      const int* nf_dev, const int* kmap, bool collect_redo, const double2* alpha,
                      const int* rows, int ntpl, double* const* o, uint8_t* flags,
-                     int64_t out_stride, int64_t out_elems, int* launches) {
+                     int64_t out_stride, int64_t out_elems, int* launches, bool time_first = false) {
   RootsArgs a{};
+  if (time_first && P->timing && !P->in_batch && P->fev_used < kMaxH &&
+      P->fev[2 * P->fev_used]) {
+    a.ev_first_start = P->fev[2 * P->fev_used];
+    a.ev_first_end = P->fev[2 * P->fev_used + 1];
+    ++P->fev_used;
+  }
   a.sums = sums;
   a.sums_elems = (int64_t)3 * P->max_H * P->nf_pad;
   a.out_elems = out_elems;
@@ -547,7 +562,7 @@ ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double
   for (const HGroup& g : groups) {
     ftp_status st = run_roots(P, kind, P->d_sums, g.H, Hs, nf, nullptr, nullptr, redo,
                               alpha + (size_t)g.first * kMaxH, row0 ? row0 : rows + g.first,
-                              g.count, o, flags, nf, out_elems, launches);
+                              g.count, o, flags, nf, out_elems, launches, true);
     if (st != FTP_OK) return st;
   }
   ev_rec(P, 5);
@@ -1427,6 +1442,8 @@ void ftp_destroy(ftp_plan_t P) {
   if (P->h_rows) cudaFreeHost(P->h_rows);
   for (auto& e : P->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : P->fev)
+    if (e) cudaEventDestroy(e);
   if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
   delete P;
   cudaSetDevice(prev);
@@ -1498,7 +1515,7 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
   FTP_AL(P->d_mom_scratch, kMomentScratchBytes);
   FTP_AL(P->d_status, ST_WORDS);
   FTP_AL(P->d_counters, CNT_WORDS);
-  FTP_AL(P->d_queue, 1);
+  FTP_AL(P->d_queue, 2);  // one work counter per roots phase
   FTP_AL(P->d_redo_list, (size_t)grid.nf);
   FTP_AL(P->d_redo_mark, (size_t)grid.nf);
   FTP_AL(P->d_redo_count, 1);
@@ -1586,6 +1603,22 @@ ftp_status ftp_solver_stats(ftp_plan_t P, int64_t* items, double* mean_iteration
 ftp_status ftp_set_timing(ftp_plan_t P, int enable) {
   if (!P) return FTP_ERR_INVALID_ARG;
   P->timing = enable != 0;
+  if (P->timing && !P->fev[0]) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(P->device);
+    bool ok = true;
+    for (auto& e : P->fev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    cudaSetDevice(prev);
+    if (!ok) return FTP_ERR_CUDA;
+  }
+  P->fev_used = 0;
+  return FTP_OK;
+}
+
+ftp_status ftp_roots_first_phase_ms(ftp_plan_t P, float* ms) {
+  if (!P || !ms) return FTP_ERR_INVALID_ARG;
+  *ms = P->first_phase_ms;
   return FTP_OK;
 }
 

@@ -167,7 +167,7 @@ struct RootsArgs {
   int64_t out_stride;
   int* status;
   unsigned long long* counters;  // CNT_* solver statistics
-  unsigned long long* queue;     // work-unit counter, zero at launch
+  unsigned long long* queue;     // two work-unit counters: [0] zero at launch, [1] cleared by the first roots kernel
   // re-solve list (mixed path): frequencies whose estimated error of P from
   // the FP32 sums exceeds kRedoTol; nullable (no re-solve)
   int* redo_list;
@@ -198,6 +198,10 @@ struct RootsArgs {
   // nullable (every unit)
   const int64_t* unit_list;
   const unsigned long long* unit_count;
+  // host side, nullable: events recorded on the launch stream before the
+  // first roots kernel and between the two (timing of the first phase)
+  cudaEvent_t ev_first_start;
+  cudaEvent_t ev_first_end;
   int ctas_per_sm;  // persistent grid: CTAs per SM (0 or more than fit: as many as fit)
   int positive_only;  // only candidates with theta1 > 0; none: P = 0 (FTP_FLAG_NO_POSITIVE)
   // `sums` holds pre-assembled coefficients instead of sums: rows a_0..a_2H,

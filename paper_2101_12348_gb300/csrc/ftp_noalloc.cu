@@ -33,7 +33,7 @@ using namespace ftp;
 // Layout of the scratch array (bytes).
 constexpr size_t kOffStatus = 0;                       // int[ST_WORDS]
 constexpr size_t kOffCounters = 64;                    // unsigned long long[CNT_WORDS]
-constexpr size_t kOffQueue = 128;                      // unsigned long long
+constexpr size_t kOffQueue = 128;                      // unsigned long long[2]
 constexpr size_t kOffMoments = 192;                    // double[MO_WORDS]
 constexpr size_t kOffRows = 256;                       // int[FTP_NOALLOC_MAX_TEMPLATES]
 constexpr size_t kOffAlpha = 512;                      // double2[max templates][kMaxH]

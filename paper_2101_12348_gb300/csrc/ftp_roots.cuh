@@ -86,7 +86,10 @@ struct Cfg {
   static constexpr size_t G_AW = G_Z + rup(RR * G * sizeof(R2), 16);
   static constexpr size_t G_BW = G_AW + rup(NA * sizeof(R2), 16);
   static constexpr size_t G_END = G_BW + rup(NB * sizeof(R2), 16);
-  static constexpr size_t GROUP_BYTES = rup(G_END, 16);
+  // An odd number of 16-byte words per group: the NGW (<= 8) groups of a warp
+  // then start in distinct 16-byte bank slots, so the per-group broadcasts of
+  // the Aberth loops (F_c, z_j) and of the assembly are free of bank conflicts.
+  static constexpr size_t GROUP_BYTES = rup(G_END, 16) + ((rup(G_END, 16) / 16) % 2 == 0 ? 16 : 0);
   // per-warp shared memory
   static constexpr size_t ROW_BYTES = NGW * sizeof(S2);
   static constexpr size_t STAGE_BYTES = (ROWS > CROWS ? ROWS : CROWS) * ROW_BYTES;
@@ -142,6 +145,15 @@ __device__ __forceinline__ float fast_rcp(float x) {
   return r;
 }
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+// 2^x: one MUFU instruction (initial guesses only)
+__device__ __forceinline__ float fast_exp2(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// 1/sqrt(x): one MUFU instruction in FP32 (candidate phases only need a few ulp)
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 template <typename T2> __device__ __forceinline__ T2 cdiv(T2 a, T2 b) {
   const auto inv = fast_rcp(cabs2(b));
   return mk<T2>((a.x * b.x + a.y * b.y) * inv, (a.y * b.x - a.x * b.y) * inv);
@@ -245,7 +257,7 @@ template <typename T2>
 __device__ __forceinline__ auto pseudo_angle(T2 p) -> decltype(p.x) {
   using T = decltype(p.x);
   const T ax = p.x < T(0) ? -p.x : p.x, ay = p.y < T(0) ? -p.y : p.y;
-  const T q = ay / (ax + ay + T(1e-30));  // in [0, 1]
+  const T q = ay * fast_rcp(ax + ay + T(1e-30));  // in [0, 1]
   // quadrants I..IV map to [0,1), [1,2), [2,3), [3,4)
   if (p.y >= T(0)) return p.x >= T(0) ? q : T(2) - q;
   return p.x < T(0) ? T(2) + q : T(4) - q;
@@ -261,7 +273,17 @@ __device__ __forceinline__ T trig_eval(const T2* c, int n, T2 psi, T v0) {
   return v0 + T(2) * acc.x;
 }
 
-template <typename S2, typename R, int H, int G>
+// The work of one item runs in two kernels over the same work units:
+//   PH = 1  assembly, final polynomial, Aberth iterations and candidate
+//           choice; it leaves the chosen phase psi and three flag bits in the
+//           item's output slots (power <- Re psi, theta1 <- Im psi,
+//           theta2 <- bits);
+//   PH = 2  assembly again (FP64-class), polish and evaluation at psi, the
+//           a-posteriori error and the outputs.
+// Each kernel's code is a fraction of the whole, so the warps of an SM, which
+// are at different points of their items, share far fewer instructions in the
+// instruction caches than one fused kernel would make them fetch.
+template <typename S2, typename R, int H, int G, int PH>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(const RootsArgs a) {
   using namespace wide;
   using C = Cfg<S2, R, H, G>;
@@ -295,6 +317,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
   R2* Aw = reinterpret_cast<R2*>(gb + C::G_AW);  // working-precision copies
   R2* Bw = reinterpret_cast<R2*>(gb + C::G_BW);
 
+  // one work counter per phase; the first kernel clears the second's (the
+  // second runs after it on the same stream)
+  unsigned long long* const queue = PH == 1 ? a.queue : a.queue + 1;
+  if (PH == 1 && blockIdx.x == 0 && threadIdx.x == 0) a.queue[1] = 0ull;
   if (a.status[ST_CODE] != DEV_OK) return;
   // Three ways to number the work units:
   //   one curve      (segs == nullptr): unit = tau * nkb + kb over a.ntpl
@@ -329,7 +355,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
 
   auto grab = [&]() -> int64_t {
     unsigned long long v = 0;
-    if (lane == 0) v = atomicAdd(a.queue, 1ull);
+    if (lane == 0) v = atomicAdd(queue, 1ull);
     return (int64_t)__shfl_sync(0xffffffffu, v, 0);
   };
   // Segment of unit u (batched main pass): the last s >= lo with
@@ -484,12 +510,16 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         const R2 rw = mk<R2>((R)v.x, (R)v.y);
         if (q <= 2 * H) {
           A64[q] = wv;
-          Aw[q] = rw;
-          amax2 = fmax(amax2, cabs2(rw));
+          if constexpr (PH == 1) {
+            Aw[q] = rw;
+            amax2 = fmax(amax2, cabs2(rw));
+          }
         } else if (q <= 3 * H) {
           B64[q - 2 * H] = wv;
-          Bw[q - 2 * H] = rw;
-          bmax2 = fmax(bmax2, cabs2(rw));
+          if constexpr (PH == 1) {
+            Bw[q - 2 * H] = rw;
+            bmax2 = fmax(bmax2, cabs2(rw));
+          }
         } else {
           C64[q - 3 * H] = wv;
         }
@@ -527,9 +557,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         }
         B64[kk] = bv;
         C64[kk] = cv;
-        const R2 bw = mk<R2>((R)w_f(re(bv)), (R)w_f(im(bv)));
-        Bw[kk] = bw;
-        bmax2 = fmax(bmax2, cabs2(bw));
+        if constexpr (PH == 1) {  // working-precision copy for the root search
+          const R2 bw = mk<R2>((R)w_f(re(bv)), (R)w_f(im(bv)));
+          Bw[kk] = bw;
+          bmax2 = fmax(bmax2, cabs2(bw));
+        }
       }
       __syncwarp();
       // a_e = conj(Z_e) K_e - S_e over slots {0}, {e, 2H+1-e}
@@ -555,16 +587,42 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
             acc = c_sub<W>(c_mul<W>(c_conj<W>(Z64[e]), KE[e]), S);
           }
           A64[e] = acc;
-          const R2 aw = mk<R2>((R)w_f(re(acc)), (R)w_f(im(acc)));
-          Aw[e] = aw;
-          amax2 = fmax(amax2, cabs2(aw));
+          if constexpr (PH == 1) {
+            const R2 aw = mk<R2>((R)w_f(re(acc)), (R)w_f(im(acc)));
+            Aw[e] = aw;
+            amax2 = fmax(amax2, cabs2(aw));
+          }
         }
       }
     }
     __syncwarp();
-    amax2 = gmax<G>(amax2);
-    bmax2 = gmax<G>(bmax2);
+    if constexpr (PH == 1) {
+      amax2 = gmax<G>(amax2);
+      bmax2 = gmax<G>(bmax2);
+    }
 
+    // ---- this item's output slot (both phases)
+    int64_t col = 0, ridx = 0, ostride = a.out_stride;
+    size_t o = 0;
+    if (valid) {
+      if (!batched) {
+        col = a.kmap ? (int64_t)a.kmap[k] : k;
+        o = (size_t)a.rows[tau] * a.out_stride + col;
+        ridx = col;
+      } else {
+        const RootsSeg& sg = a.segs[cu.seg];
+        col = redo_pass ? (int64_t)a.kmap[k] - sg.redo_base : k;
+        const int row = sg.row_first < 0 ? 0 : a.rows[sg.row_first + cu.tl];
+        o = (size_t)(sg.out_off + (int64_t)row * sg.nf + col);
+        ostride = sg.nf;
+        ridx = sg.redo_base + col;
+      }
+    }
+    const bool in_range =
+        FTP_DCHECK(a.status, !valid || (col >= 0 && col < ostride), 21, col, ostride) &&
+        FTP_DCHECK(a.status, !valid || (int64_t)o < a.out_elems, 22, o, a.out_elems);
+
+    if constexpr (PH == 1) {
     // ---- final polynomial F_p, p = 0..3H-1, in the working precision:
     //      [psi^p] (2 MM' d(YM') - YM' d(MM')) = sum_{j+l=p+1} (2l - j) m_j y_l
     R2 Fl[C::NFL];
@@ -603,21 +661,81 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       }
     }
 
+    // ---- initial guesses from the Newton polygon of F (Bini's rule): the
+    //      upper convex hull of the points (k, log2|F_k|^2), k = 0..D.  An
+    //      edge from vertex a to vertex b stands for b - a roots of modulus
+    //      about 2^(-slope/2).  F is anti-self-inversive (|F_k| = |F_{D-k}|),
+    //      so the hull is symmetric about D/2: only k <= D/2 are tested, slot
+    //      m < D/2 takes the m-th root counted from the innermost circle and
+    //      slot D/2 + m its mirror 1/conj(z), half a step further round.  The
+    //      circles' angles are offset by golden-ratio multiples of their first
+    //      vertex, so that no two circles start aligned.  Every lane tests
+    //      vertices k = gl, gl + G, ... against all other points (strict test:
+    //      collinear points are not vertices), in FP32 for either precision.
+    constexpr int HD = D / 2;
+    constexpr int NKV = cdiv_i(HD + 1, G);
+    __syncwarp();
+    float* Lg = reinterpret_cast<float*>(Z64);  // the sums are dead after the assembly
+    for (int q = gl; q <= HD; q += G) {
+      const float fx = (float)Fs[q].x, fy = (float)Fs[q].y;
+      Lg[q] = __log2f(fmaf(fx, fx, fmaf(fy, fy, 1.17549435e-38f)));
+    }
+    __syncwarp();
+    unsigned long long vmask = 1ull;  // k = 0 is always a vertex
+    {
+      float Lk[NKV], minl[NKV], maxr[NKV];
+#pragma unroll
+      for (int v = 0; v < NKV; ++v) {
+        const int k = gl + G * v;
+        Lk[v] = k <= HD ? Lg[k] : 0.0f;
+        minl[v] = __int_as_float(0x7f800000);
+        maxr[v] = -__int_as_float(0x7f800000);
+      }
+#pragma unroll 1
+      for (int d = 1; d <= D; ++d) {
+        const float inv = fast_rcp((float)d);
+#pragma unroll
+        for (int v = 0; v < NKV; ++v) {
+          const int k = gl + G * v;
+          if (k > HD) continue;
+          if (d <= k) minl[v] = fminf(minl[v], (Lk[v] - Lg[k - d]) * inv);
+          const int j = k + d;
+          if (j <= D) maxr[v] = fmaxf(maxr[v], (Lg[j <= HD ? j : D - j] - Lk[v]) * inv);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NKV; ++v) {
+        const int k = gl + G * v;
+        if (k <= HD && minl[v] > maxr[v]) vmask |= 1ull << k;
+      }
+    }
+#pragma unroll
+    for (int sh = G / 2; sh > 0; sh >>= 1) vmask |= __shfl_xor_sync(0xffffffffu, vmask, sh, G);
+
     // ---- (c) Aberth-Ehrlich on F (degree D), roots i = r*G + gl
     R2 z[RR];
     bool conv[RR];
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
       const int i = r * G + gl;
-      R sn, cs;
-      const R ang = kTwoPi * (R)i / (R)D + R(0.4);
-      if constexpr (kFast) {
+      z[r] = mk<R2>(0, 0);
+      if (i < D) {
+        const bool outer = i >= HD;
+        const int m = outer ? i - HD : i;
+        const unsigned long long below = (2ull << m) - 1ull;  // bits 0..m
+        const int va = 63 - __clzll(vmask & below);           // last vertex <= m
+        const unsigned long long above = vmask & ~below;
+        const int vb = above ? __ffsll(above) - 1 : D - va;  // next vertex (or the mirror of va)
+        const int cnt = min(vb, HD) - va;                     // roots of this circle in slots < D/2
+        const float slope = (Lg[vb <= HD ? vb : D - vb] - Lg[va]) * fast_rcp((float)(2 * (vb - va)));
+        const float lr = fminf(fmaxf(-slope, -12.0f), 12.0f);  // log2 of the inner modulus
+        const float ang = 6.2831853f * ((float)(m - va) + (outer ? 0.5f : 0.0f)) * fast_rcp((float)cnt) +
+                          0.4f + 3.8832221f * (float)va;       // 2 pi (golden ratio - 1) per vertex
+        float sn, cs;
         __sincosf(ang, &sn, &cs);
-      } else {
-        sincos(ang, &sn, &cs);
+        const float rad = fast_exp2(outer ? -lr : lr);
+        z[r] = mk<R2>((R)(rad * cs), (R)(rad * sn));
       }
-      const R rad = (i & 1) ? R(0.5) : R(2);
-      z[r] = mk<R2>(rad * cs, rad * sn);
       conv[r] = (i >= D) || constant;
       if (i < D) Zs[i] = z[r];
     }
@@ -694,65 +812,91 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     for (int r = 0; r < RR; ++r) lane_nc = lane_nc || !conv[r];
     const bool nonconv = gor<G>(lane_nc) && !constant;
 
-    // ---- candidates: P at every root scaled onto |psi| = 1 (working precision)
-    R sc[RR], th[RR];
-    R2 ps[RR];
-    bool pos[RR];
+    // ---- candidates: P at every root scaled onto |psi| = 1 (working precision).
+    //      Rolled loops over the lane's root slots (roots read back from
+    //      shared memory): this phase runs once per item, so its code is kept
+    //      short rather than unrolled.
+    R sc[RR], key[RR];
     R lmax = R(-1);
     const R a0w = Aw[0].x;
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < RR; ++r) {
       const int i = r * G + gl;
-      sc[r] = R(-1);
-      th[r] = R(0);
-      pos[r] = false;
-      ps[r] = mk<R2>(1, 0);
+      R s = R(-1), kk = R(0);
       bool have = false;
+      R2 p = mk<R2>(1, 0);
       if (constant) {
         have = (i == 0);
       } else if (i < D) {
-        const R m2 = cabs2(z[r]);
+        const R2 zi = Zs[i];
+        const R m2 = cabs2(zi);
         have = m2 > R(0) && isfinite(m2);
-        const R inv = have ? R(1) / sqrt(m2) : R(0);
-        ps[r] = mk<R2>(z[r].x * inv, z[r].y * inv);
+        const R inv = have ? fast_rsqrt(m2) : R(0);
+        p = mk<R2>(zi.x * inv, zi.y * inv);
       }
       if (have) {
-        const R mm = trig_eval(Aw, 2 * H, ps[r], a0w);
-        const R ym = trig_eval(Bw, H, ps[r], R(0));
-        sc[r] = (mm > R(1e-9) * a0w) ? ym * ym / mm : R(0);
-        pos[r] = ym > R(0);
+        const R mm = trig_eval(Aw, 2 * H, p, a0w);
+        const R ym = trig_eval(Bw, H, p, R(0));
+        s = (mm > R(1e-9) * a0w) ? ym * ym * fast_rcp(mm) : R(0);
+        const bool pos = ym > R(0);
         // positive-amplitude mode: only candidates with theta1 = YM/MM > 0
-        if (a.positive_only && !pos[r]) sc[r] = R(-1);
-        th[r] = pseudo_angle(ps[r]);
-        lmax = fmax(lmax, sc[r]);
+        if (a.positive_only && !pos) s = R(-1);
+        kk = (pos ? R(0) : R(16)) + pseudo_angle(p);
+        lmax = fmax(lmax, s);
       }
+      sc[r] = s;
+      key[r] = kk;
     }
     const R pmax = gmax<G>(lmax);
     const R thr = pmax - tie * (pmax > R(0) ? pmax : R(0));
     // among candidates within the tie band: theta1 > 0 first, then smallest
     // theta2; the winner's psi travels with its key
     R bkey = R(1e30);
-    R2 bpsi = mk<R2>(1, 0);
-#pragma unroll
+    int bslot = -1;
+#pragma unroll 1
     for (int r = 0; r < RR; ++r)
-      if (sc[r] >= thr && sc[r] >= R(0)) {
-        const R key = (pos[r] ? R(0) : R(16)) + th[r];
-        if (key < bkey) {
-          bkey = key;
-          bpsi = ps[r];
-        }
+      if (sc[r] >= thr && sc[r] >= R(0) && key[r] < bkey) {
+        bkey = key[r];
+        bslot = r * G + gl;
       }
+    R2 bpsi = mk<R2>(1, 0);
+    if (bslot >= 0 && !constant) {
+      const R2 zi = Zs[bslot];
+      const R inv = fast_rsqrt(cabs2(zi));
+      bpsi = mk<R2>(zi.x * inv, zi.y * inv);
+    }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const R ok = __shfl_xor_sync(0xffffffffu, bkey, o, G);
-      const R ox = __shfl_xor_sync(0xffffffffu, bpsi.x, o, G);
-      const R oy = __shfl_xor_sync(0xffffffffu, bpsi.y, o, G);
-      if (ok < bkey || (ok == bkey && (lane ^ o) < lane)) {
+    for (int sh = G / 2; sh > 0; sh >>= 1) {
+      const R ok = __shfl_xor_sync(0xffffffffu, bkey, sh, G);
+      const R ox = __shfl_xor_sync(0xffffffffu, bpsi.x, sh, G);
+      const R oy = __shfl_xor_sync(0xffffffffu, bpsi.y, sh, G);
+      if (ok < bkey || (ok == bkey && (lane ^ sh) < lane)) {
         bkey = ok;
         bpsi = mk<R2>(ox, oy);
       }
     }
     const bool no_candidate = !(bkey < R(1e29));
+    // the chosen phase and the flags for the second kernel
+    {
+      const unsigned bits = (constant ? 1u : 0u) | (nonconv ? 2u : 0u) | (no_candidate ? 4u : 0u);
+      const double rv = gl == 0 ? (double)bpsi.x : gl == 1 ? (double)bpsi.y : (double)bits;
+      if (valid && in_range && gl < 3) (gl == 0 ? a.power : gl == 1 ? a.theta1 : a.theta2)[o] = rv;
+    }
+    if (valid && in_range && gl == 0) {
+      st_iters += (unsigned long long)iters;
+      st_items += 1;
+      st_nonconv += nonconv ? 1 : 0;
+    }
+    } else {
+    bool constant = true, nonconv = false, no_candidate = false;
+    R2 bpsi = mk<R2>(1, 0);
+    if (valid && in_range) {
+      bpsi = mk<R2>((R)a.power[o], (R)a.theta1[o]);
+      const unsigned bits = (unsigned)a.theta2[o];
+      constant = (bits & 1u) != 0;
+      nonconv = (bits & 2u) != 0;
+      no_candidate = (bits & 4u) != 0;
+    }
     R theta_w = atan2(bpsi.y, bpsi.x);
     if (theta_w < R(0)) theta_w += kTwoPi;
     // psi in wide precision, one Newton step onto |psi| = 1
@@ -783,6 +927,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
 #pragma unroll
       for (int i = 0; i < 8; ++i) v[i] = w_zero<W>();
       WC pw = pw0;
+#pragma unroll 1
       for (int e = gl + 1; e <= 2 * H; e += G) {
         const WC t = c_mul<W>(A64[e], pw);
         v[0] = w_add(v[0], re(t));
@@ -804,46 +949,53 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     };
     W MM, YM, Mbar, dl = w_zero<W>(), th1 = w_zero<W>();
     {
-      W v[8];
-      trig_sums(psi, v);
-      MM = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
-      const W MMt = w_mulf(v[1], -2.0f), MMtt = w_mulf(v[2], -2.0f);
-      YM = w_mulf(v[3], 2.0f);
-      const W YMt = w_mulf(v[4], -2.0f), YMtt = w_mulf(v[5], -2.0f);
-      Mbar = w_mulf(v[6], 2.0f);
-      const W Mbart = w_mulf(v[7], -2.0f);
-      if (a.polish_steps > 0 && !constant) {
-        const W g = w_sub(w_mulf(w_mul(MM, YMt), 2.0f), w_mul(YM, MMt));
-        const W gt = w_sub(w_add(w_mul(MMt, YMt), w_mulf(w_mul(MM, YMtt), 2.0f)), w_mul(YM, MMtt));
-        const W d = w_div(g, gt);
-        const float df = w_f(d);
-        if (isfinite(df) && fabsf(df) < 1e-3f) dl = d;
-      }
-      if (w_f(MM) > 0.0f) {
-        const W q = w_div(YM, MM);
-        const W dq = w_div(w_sub(w_mul(YMt, MM), w_mul(YM, MMt)), w_mul(MM, MM));
-        th1 = w_sub(q, w_mul(dl, dq));
-      }
-      Mbar = w_sub(Mbar, w_mul(dl, Mbart));
-      // A correction that is not tiny (an ill-conditioned item) makes the
-      // O(dl^2) shortcut too coarse: evaluate again at the corrected phase
-      // psi e^{-i dl} (Taylor series of cos, sin; |dl| < 1e-3).
-      const bool again = fabsf(w_f(dl)) > (kFast ? 1e-5f : 1e-9f);
-      if (__any_sync(0xffffffffu, again)) {
+      // pass 0 at psi; pass 1 (only when some item needs it) at the
+      // corrected phase.  One loop keeps a single copy of the sums' code.
+      WC pe = psi;
+      bool again = false;
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        W v[8];
+        trig_sums(pe, v);
+        if (pass == 1) {
+          if (again) {
+            MM = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
+            YM = w_mulf(v[3], 2.0f);
+            Mbar = w_mulf(v[6], 2.0f);
+            th1 = (w_f(MM) > 0.0f) ? w_div(YM, MM) : w_zero<W>();
+          }
+          break;
+        }
+        MM = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
+        const W MMt = w_mulf(v[1], -2.0f), MMtt = w_mulf(v[2], -2.0f);
+        YM = w_mulf(v[3], 2.0f);
+        const W YMt = w_mulf(v[4], -2.0f), YMtt = w_mulf(v[5], -2.0f);
+        Mbar = w_mulf(v[6], 2.0f);
+        const W Mbart = w_mulf(v[7], -2.0f);
+        if (a.polish_steps > 0 && !constant) {
+          const W g = w_sub(w_mulf(w_mul(MM, YMt), 2.0f), w_mul(YM, MMt));
+          const W gt = w_sub(w_add(w_mul(MMt, YMt), w_mulf(w_mul(MM, YMtt), 2.0f)), w_mul(YM, MMtt));
+          const W d = w_div(g, gt);
+          const float df = w_f(d);
+          if (isfinite(df) && fabsf(df) < 1e-3f) dl = d;
+        }
+        if (w_f(MM) > 0.0f) {
+          const W q = w_div(YM, MM);
+          const W dq = w_div(w_sub(w_mul(YMt, MM), w_mul(YM, MMt)), w_mul(MM, MM));
+          th1 = w_sub(q, w_mul(dl, dq));
+        }
+        Mbar = w_sub(Mbar, w_mul(dl, Mbart));
+        // A correction that is not tiny (an ill-conditioned item) makes the
+        // O(dl^2) shortcut too coarse: evaluate again at the corrected phase
+        // psi e^{-i dl} (Taylor series of cos, sin; |dl| < 1e-3).
+        again = fabsf(w_f(dl)) > (kFast ? 1e-5f : 1e-9f);
+        if (!__any_sync(0xffffffffu, again)) break;
         const W d2 = w_mul(dl, dl);
         const W cs = w_sub(w_of<W>(1.0), w_mul(d2, w_sub(w_of<W>(0.5), w_mul(d2, w_of<W>(1.0 / 24.0)))));
         const W sn = w_mul(dl, w_sub(w_of<W>(1.0), w_mul(d2, w_sub(w_of<W>(1.0 / 6.0),
                                                                   w_mul(d2, w_of<W>(1.0 / 120.0))))));
-        const WC ps2 = mkc(w_add(w_mul(re(psi), cs), w_mul(im(psi), sn)),
-                           w_sub(w_mul(im(psi), cs), w_mul(re(psi), sn)));
-        W v2[8];
-        trig_sums(ps2, v2);
-        if (again) {
-          MM = w_add(re(A64[0]), w_mulf(v2[0], 2.0f));
-          YM = w_mulf(v2[3], 2.0f);
-          Mbar = w_mulf(v2[6], 2.0f);
-          th1 = (w_f(MM) > 0.0f) ? w_div(YM, MM) : w_zero<W>();
-        }
+        pe = mkc(w_add(w_mul(re(psi), cs), w_mul(im(psi), sn)),
+                 w_sub(w_mul(im(psi), cs), w_mul(re(psi), sn)));
       }
     }
     W theta;
@@ -884,33 +1036,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       } else {
         const R Pf = (R)w_f(P), Mf = (R)MMf;
         const R dMM = R(9) * (R)a.sum_err * sum_abs_alpha * sum_abs_alpha;
-        const R dYM = R(2) * (R)a.sum_err * sum_abs_alpha * sqrt(YYr);
-        const R err = Pf * dMM / Mf + R(2) * sqrt(fmax(Pf, R(0)) / (YYr * Mf)) * dYM;
+        // an estimate with margin: MUFU reciprocal and square root suffice
+        const R dYM = R(2) * (R)a.sum_err * sum_abs_alpha * (YYr * fast_rsqrt(YYr));
+        const R q = fmax(Pf, R(0)) * fast_rcp(YYr * Mf);
+        const R sq = q > R(0) ? q * fast_rsqrt(q) : R(0);
+        const R err = Pf * dMM * fast_rcp(Mf) + R(2) * sq * dYM;
         redo = !(err <= (R)a.redo_tol);
       }
     }
 
     // ---- outputs: lanes 0..3 of the group convert one value each (one
     //      conversion instruction for the whole warp), then write it
-    int64_t col = 0, ridx = 0, ostride = a.out_stride;
-    size_t o = 0;
-    if (valid) {
-      if (!batched) {
-        col = a.kmap ? (int64_t)a.kmap[k] : k;
-        o = (size_t)a.rows[tau] * a.out_stride + col;
-        ridx = col;
-      } else {
-        const RootsSeg& sg = a.segs[cu.seg];
-        col = redo_pass ? (int64_t)a.kmap[k] - sg.redo_base : k;
-        const int row = sg.row_first < 0 ? 0 : a.rows[sg.row_first + cu.tl];
-        o = (size_t)(sg.out_off + (int64_t)row * sg.nf + col);
-        ostride = sg.nf;
-        ridx = sg.redo_base + col;
-      }
-    }
-    const bool in_range =
-        FTP_DCHECK(a.status, !valid || (col >= 0 && col < ostride), 21, col, ostride) &&
-        FTP_DCHECK(a.status, !valid || (int64_t)o < a.out_elems, 22, o, a.out_elems);
     {
       const W v = gl == 0 ? P : gl == 1 ? th1 : gl == 2 ? theta : th3;
       const double dv = w_d(v);
@@ -941,10 +1077,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         if (no_positive) f |= 64u;
         a.flags[o] = (uint8_t)f;
       }
-      st_iters += (unsigned long long)iters;
-      st_items += 1;
-      st_nonconv += nonconv ? 1 : 0;
     }
+    }  // phase 2
     __syncwarp();
     u = un;
     buf ^= 1;
@@ -957,7 +1091,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     st_nonconv += __shfl_xor_sync(0xffffffffu, st_nonconv, o);
     st_redo += __shfl_xor_sync(0xffffffffu, st_redo, o);
   }
-  if (lane == 0 && st_items) {
+  if (lane == 0 && (st_items || st_redo)) {
     atomicAdd(&a.counters[CNT_ITERS], st_iters);
     atomicAdd(&a.counters[CNT_ITEMS], st_items);
     atomicAdd(&a.counters[CNT_NONCONV], st_nonconv);
@@ -965,18 +1099,19 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
   }
 }
 
-// Host side: opt in to the dynamic shared memory once, size the persistent grid.
-template <typename S2, typename R, int H, int G>
-int launch_h(const RootsArgs& a, int num_sms, cudaStream_t s) {
+// Host side: opt in to the dynamic shared memory once per phase kernel, size
+// the persistent grids, launch the two phases back to back.
+template <typename S2, typename R, int H, int G, int PH>
+int launch_phase(const RootsArgs& a, int num_sms, cudaStream_t s) {
   using C = Cfg<S2, R, H, G>;
   static int blocks_per_sm = -1;
   if (blocks_per_sm < 0) {
-    if (cudaFuncSetAttribute(roots_kernel<S2, R, H, G>,
+    if (cudaFuncSetAttribute(roots_kernel<S2, R, H, G, PH>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)C::SMEM) != cudaSuccess)
       return -2;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, roots_kernel<S2, R, H, G>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, roots_kernel<S2, R, H, G, PH>,
                                                       C::WARPS * 32, C::SMEM) != cudaSuccess ||
         b < 1)
       return -2;
@@ -990,8 +1125,17 @@ int launch_h(const RootsArgs& a, int num_sms, cudaStream_t s) {
   const int64_t need = (nunits + C::WARPS - 1) / C::WARPS;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  roots_kernel<S2, R, H, G><<<(unsigned)grid, C::WARPS * 32, C::SMEM, s>>>(a);
+  roots_kernel<S2, R, H, G, PH><<<(unsigned)grid, C::WARPS * 32, C::SMEM, s>>>(a);
   return 1;
+}
+template <typename S2, typename R, int H, int G>
+int launch_h(const RootsArgs& a, int num_sms, cudaStream_t s) {
+  if (a.ev_first_start) cudaEventRecord(a.ev_first_start, s);
+  const int r = launch_phase<S2, R, H, G, 1>(a, num_sms, s);
+  if (r < 0) return r;
+  if (a.ev_first_end) cudaEventRecord(a.ev_first_end, s);
+  const int r2 = launch_phase<S2, R, H, G, 2>(a, num_sms, s);
+  return r2 < 0 ? r2 : r + r2;
 }
 
 }  // namespace roots

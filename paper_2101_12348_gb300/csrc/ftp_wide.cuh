@@ -59,10 +59,14 @@ __device__ __forceinline__ dd dd_mulf(dd a, float b) {
   e = fmaf(a.lo, b, e);
   return fast_two_sum(p, e);
 }
+// Quotient q1 + q2 with q2 from the exact remainder a - b q1 (Dekker).  The
+// two float quotients may be approximate (a few ulp): the remainder absorbs
+// q1's error, and q2's error is ulp-level of a term ~2^-22 |q|, so the
+// result keeps ~44 bits.
 __device__ __forceinline__ dd dd_div(dd a, dd b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float q1 = __fdividef(a.hi, b.hi);
   const dd r = dd_sub(a, dd_mulf(b, q1));
-  const float q2 = __fdiv_rn(r.hi, b.hi);
+  const float q2 = __fdividef(r.hi, b.hi);
   return fast_two_sum(q1, q2);
 }
 __device__ __forceinline__ dd dd_from_double(double v) {

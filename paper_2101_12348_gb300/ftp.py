@@ -44,7 +44,7 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows",
            "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune",
            "ftp_set_positive_amplitude", "ftp_multiband_periodogram",
-           "ftp_shared_multiband")
+           "ftp_shared_multiband", "ftp_roots_first_phase_ms")
 
 
 class FtpGrid(C.Structure):
@@ -94,6 +94,7 @@ def load(path: str | None = None) -> C.CDLL:
                                                  C.POINTER(FtpTemplate), i32, vp, vp, vp, vp,
                                                  vp, i32, vp]
     lib.ftp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
+    lib.ftp_roots_first_phase_ms.argtypes = [vp, C.POINTER(C.c_float)]
     lib.ftp_set_batch_options.argtypes = [vp, i64, i32]
     lib.ftp_batch_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32)]
     u64, f32 = C.c_uint64, C.c_float
@@ -404,6 +405,12 @@ def ftp_stage_times(plan: int) -> list:
     a = (C.c_float * 6)()
     _check(load().ftp_stage_times(plan, a), "ftp_stage_times")
     return list(a)
+
+
+def ftp_roots_first_phase_ms(plan: int) -> float:
+    v = C.c_float()
+    _check(load().ftp_roots_first_phase_ms(plan, C.byref(v)), "ftp_roots_first_phase_ms")
+    return float(v.value)
 
 
 def ftp_periodogram_sums_noalloc(sums, row_stride: int, precision: str, nf: int, H_sums: int,
