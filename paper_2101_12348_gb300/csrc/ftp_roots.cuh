@@ -215,6 +215,75 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
+// ------------------------------------------------------------ Aberth step
+// One Aberth-Ehrlich iteration for the NS root slots of a lane.  Slot r holds
+// root idx[r] of the item (idx < 0: an empty slot, marked converged), z[r] its
+// position; Fs holds F's D + 1 coefficients and Zs the positions of all D
+// roots of the item (read for the pair sums, written back at the end).
+template <int NS, int D, bool kFast, typename R, typename R2>
+__device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const int (&idx)[NS],
+                                            const R2* Fs, R2* Zs, R tol) {
+  R2 uu[NS], p[NS], dp[NS], S[NS];
+  bool outside[NS];
+#pragma unroll
+  for (int r = 0; r < NS; ++r) {
+    const R m2 = cabs2(z[r]);
+    outside[r] = m2 > R(1);
+    const R inv = outside[r] ? fast_rcp(m2) : R(1);
+    uu[r] = mk<R2>(z[r].x * inv, z[r].y * inv);  // 1/conj(z) outside the unit disc
+    p[r] = mk<R2>(0, 0);
+    dp[r] = mk<R2>(0, 0);
+    S[r] = mk<R2>(0, 0);
+  }
+#pragma unroll 2
+  for (int c = D; c >= 0; --c) {
+    const R2 f = Fs[c];
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      dp[r] = cfma(dp[r], uu[r], p[r]);
+      p[r] = cfma(p[r], uu[r], f);
+    }
+  }
+  // sum_{j != i} 1/(z_i - z_j): the j = i term has d = 0 and contributes
+  // conj(0) / (0 + tiny) = 0, so no branch is needed
+#pragma unroll 2
+  for (int j = 0; j < D; ++j) {
+    const R2 zj = Zs[j];
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      const R2 d = csub(z[r], zj);
+      const R inv = fast_rcp(fma(d.x, d.x, fma(d.y, d.y, kFast ? R(1e-30) : R(1e-300))));
+      S[r].x = fma(d.x, inv, S[r].x);
+      S[r].y = fma(-d.y, inv, S[r].y);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < NS; ++r) {
+    // Newton ratio p/p'.  Outside the disc use the anti-self-inversive
+    // identity p(z) = -z^D conj(p(u)), u = 1/conj(z):
+    //   p/p' = z / (D - conj(p'(u)/p(u)) / z).
+    R2 N;
+    if (outside[r]) {
+      const R2 q = cconj(cdiv(dp[r], p[r]));
+      N = cdiv(z[r], csub(mk<R2>((R)D, 0), cdiv(q, z[r])));
+    } else {
+      N = cdiv(p[r], dp[r]);
+    }
+    R2 w = cdiv(N, csub(mk<R2>(1, 0), cmul(N, S[r])));
+    if (!finite2(w)) w = mk<R2>(0, 0);
+    if (!conv[r]) {
+      const R zz = cabs2(z[r]);
+      conv[r] = cabs2(w) <= tol * tol * (zz > R(1) ? zz : R(1));
+      z[r] = csub(z[r], w);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < NS; ++r)
+    if (idx[r] >= 0) Zs[idx[r]] = z[r];
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ group reductions
 template <int G, typename T> __device__ __forceinline__ T gsum(T v) {
 #pragma unroll
@@ -768,76 +837,82 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       if (i < D) Zs[i] = z[r];
     }
     __syncwarp();
+    // Iterations over all RR slots per lane until every group of the warp has
+    // at most RS * G unconverged roots, then over RS slots per lane holding
+    // the unconverged roots only (listed per group in shared memory;
+    // converged ones stay in Zs for the pair sums).
+    constexpr int RS = (RR + 1) / 2;
     int iters = 0;
-#pragma unroll 1
-    for (; iters < a.maxit; ++iters) {
-      bool lane_done = true;
-#pragma unroll
-      for (int r = 0; r < RR; ++r) lane_done = lane_done && conv[r];
-      if (__all_sync(0xffffffffu, lane_done)) break;
-      R2 uu[RR], p[RR], dp[RR], S[RR];
-      bool outside[RR];
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        const R m2 = cabs2(z[r]);
-        outside[r] = m2 > R(1);
-        const R inv = outside[r] ? fast_rcp(m2) : R(1);
-        uu[r] = mk<R2>(z[r].x * inv, z[r].y * inv);  // 1/conj(z) outside the unit disc
-        p[r] = mk<R2>(0, 0);
-        dp[r] = mk<R2>(0, 0);
-        S[r] = mk<R2>(0, 0);
-      }
-#pragma unroll 2
-      for (int c = D; c >= 0; --c) {
-        const R2 f = Fs[c];
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          dp[r] = cfma(dp[r], uu[r], p[r]);
-          p[r] = cfma(p[r], uu[r], f);
-        }
-      }
-      // sum_{j != i} 1/(z_i - z_j): the j = i term has d = 0 and contributes
-      // conj(0) / (0 + tiny) = 0, so no branch is needed
-#pragma unroll 2
-      for (int j = 0; j < D; ++j) {
-        const R2 zj = Zs[j];
-#pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          const R2 d = csub(z[r], zj);
-          const R inv = fast_rcp(fma(d.x, d.x, fma(d.y, d.y, kFast ? R(1e-30) : R(1e-300))));
-          S[r].x = fma(d.x, inv, S[r].x);
-          S[r].y = fma(-d.y, inv, S[r].y);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        // Newton ratio p/p'.  Outside the disc use the anti-self-inversive
-        // identity p(z) = -z^D conj(p(u)), u = 1/conj(z):
-        //   p/p' = z / (D - conj(p'(u)/p(u)) / z).
-        R2 N;
-        if (outside[r]) {
-          const R2 q = cconj(cdiv(dp[r], p[r]));
-          N = cdiv(z[r], csub(mk<R2>((R)D, 0), cdiv(q, z[r])));
-        } else {
-          N = cdiv(p[r], dp[r]);
-        }
-        R2 w = cdiv(N, csub(mk<R2>(1, 0), cmul(N, S[r])));
-        if (!finite2(w)) w = mk<R2>(0, 0);
-        if (!conv[r]) {
-          const R zz = cabs2(z[r]);
-          conv[r] = cabs2(w) <= tol * tol * (zz > R(1) ? zz : R(1));
-          z[r] = csub(z[r], w);
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < RR; ++r)
-        if (r * G + gl < D) Zs[r * G + gl] = z[r];
-      __syncwarp();
-    }
     bool lane_nc = false;
+    {
+      int idx[RR];
 #pragma unroll
-    for (int r = 0; r < RR; ++r) lane_nc = lane_nc || !conv[r];
+      for (int r = 0; r < RR; ++r) idx[r] = r * G + gl < D ? r * G + gl : -1;
+      bool compact = false;
+      int nact = 0;
+#pragma unroll 1
+      for (; iters < a.maxit; ++iters) {
+        nact = 0;
+#pragma unroll
+        for (int r = 0; r < RR; ++r) nact += conv[r] ? 0 : 1;
+        if (__all_sync(0xffffffffu, nact == 0)) break;
+        if constexpr (RS < RR) {
+          int wmax = gsum<G>(nact);
+#pragma unroll
+          for (int sh = G; sh < 32; sh <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, sh));
+          if (wmax <= RS * G) {
+            compact = true;
+            break;
+          }
+        }
+        aberth_step<RR, D, kFast>(z, conv, idx, Fs, Zs, tol);
+      }
+      if constexpr (RS < RR) {
+        if (compact) {
+          // list the group's unconverged roots: exclusive prefix of the lanes' counts
+          short* act = reinterpret_cast<short*>(Z64);  // free after the Newton polygon
+          int incl = nact;
+#pragma unroll
+          for (int sh = 1; sh < G; sh <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, sh, G);
+            if (gl >= sh) incl += t;
+          }
+          const int gact = __shfl_sync(0xffffffffu, incl, G - 1, G);
+          int pos = incl - nact;
+#pragma unroll
+          for (int r = 0; r < RR; ++r)
+            if (!conv[r]) act[pos++] = (short)(r * G + gl);
+          __syncwarp();
+          R2 zs[RS];
+          bool cs[RS];
+          int is[RS];
+#pragma unroll
+          for (int k = 0; k < RS; ++k) {
+            const int q = gl + k * G;
+            is[k] = q < gact ? (int)act[q] : -1;
+            zs[k] = is[k] >= 0 ? Zs[is[k]] : mk<R2>(0, 0);
+            cs[k] = is[k] < 0;
+          }
+          __syncwarp();
+#pragma unroll 1
+          for (; iters < a.maxit; ++iters) {
+            bool done = true;
+#pragma unroll
+            for (int k = 0; k < RS; ++k) done = done && cs[k];
+            if (__all_sync(0xffffffffu, done)) break;
+            aberth_step<RS, D, kFast>(zs, cs, is, Fs, Zs, tol);
+          }
+#pragma unroll
+          for (int k = 0; k < RS; ++k) lane_nc = lane_nc || !cs[k];
+        } else {
+#pragma unroll
+          for (int r = 0; r < RR; ++r) lane_nc = lane_nc || !conv[r];
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RR; ++r) lane_nc = lane_nc || !conv[r];
+      }
+    }
     const bool nonconv = gor<G>(lane_nc) && !constant;
 
     // ---- candidates: P at every root scaled onto |psi| = 1 (working precision).
