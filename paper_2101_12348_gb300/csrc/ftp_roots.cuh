@@ -284,6 +284,67 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
   __syncwarp();
 }
 
+// Iterations over NS slots per lane until every root converged (false) or,
+// if NT < NS, until every group of the warp has at most NT * G unconverged
+// roots (true: time to compact).
+template <int G, int NS, int NT, int D, bool kFast, typename R, typename R2>
+__device__ __forceinline__ bool aberth_run(R2 (&z)[NS], bool (&conv)[NS], const int (&idx)[NS],
+                                           const R2* Fs, R2* Zs, R tol, int& iters, int maxit) {
+#pragma unroll 1
+  for (; iters < maxit; ++iters) {
+    int nact = 0;
+#pragma unroll
+    for (int r = 0; r < NS; ++r) nact += conv[r] ? 0 : 1;
+    if (__all_sync(0xffffffffu, nact == 0)) return false;
+    if constexpr (NT < NS) {
+      int wmax = 0;
+      {
+        int v = nact;
+#pragma unroll
+        for (int sh = G / 2; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh, G);
+        wmax = v;
+      }
+#pragma unroll
+      for (int sh = G; sh < 32; sh <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, sh));
+      if (wmax <= NT * G) return true;
+    }
+    aberth_step<NS, D, kFast>(z, conv, idx, Fs, Zs, tol);
+  }
+  return false;
+}
+// Moves a group's unconverged roots from NS slots per lane into NT slots per
+// lane: the roots are listed in `act` (prefix over the lanes' counts), lane
+// gl takes list entries gl, gl + G, ...; positions come from Zs.
+template <int G, int NS, int NT, typename R2>
+__device__ __forceinline__ void compact_roots(const bool (&conv)[NS], const int (&idx)[NS],
+                                              short* act, const R2* Zs, int gl, R2 (&z2)[NT],
+                                              bool (&c2)[NT], int (&i2)[NT]) {
+  int nact = 0;
+#pragma unroll
+  for (int r = 0; r < NS; ++r) nact += conv[r] ? 0 : 1;
+  int incl = nact;
+#pragma unroll
+  for (int sh = 1; sh < G; sh <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, sh, G);
+    if (gl >= sh) incl += t;
+  }
+  const int gact = __shfl_sync(0xffffffffu, incl, G - 1, G);
+  int pos = incl - nact;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < NS; ++r)
+    if (!conv[r]) act[pos++] = (short)idx[r];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < NT; ++k) {
+    const int q = gl + k * G;
+    i2[k] = q < gact ? (int)act[q] : -1;
+    z2[k] = i2[k] >= 0 ? Zs[i2[k]] : mk<R2>(0, 0);
+    c2[k] = i2[k] < 0;
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------ group reductions
 template <int G, typename T> __device__ __forceinline__ T gsum(T v) {
 #pragma unroll
@@ -840,73 +901,36 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     // Iterations over all RR slots per lane until every group of the warp has
     // at most RS * G unconverged roots, then over RS slots per lane holding
     // the unconverged roots only (listed per group in shared memory;
-    // converged ones stay in Zs for the pair sums).
+    // converged ones stay in Zs for the pair sums), then likewise over RT.
     constexpr int RS = (RR + 1) / 2;
+    constexpr int RT = (RR + 3) / 4;
     int iters = 0;
     bool lane_nc = false;
     {
+      short* act = reinterpret_cast<short*>(Z64);  // free after the Newton polygon
       int idx[RR];
 #pragma unroll
       for (int r = 0; r < RR; ++r) idx[r] = r * G + gl < D ? r * G + gl : -1;
-      bool compact = false;
-      int nact = 0;
-#pragma unroll 1
-      for (; iters < a.maxit; ++iters) {
-        nact = 0;
-#pragma unroll
-        for (int r = 0; r < RR; ++r) nact += conv[r] ? 0 : 1;
-        if (__all_sync(0xffffffffu, nact == 0)) break;
+      if (aberth_run<G, RR, RS, D, kFast>(z, conv, idx, Fs, Zs, tol, iters, a.maxit)) {
         if constexpr (RS < RR) {
-          int wmax = gsum<G>(nact);
+          R2 z2[RS];
+          bool c2[RS];
+          int i2[RS];
+          compact_roots<G, RR, RS>(conv, idx, act, Zs, gl, z2, c2, i2);
+          if (aberth_run<G, RS, RT, D, kFast>(z2, c2, i2, Fs, Zs, tol, iters, a.maxit)) {
+            if constexpr (RT < RS) {
+              R2 z3[RT];
+              bool c3[RT];
+              int i3[RT];
+              compact_roots<G, RS, RT>(c2, i2, act, Zs, gl, z3, c3, i3);
+              aberth_run<G, RT, RT, D, kFast>(z3, c3, i3, Fs, Zs, tol, iters, a.maxit);
 #pragma unroll
-          for (int sh = G; sh < 32; sh <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, sh));
-          if (wmax <= RS * G) {
-            compact = true;
-            break;
+              for (int k = 0; k < RT; ++k) lane_nc = lane_nc || !c3[k];
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < RS; ++k) lane_nc = lane_nc || !c2[k];
           }
-        }
-        aberth_step<RR, D, kFast>(z, conv, idx, Fs, Zs, tol);
-      }
-      if constexpr (RS < RR) {
-        if (compact) {
-          // list the group's unconverged roots: exclusive prefix of the lanes' counts
-          short* act = reinterpret_cast<short*>(Z64);  // free after the Newton polygon
-          int incl = nact;
-#pragma unroll
-          for (int sh = 1; sh < G; sh <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, sh, G);
-            if (gl >= sh) incl += t;
-          }
-          const int gact = __shfl_sync(0xffffffffu, incl, G - 1, G);
-          int pos = incl - nact;
-#pragma unroll
-          for (int r = 0; r < RR; ++r)
-            if (!conv[r]) act[pos++] = (short)(r * G + gl);
-          __syncwarp();
-          R2 zs[RS];
-          bool cs[RS];
-          int is[RS];
-#pragma unroll
-          for (int k = 0; k < RS; ++k) {
-            const int q = gl + k * G;
-            is[k] = q < gact ? (int)act[q] : -1;
-            zs[k] = is[k] >= 0 ? Zs[is[k]] : mk<R2>(0, 0);
-            cs[k] = is[k] < 0;
-          }
-          __syncwarp();
-#pragma unroll 1
-          for (; iters < a.maxit; ++iters) {
-            bool done = true;
-#pragma unroll
-            for (int k = 0; k < RS; ++k) done = done && cs[k];
-            if (__all_sync(0xffffffffu, done)) break;
-            aberth_step<RS, D, kFast>(zs, cs, is, Fs, Zs, tol);
-          }
-#pragma unroll
-          for (int k = 0; k < RS; ++k) lane_nc = lane_nc || !cs[k];
-        } else {
-#pragma unroll
-          for (int r = 0; r < RR; ++r) lane_nc = lane_nc || !conv[r];
         }
       } else {
 #pragma unroll
