@@ -163,6 +163,8 @@ struct ftp_plan_s {
   size_t bsums_cap = 0;
   double* d_bmom = nullptr;
   size_t bmom_cap = 0;
+  unsigned char* d_bprep = nullptr;  // step (a) preparation scratch of a chunk
+  size_t bprep_cap = 0;
   double* d_bobs = nullptr;  // staged host observations [3][count]
   size_t bobs_cap = 0;
   double* d_bout = nullptr;  // staged host outputs [4][extent]
@@ -366,6 +368,45 @@ ftp_status run_sums(ftp_plan_t P, SumLane& L, const double* t, const double* y, 
   }
   ev_rec(P, 4);
   *launches += 7;
+  FTP_CK(cudaGetLastError());
+  return FTP_OK;
+}
+
+// Spreading, FFT and gather of one batched curve on lane L, from its
+// observations already in tile order (tile offsets relative to cell_s).
+ftp_status run_sums_prepped(ftp_plan_t P, SumLane& L, int64_t k0, int64_t nf, int Hs,
+                            int64_t ngrid, int64_t ntiles, const int* tile_off,
+                            const int* cell_s, const void* frac_s, const void* coef_s,
+                            void* sums, int64_t nf_pad, int* launches) {
+  if (ngrid > P->ngrid || ntiles > P->ntiles) return FTP_ERR_UNSUPPORTED;
+  cufftHandle fft;
+  ftp_status st = get_fft(P, L, ngrid, &fft);
+  if (st != FTP_OK) return st;
+  cudaStream_t s = L.s;
+  if (P->mixed) {
+    launch_spread<float>(tile_off, cell_s, (const float*)frac_s, (const float2*)coef_s, ngrid,
+                         ntiles, P->m, P->beta, (float2*)L.grid, P->d_status, s);
+  } else {
+    launch_spread<double>(tile_off, cell_s, (const double*)frac_s, (const double2*)coef_s,
+                          ngrid, ntiles, P->m, P->beta, (double2*)L.grid, P->d_status, s);
+  }
+  if (cufftSetStream(fft, s) != CUFFT_SUCCESS) return FTP_ERR_CUDA;
+  cufftResult fr;
+  if (P->mixed) {
+    fr = cufftExecC2C(fft, (cufftComplex*)L.grid, (cufftComplex*)L.grid, CUFFT_INVERSE);
+  } else {
+    fr = cufftExecZ2Z(fft, (cufftDoubleComplex*)L.grid, (cufftDoubleComplex*)L.grid,
+                      CUFFT_INVERSE);
+  }
+  if (fr != CUFFT_SUCCESS) return FTP_ERR_CUDA;
+  if (P->mixed) {
+    launch_gather<float>((const float2*)L.grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
+                         (float2*)sums, P->d_status, s);
+  } else {
+    launch_gather<double>((const double2*)L.grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
+                          (double2*)sums, P->d_status, s);
+  }
+  *launches += 2;
   FTP_CK(cudaGetLastError());
   return FTP_OK;
 }
@@ -727,6 +768,7 @@ struct BCurve {
   double df;
   int Hc, ntc, tpl;
   int Ht;  // template harmonics (Hc, the sums' harmonics, may be larger for features)
+  int64_t obs_base, tile_base;  // within the chunk's preparation scratch
 };
 struct BLaunch {
   int H, ntpl, Hs;
@@ -738,6 +780,20 @@ struct BChunk {
   int Hs;
   std::vector<BLaunch> launches;
   int64_t items;  // (template, frequency) output items of the chunk's curves
+  int64_t obs_total = 0, tiles_total = 0;  // preparation scratch of the chunk
+};
+// The chunk's step (a) preparation scratch: observations in tile order (and
+// the unsorted copies), tile offsets and counters.
+struct PrepBufs {
+  const PrepCurve* curves;  // device, [ncurves]
+  int* cell;
+  int* cell_s;
+  void* frac;
+  void* frac_s;
+  void* coef;
+  void* coef_s;
+  int* tile_cnt;
+  int* tile_off;
 };
 
 // Optional extra work of a batch: features only (feat_out), or screening by
@@ -767,7 +823,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
                                 const int* d_cseg, double* const* o, uint8_t* of,
                                 int64_t extent, const BatchScreen* scr,
                                 const ScreenCurve* d_scurves, const int64_t* d_rowoff,
-                                int* launches) {
+                                const PrepBufs& pb, int* launches) {
   cudaStream_t s = P->stream;
   const RootsKind kind = P->mixed ? ROOTS_MIXED : ROOTS_FP64;
   const RootsKind rkind = P->mixed ? ROOTS_REDO : ROOTS_FP64;
@@ -775,8 +831,21 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
   for (size_t q = 0; q < chunks.size(); ++q) {
     const BChunk& ch = chunks[q];
     if (tm) cudaEventRecord(P->bev[4 * q + 0], s);
-    // step (a) of the chunk's curves, round-robin over the lanes (fork/join
-    // through events, so a captured graph holds parallel branches)
+    // step (a) preparation of every curve of the chunk in one launch
+    // (moments, cells, tile order), then spreading, FFT and gather of each
+    // curve, round-robin over the lanes (fork/join through events, so a
+    // captured graph holds parallel branches)
+    if (P->mixed) {
+      launch_prep_batch<float>(pb.curves + ch.c0, (int)(ch.c1 - ch.c0), P->d_bmom, pb.tile_cnt,
+                               pb.tile_off, pb.cell, (float*)pb.frac, (float2*)pb.coef,
+                               pb.cell_s, (float*)pb.frac_s, (float2*)pb.coef_s, P->d_status, s);
+    } else {
+      launch_prep_batch<double>(pb.curves + ch.c0, (int)(ch.c1 - ch.c0), P->d_bmom, pb.tile_cnt,
+                                pb.tile_off, pb.cell, (double*)pb.frac, (double2*)pb.coef,
+                                pb.cell_s, (double*)pb.frac_s, (double2*)pb.coef_s, P->d_status,
+                                s);
+    }
+    *launches += 1;
     const int used = (int)std::min<int64_t>(
         std::min<int64_t>(1 + (int64_t)P->xlanes.size(), P->sum_lanes), ch.c1 - ch.c0);
     if (used > 1) {
@@ -787,10 +856,11 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       const BCurve& b = cv[(size_t)c];
       const int l = (int)((c - ch.c0) % used);
       SumLane& L = l == 0 ? P->l0 : *P->xlanes[l - 1];
-      ftp_status st = run_sums(P, L, b.t, b.y, b.dy, b.n, b.df, b.k0, b.nf, b.Hc, b.ngrid,
-                               b.ntiles, P->d_bmom + (size_t)(c - ch.c0) * MO_WORDS,
-                               (unsigned char*)P->d_bsums + (size_t)b.sums_off * P->csz,
-                               b.nf_pad, launches);
+      ftp_status st = run_sums_prepped(
+          P, L, b.k0, b.nf, b.Hc, b.ngrid, b.ntiles, pb.tile_off + b.tile_base,
+          pb.cell_s + b.obs_base, (unsigned char*)pb.frac_s + (size_t)b.obs_base * (P->csz / 2),
+          (unsigned char*)pb.coef_s + (size_t)b.obs_base * P->csz,
+          (unsigned char*)P->d_bsums + (size_t)b.sums_off * P->csz, b.nf_pad, launches);
       if (st != FTP_OK) return st;
     }
     for (int l = 1; l < used; ++l) {
@@ -1048,6 +1118,10 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       }
       b.sums_off = cur.sums_elems;
       b.redo_base = cur.nf_total;
+      b.obs_base = cur.obs_total;
+      b.tile_base = cur.tiles_total;
+      cur.obs_total += b.n;
+      cur.tiles_total += b.ntiles + 1;
       cur.sums_elems += elems;
       cur.nf_total += b.nf;
       cur.items += (int64_t)b.ntc * b.nf;
@@ -1171,7 +1245,19 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   const size_t off_cseg = off_curves + al64(curves.size() * sizeof(CurveDesc));
   const size_t off_scur = off_cseg + al64(cseg.size() * sizeof(int));
   const size_t off_rowoff = off_scur + al64(scurves.size() * sizeof(ScreenCurve));
-  const size_t blob = off_rowoff + al64(rowoff.size() * sizeof(int64_t));
+  std::vector<PrepCurve> prep((size_t)ncurves);
+  int64_t max_obs_total = 0, max_tiles_total = 0;
+  for (const BChunk& ch : chunks) {
+    max_obs_total = std::max(max_obs_total, ch.obs_total);
+    max_tiles_total = std::max(max_tiles_total, ch.tiles_total);
+    for (int64_t c = ch.c0; c < ch.c1; ++c) {
+      const BCurve& b = cv[(size_t)c];
+      prep[(size_t)c] = PrepCurve{b.t, b.y, b.dy, b.n, b.df, b.ngrid, b.ntiles, b.obs_base,
+                                  b.tile_base};
+    }
+  }
+  const size_t off_prep = off_rowoff + al64(rowoff.size() * sizeof(int64_t));
+  const size_t blob = off_prep + al64(prep.size() * sizeof(PrepCurve));
 
   // ---- workspace (growing it drops a captured graph)
   st = grow_dev(reinterpret_cast<unsigned char**>(&P->d_bsums), &P->bsums_cap,
@@ -1179,6 +1265,16 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   if (st == FTP_OK) st = grow_dev(&P->d_bmom, &P->bmom_cap, max_chunk_curves * MO_WORDS, &grew);
   if (st == FTP_OK) st = grow_dev(&P->d_bmark, &P->bmark_cap, (size_t)max_nf_total, &grew);
   if (st == FTP_OK) st = grow_dev(&P->d_bdesc, &P->bdesc_cap, blob, &grew);
+  // preparation scratch: cells (unsorted, sorted), fractions, coefficients,
+  // tile counters and offsets of the largest chunk
+  const size_t rsz = P->csz / 2;
+  const size_t mo = (size_t)std::max<int64_t>(max_obs_total, 1);
+  const size_t mt = (size_t)std::max<int64_t>(max_tiles_total, 1);
+  const size_t pb_cell = 0, pb_frac = al64(2 * mo * sizeof(int));
+  const size_t pb_coef = pb_frac + al64(2 * mo * rsz);
+  const size_t pb_tile = pb_coef + al64(2 * mo * P->csz);
+  const size_t pb_end = pb_tile + al64(2 * mt * sizeof(int));
+  if (st == FTP_OK) st = grow_dev(&P->d_bprep, &P->bprep_cap, pb_end, &grew);
   if (st == FTP_OK && !P->d_blist) {
     grew = true;
     if (dalloc(&P->d_blist, kBatchRedoCap) != FTP_OK ||
@@ -1215,6 +1311,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   memcpy(P->h_bdesc + off_cseg, cseg.data(), cseg.size() * sizeof(int));
   memcpy(P->h_bdesc + off_scur, scurves.data(), scurves.size() * sizeof(ScreenCurve));
   memcpy(P->h_bdesc + off_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t));
+  memcpy(P->h_bdesc + off_prep, prep.data(), prep.size() * sizeof(PrepCurve));
   // step (a) lanes, then every FFT size on every lane that runs one: making a
   // plan may resize (and so synchronise) a work area
   {
@@ -1262,6 +1359,16 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   const int* d_cseg = reinterpret_cast<const int*>(P->d_bdesc + off_cseg);
   const ScreenCurve* d_scur = reinterpret_cast<const ScreenCurve*>(P->d_bdesc + off_scur);
   const int64_t* d_rowoff = reinterpret_cast<const int64_t*>(P->d_bdesc + off_rowoff);
+  PrepBufs pbufs{};
+  pbufs.curves = reinterpret_cast<const PrepCurve*>(P->d_bdesc + off_prep);
+  pbufs.cell = reinterpret_cast<int*>(P->d_bprep + pb_cell);
+  pbufs.cell_s = pbufs.cell + mo;
+  pbufs.frac = P->d_bprep + pb_frac;
+  pbufs.frac_s = P->d_bprep + pb_frac + mo * rsz;
+  pbufs.coef = P->d_bprep + pb_coef;
+  pbufs.coef_s = P->d_bprep + pb_coef + mo * P->csz;
+  pbufs.tile_cnt = reinterpret_cast<int*>(P->d_bprep + pb_tile);
+  pbufs.tile_off = pbufs.tile_cnt + mt;
   double* o[4] = {power, theta1, theta2, theta3};
   uint8_t* of = flags;
   if (!out_dev) {
@@ -1314,7 +1421,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     cudaGraph_t graph = nullptr;
     FTP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                              scr, d_scur, d_rowoff, &launches);
+                              scr, d_scur, d_rowoff, pbufs, &launches);
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     cudaGraphExec_t exec = nullptr;
     if (st == FTP_OK && ce == cudaSuccess && graph &&
@@ -1333,12 +1440,12 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       P->eager_key = 0;  // capture failed: stay eager for this call pattern
       launches = 0;
       st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                                scr, d_scur, d_rowoff, &launches);
+                                scr, d_scur, d_rowoff, pbufs, &launches);
       if (st != FTP_OK) return st;
     }
   } else {
     st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                              scr, d_scur, d_rowoff, &launches);
+                              scr, d_scur, d_rowoff, pbufs, &launches);
     if (st != FTP_OK) return st;
     if (graphable) P->eager_key = key;
   }
@@ -1429,7 +1536,7 @@ void ftp_destroy(ftp_plan_t P) {
                    P->d_blist, P->d_bslot_curve, P->d_bcount, P->d_bredo_sums, P->d_bdesc,
                    P->d_bfeat, P->d_bscore, P->d_bsel, P->d_bulist, P->d_bucount,
                    P->d_mb, P->d_mbflags, P->d_mbpow, P->d_shsums, P->d_shmisc,
-                   P->d_shalpha, P->d_shcoef};
+                   P->d_shalpha, P->d_shcoef, P->d_bprep};
   for (void* p : bptrs)
     if (p) cudaFree(p);
   if (P->h_bdesc) cudaFreeHost(P->h_bdesc);

@@ -111,6 +111,31 @@ struct CurveDesc {
 };
 static_assert(sizeof(CurveDesc) == 80, "CurveDesc layout");
 
+// One curve of a batched step (a) preparation: its observations, NFFT grid,
+// and where its per-observation and per-tile scratch starts in the chunk's
+// arrays (obs_base + i, tile_base + tile).
+struct PrepCurve {
+  const double* t;
+  const double* y;
+  const double* dy;
+  int64_t n;
+  double df;
+  int64_t ngrid;
+  int64_t ntiles;
+  int64_t obs_base;
+  int64_t tile_base;  // tile_off needs ntiles + 1 entries from here
+};
+
+// Step (a) preparation of `ncurves` curves in one launch (one CTA per curve):
+// moments into moments[c * MO_WORDS ..], then the curve's observations in
+// spreading-tile order (cell_s, frac_s, coef_s from obs_base) and the tile
+// offsets relative to obs_base (tile_off from tile_base).  cell/frac/coef and
+// tile_cnt are scratch of the same sizes.
+template <typename R>
+void launch_prep_batch(const PrepCurve* curves, int ncurves, double* moments, int* tile_cnt,
+                       int* tile_off, int* cell, R* frac, typename C2<R>::type* coef, int* cell_s,
+                       R* frac_s, typename C2<R>::type* coef_s, int* status, cudaStream_t s);
+
 // Direct FP64 sums for the listed global frequency indices of a batch:
 // slot i of `list` (< min(*count, cap)) gets the sums of its curve at row
 // stride `stride` and slot_curve[i] = the curve's index.  moments holds

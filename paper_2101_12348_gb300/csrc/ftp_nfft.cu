@@ -68,6 +68,33 @@ struct MomentPartial {
   long long nzero, nbad;
 };
 
+// The weight rules on the totals of pass 1: unit weights when every sigma
+// is 0, errors for non-finite input, mixed zero / non-zero sigma and
+// constant y; writes ybar, the weight sum and the unit flag (YY = 0 so far).
+__device__ void finish_pass1(const MomentPartial& q, int64_t n, double* moments, int* status) {
+  int code = DEV_OK;
+  double wsum = 0, ybar = 0;
+  bool unit = false;
+  if (q.nbad > 0) {
+    code = DEV_NONFINITE;
+  } else if (q.nzero == n) {
+    unit = true;
+    wsum = (double)n;
+    ybar = q.sy / (double)n;
+  } else if (q.nzero > 0) {
+    code = DEV_MIXED_ZERO_SIGMA;
+  } else {
+    wsum = q.s0;
+    ybar = q.s1 / q.s0;
+  }
+  if (code == DEV_OK && !(q.ymax > q.ymin)) code = DEV_ZERO_VARIANCE;
+  moments[MO_YBAR] = ybar;
+  moments[MO_YY] = 0.0;
+  moments[MO_WSUM] = wsum;
+  moments[MO_UNIT] = unit ? 1.0 : 0.0;
+  if (code != DEV_OK) atomicCAS(&status[ST_CODE], DEV_OK, code);
+}
+
 __device__ __forceinline__ bool last_block(unsigned* ticket) {
   __shared__ bool last;
   __threadfence();
@@ -126,27 +153,7 @@ __global__ void __launch_bounds__(256) moments_pass1(const double* __restrict__ 
       q.nzero += r.nzero;
       q.nbad += r.nbad;
     }
-    int code = DEV_OK;
-    double wsum = 0, ybar = 0;
-    bool unit = false;
-    if (q.nbad > 0) {
-      code = DEV_NONFINITE;
-    } else if (q.nzero == n) {
-      unit = true;
-      wsum = (double)n;
-      ybar = q.sy / (double)n;
-    } else if (q.nzero > 0) {
-      code = DEV_MIXED_ZERO_SIGMA;
-    } else {
-      wsum = q.s0;
-      ybar = q.s1 / q.s0;
-    }
-    if (code == DEV_OK && !(q.ymax > q.ymin)) code = DEV_ZERO_VARIANCE;
-    moments[MO_YBAR] = ybar;
-    moments[MO_YY] = 0.0;
-    moments[MO_WSUM] = wsum;
-    moments[MO_UNIT] = unit ? 1.0 : 0.0;
-    if (code != DEV_OK) atomicCAS(&status[ST_CODE], DEV_OK, code);
+    finish_pass1(q, n, moments, status);
     *ticket = 0u;  // ready for the next reduction
   }
 }
@@ -178,6 +185,30 @@ __global__ void __launch_bounds__(256) moments_pass2(const double* __restrict__ 
   }
 }
 
+// One observation: normalised weight and packed coefficient (w, w (y - ybar)),
+// and the FP64 reduction of u = frac(df t) and of its grid position
+// x = ngrid u into the returned cell and the fraction (only the fraction is
+// handed to the working precision).
+template <typename R>
+__device__ __forceinline__ int point_of(double t, double y, double dy, double ybar, double wsum,
+                                        bool unit, double df, int64_t ngrid, R* frac,
+                                        typename C2<R>::type* coef) {
+  const double w = (unit ? 1.0 : 1.0 / (dy * dy)) / wsum;
+  double u = df * t;
+  u -= floor(u);
+  const double x = u * (double)ngrid;
+  const double fl = floor(x);
+  int64_t c = (int64_t)fl;
+  if (c >= ngrid) c -= ngrid;
+  if (c < 0) c = 0;
+  *frac = (R)(x - fl);
+  typename C2<R>::type cc;
+  cc.x = (R)w;
+  cc.y = (R)(w * (y - ybar));
+  *coef = cc;
+  return (int)c;
+}
+
 // Per observation: normalised weight, packed coefficient, FP64 reduction of
 // u = frac(df t) and of its grid position x = n u into an integer cell and a
 // fraction (only the fraction is handed to the working precision), and the
@@ -194,32 +225,17 @@ __global__ void points_kernel(const double* __restrict__ t, const double* __rest
   const bool unit = moments[MO_UNIT] != 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double si = dy[i];
-    const double w = (unit ? 1.0 : 1.0 / (si * si)) / wsum;
-    double u = df * t[i];
-    u -= floor(u);
-    const double x = u * (double)ngrid;
-    const double fl = floor(x);
-    int64_t c = (int64_t)fl;
-    if (c >= ngrid) c -= ngrid;
-    if (c < 0) c = 0;
-    cell[i] = (int)c;
-    frac[i] = (R)(x - fl);
-    typename C2<R>::type cc;
-    cc.x = (R)w;
-    cc.y = (R)(w * (y[i] - ybar));
-    coef[i] = cc;
+    const int c = point_of<R>(t[i], y[i], dy[i], ybar, wsum, unit, df, ngrid, &frac[i], &coef[i]);
+    cell[i] = c;
     atomicAdd(&tile_count[c >> kSpreadTileShift], 1);
   }
 }
 
-// Exclusive scan of the tile histogram (one CTA); also clears the cursors.
-__global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ count, int64_t ntiles,
-                                                     int* __restrict__ off, int* __restrict__ cursor,
-                                                     const int* __restrict__ status) {
-  __shared__ int sh[32];
-  __shared__ int carry;
-  if (status[ST_CODE] != DEV_OK) return;
+// Exclusive scan of a tile histogram by the whole CTA (blockDim a multiple
+// of 32, at most 1024); also clears the cursors.  `sh` holds 32 ints.
+__device__ void block_scan_tiles(const int* __restrict__ count, int64_t ntiles,
+                                 int* __restrict__ off, int* __restrict__ cursor, int* sh,
+                                 int& carry) {
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -256,6 +272,16 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ coun
   if (threadIdx.x == 0) off[ntiles] = carry;
 }
 
+// Exclusive scan of the tile histogram (one CTA); also clears the cursors.
+__global__ void __launch_bounds__(1024) scan_kernel(const int* __restrict__ count, int64_t ntiles,
+                                                     int* __restrict__ off, int* __restrict__ cursor,
+                                                     const int* __restrict__ status) {
+  __shared__ int sh[32];
+  __shared__ int carry;
+  if (status[ST_CODE] != DEV_OK) return;
+  block_scan_tiles(count, ntiles, off, cursor, sh, carry);
+}
+
 template <typename R>
 __global__ void scatter_kernel(int64_t n, const int* __restrict__ off, int* __restrict__ cursor,
                                const int* __restrict__ cell, const R* __restrict__ frac,
@@ -272,6 +298,99 @@ __global__ void scatter_kernel(int64_t n, const int* __restrict__ off, int* __re
     cell_s[pos] = c;
     frac_s[pos] = frac[i];
     coef_s[pos] = coef[i];
+  }
+}
+
+// Step (a) preparation of a chunk of curves in one launch, one CTA per
+// curve: the two moment passes as block reductions, then per observation the
+// weight, coefficient, cell and fraction with the tile histogram, its scan,
+// and the scatter into tile order — what moments_pass1/2, points_kernel,
+// scan_kernel and scatter_kernel do for one curve, without their launches.
+template <typename R>
+__global__ void __launch_bounds__(512) prep_batch_kernel(
+    const PrepCurve* __restrict__ curves, double* __restrict__ moments_all,
+    int* __restrict__ tile_cnt, int* __restrict__ tile_off, int* __restrict__ cell,
+    R* __restrict__ frac, typename C2<R>::type* __restrict__ coef, int* __restrict__ cell_s,
+    R* __restrict__ frac_s, typename C2<R>::type* __restrict__ coef_s, int* status) {
+  __shared__ double shd[32];
+  __shared__ long long shl[32];
+  __shared__ int shi[32];
+  __shared__ int carry;
+  __shared__ int ok;
+  const PrepCurve pc = curves[blockIdx.x];
+  double* moments = moments_all + (size_t)blockIdx.x * MO_WORDS;
+  const int64_t n = pc.n;
+  // ---- pass 1: weight sums, mean, range, sigma classes
+  double s0 = 0, s1 = 0, sy = 0, ymin = INFINITY, ymax = -INFINITY;
+  long long nzero = 0, nbad = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double ti = pc.t[i], yi = pc.y[i], si = pc.dy[i];
+    if (!isfinite(ti) || !isfinite(yi) || !isfinite(si) || si < 0.0) {
+      ++nbad;
+      continue;
+    }
+    sy += yi;
+    ymin = fmin(ymin, yi);
+    ymax = fmax(ymax, yi);
+    if (si == 0.0) {
+      ++nzero;
+    } else {
+      const double w = 1.0 / (si * si);
+      s0 += w;
+      s1 += w * yi;
+    }
+  }
+  MomentPartial q;
+  q.s0 = block_reduce(s0, shd, OpSum());
+  q.s1 = block_reduce(s1, shd, OpSum());
+  q.sy = block_reduce(sy, shd, OpSum());
+  q.ymin = block_reduce(ymin, shd, OpMin());
+  q.ymax = block_reduce(ymax, shd, OpMax());
+  q.nzero = block_reduce(nzero, shl, OpSum());
+  q.nbad = block_reduce(nbad, shl, OpSum());
+  if (threadIdx.x == 0) {
+    finish_pass1(q, n, moments, status);
+    ok = status[ST_CODE] == DEV_OK;
+  }
+  __syncthreads();
+  if (!ok) return;  // uniform
+  const double ybar = moments[MO_YBAR], wsum = moments[MO_WSUM];
+  const bool unit = moments[MO_UNIT] != 0.0;
+  // ---- pass 2: weighted sum of squared deviations
+  double yy = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double si = pc.dy[i];
+    const double w = unit ? 1.0 : 1.0 / (si * si);
+    const double r = pc.y[i] - ybar;
+    yy += w * r * r;
+  }
+  yy = block_reduce(yy, shd, OpSum());
+  if (threadIdx.x == 0) moments[MO_YY] = yy / wsum;
+  // ---- points and tile histogram
+  int* cnt = tile_cnt + pc.tile_base;
+  int* off = tile_off + pc.tile_base;
+  for (int64_t j = threadIdx.x; j < pc.ntiles; j += blockDim.x) cnt[j] = 0;
+  __syncthreads();
+  int* cl = cell + pc.obs_base;
+  R* fr = frac + pc.obs_base;
+  typename C2<R>::type* cf = coef + pc.obs_base;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int c = point_of<R>(pc.t[i], pc.y[i], pc.dy[i], ybar, wsum, unit, pc.df, pc.ngrid,
+                              &fr[i], &cf[i]);
+    cl[i] = c;
+    atomicAdd(&cnt[c >> kSpreadTileShift], 1);
+  }
+  __syncthreads();
+  // ---- scan (the counters become the cursors), scatter into tile order
+  block_scan_tiles(cnt, pc.ntiles, off, cnt, shi, carry);
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int c = cl[i];
+    const int tile = c >> kSpreadTileShift;
+    const int64_t pos = pc.obs_base + off[tile] + atomicAdd(&cnt[tile], 1);
+    cell_s[pos] = c;
+    frac_s[pos] = fr[i];
+    coef_s[pos] = cf[i];
   }
 }
 
@@ -693,6 +812,16 @@ void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int
                                                     status);
 }
 
+template <typename R>
+void launch_prep_batch(const PrepCurve* curves, int ncurves, double* moments, int* tile_cnt,
+                       int* tile_off, int* cell, R* frac, typename C2<R>::type* coef, int* cell_s,
+                       R* frac_s, typename C2<R>::type* coef_s, int* status, cudaStream_t s) {
+  if (ncurves < 1) return;
+  prep_batch_kernel<R><<<(unsigned)ncurves, 512, 0, s>>>(curves, moments, tile_cnt, tile_off,
+                                                          cell, frac, coef, cell_s, frac_s,
+                                                          coef_s, status);
+}
+
 #define FTP_INST(R)                                                                            \
   template void launch_points<R>(const double*, const double*, const double*, int64_t,         \
                                  const double*, const int*, double, int64_t, int*, int*, R*,   \
@@ -704,7 +833,9 @@ void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int
                                  int64_t, int64_t, int, double, C2<R>::type*, const int*,      \
                                  cudaStream_t);                                                \
   template void launch_gather<R>(const C2<R>::type*, int64_t, int64_t, int64_t, int64_t, int,  \
-                                 int, double, C2<R>::type*, const int*, cudaStream_t);
+                                 int, double, C2<R>::type*, const int*, cudaStream_t);         \
+  template void launch_prep_batch<R>(const PrepCurve*, int, double*, int*, int*, int*, R*,      \
+                                     C2<R>::type*, int*, R*, C2<R>::type*, int*, cudaStream_t);
 FTP_INST(float)
 FTP_INST(double)
 #undef FTP_INST
