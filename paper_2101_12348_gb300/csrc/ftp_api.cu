@@ -323,22 +323,37 @@ ftp_status run_sums(ftp_plan_t P, SumLane& L, const double* t, const double* y, 
   if (st != FTP_OK) return st;
   cudaStream_t s = L.s;
   ev_rec(P, 0);
-  FTP_CK(cudaMemsetAsync(L.tile_count, 0, sizeof(int) * ntiles, s));
-  launch_moments(t, y, dy, nobs, moments, P->d_status, L.mom_scratch, s);
-  if (P->mixed) {
-    launch_points<float>(t, y, dy, nobs, moments, P->d_status, df, ngrid, L.tile_count, L.cell,
-                         (float*)L.frac, (float2*)L.coef, s);
+  if (nobs <= kPrepOneMaxObs) {
+    // short curve: moments, cells, tile order in one single-CTA launch
+    const PrepCurve pc{t, y, dy, nobs, df, ngrid, ntiles, 0, 0};
+    if (P->mixed) {
+      launch_prep_one<float>(pc, moments, L.tile_count, L.tile_off, L.cell, (float*)L.frac,
+                             (float2*)L.coef, L.cell_s, (float*)L.frac_s, (float2*)L.coef_s,
+                             P->d_status, s);
+    } else {
+      launch_prep_one<double>(pc, moments, L.tile_count, L.tile_off, L.cell, (double*)L.frac,
+                              (double2*)L.coef, L.cell_s, (double*)L.frac_s, (double2*)L.coef_s,
+                              P->d_status, s);
+    }
+    *launches -= 4;  // three kernels in all, where the general path launches seven
   } else {
-    launch_points<double>(t, y, dy, nobs, moments, P->d_status, df, ngrid, L.tile_count, L.cell,
-                          (double*)L.frac, (double2*)L.coef, s);
-  }
-  launch_scan(L.tile_count, ntiles, L.tile_off, L.cursor, P->d_status, s);
-  if (P->mixed) {
-    launch_scatter<float>(nobs, L.tile_off, L.cursor, L.cell, (float*)L.frac, (float2*)L.coef,
-                          L.cell_s, (float*)L.frac_s, (float2*)L.coef_s, P->d_status, s);
-  } else {
-    launch_scatter<double>(nobs, L.tile_off, L.cursor, L.cell, (double*)L.frac, (double2*)L.coef,
-                           L.cell_s, (double*)L.frac_s, (double2*)L.coef_s, P->d_status, s);
+    FTP_CK(cudaMemsetAsync(L.tile_count, 0, sizeof(int) * ntiles, s));
+    launch_moments(t, y, dy, nobs, moments, P->d_status, L.mom_scratch, s);
+    if (P->mixed) {
+      launch_points<float>(t, y, dy, nobs, moments, P->d_status, df, ngrid, L.tile_count, L.cell,
+                           (float*)L.frac, (float2*)L.coef, s);
+    } else {
+      launch_points<double>(t, y, dy, nobs, moments, P->d_status, df, ngrid, L.tile_count, L.cell,
+                            (double*)L.frac, (double2*)L.coef, s);
+    }
+    launch_scan(L.tile_count, ntiles, L.tile_off, L.cursor, P->d_status, s);
+    if (P->mixed) {
+      launch_scatter<float>(nobs, L.tile_off, L.cursor, L.cell, (float*)L.frac, (float2*)L.coef,
+                            L.cell_s, (float*)L.frac_s, (float2*)L.coef_s, P->d_status, s);
+    } else {
+      launch_scatter<double>(nobs, L.tile_off, L.cursor, L.cell, (double*)L.frac, (double2*)L.coef,
+                             L.cell_s, (double*)L.frac_s, (double2*)L.coef_s, P->d_status, s);
+    }
   }
   ev_rec(P, 1);
   if (P->mixed) {
@@ -1584,8 +1599,12 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
   P->max_H = max_H;
   P->grid = grid;
   P->max_templates = max_templates;
+  // Kaiser-Bessel half-width and oversampling.  FP32 sums reach their
+  // rounding floor (~2e-7 of sum w) already at sigma = 1.5 with m = 4 (sigma
+  // 2: 1.6e-7; sigma 1.25, m = 5: 4.4e-7), so the mixed path takes the 25 %
+  // smaller grid; the FP64 path keeps sigma = 2, m = 8.
   P->m = P->mixed ? 4 : 8;
-  P->sigma = 2.0;
+  P->sigma = P->mixed ? 1.5 : 2.0;
   P->beta = kb_beta(P->m, P->sigma);
   P->rsz = P->mixed ? sizeof(float) : sizeof(double);
   P->csz = 2 * P->rsz;

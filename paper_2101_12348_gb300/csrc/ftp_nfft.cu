@@ -307,18 +307,17 @@ __global__ void scatter_kernel(int64_t n, const int* __restrict__ off, int* __re
 // and the scatter into tile order — what moments_pass1/2, points_kernel,
 // scan_kernel and scatter_kernel do for one curve, without their launches.
 template <typename R>
-__global__ void __launch_bounds__(512) prep_batch_kernel(
-    const PrepCurve* __restrict__ curves, double* __restrict__ moments_all,
-    int* __restrict__ tile_cnt, int* __restrict__ tile_off, int* __restrict__ cell,
-    R* __restrict__ frac, typename C2<R>::type* __restrict__ coef, int* __restrict__ cell_s,
-    R* __restrict__ frac_s, typename C2<R>::type* __restrict__ coef_s, int* status) {
+__device__ void prep_curve(const PrepCurve& pc, double* __restrict__ moments,
+                           int* __restrict__ tile_cnt, int* __restrict__ tile_off,
+                           int* __restrict__ cell, R* __restrict__ frac,
+                           typename C2<R>::type* __restrict__ coef, int* __restrict__ cell_s,
+                           R* __restrict__ frac_s, typename C2<R>::type* __restrict__ coef_s,
+                           int* status) {
   __shared__ double shd[32];
   __shared__ long long shl[32];
   __shared__ int shi[32];
   __shared__ int carry;
   __shared__ int ok;
-  const PrepCurve pc = curves[blockIdx.x];
-  double* moments = moments_all + (size_t)blockIdx.x * MO_WORDS;
   const int64_t n = pc.n;
   // ---- pass 1: weight sums, mean, range, sigma classes
   double s0 = 0, s1 = 0, sy = 0, ymin = INFINITY, ymax = -INFINITY;
@@ -392,6 +391,28 @@ __global__ void __launch_bounds__(512) prep_batch_kernel(
     frac_s[pos] = fr[i];
     coef_s[pos] = cf[i];
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) prep_batch_kernel(
+    const PrepCurve* __restrict__ curves, double* __restrict__ moments_all,
+    int* __restrict__ tile_cnt, int* __restrict__ tile_off, int* __restrict__ cell,
+    R* __restrict__ frac, typename C2<R>::type* __restrict__ coef, int* __restrict__ cell_s,
+    R* __restrict__ frac_s, typename C2<R>::type* __restrict__ coef_s, int* status) {
+  prep_curve<R>(curves[blockIdx.x], moments_all + (size_t)blockIdx.x * MO_WORDS, tile_cnt,
+                tile_off, cell, frac, coef, cell_s, frac_s, coef_s, status);
+}
+
+// The same for one curve whose descriptor travels as a kernel parameter (a
+// short single curve: one launch instead of six).
+template <typename R>
+__global__ void __launch_bounds__(512) prep_one_kernel(
+    const PrepCurve pc, double* __restrict__ moments, int* __restrict__ tile_cnt,
+    int* __restrict__ tile_off, int* __restrict__ cell, R* __restrict__ frac,
+    typename C2<R>::type* __restrict__ coef, int* __restrict__ cell_s, R* __restrict__ frac_s,
+    typename C2<R>::type* __restrict__ coef_s, int* status) {
+  prep_curve<R>(pc, moments, tile_cnt, tile_off, cell, frac, coef, cell_s, frac_s, coef_s,
+                status);
 }
 
 // Modified Bessel function I0 from its power series sum_k (x^2/4)^k / (k!)^2,
@@ -822,6 +843,14 @@ void launch_prep_batch(const PrepCurve* curves, int ncurves, double* moments, in
                                                           coef_s, status);
 }
 
+template <typename R>
+void launch_prep_one(const PrepCurve& pc, double* moments, int* tile_cnt, int* tile_off,
+                     int* cell, R* frac, typename C2<R>::type* coef, int* cell_s, R* frac_s,
+                     typename C2<R>::type* coef_s, int* status, cudaStream_t s) {
+  prep_one_kernel<R><<<1, 512, 0, s>>>(pc, moments, tile_cnt, tile_off, cell, frac, coef, cell_s,
+                                        frac_s, coef_s, status);
+}
+
 #define FTP_INST(R)                                                                            \
   template void launch_points<R>(const double*, const double*, const double*, int64_t,         \
                                  const double*, const int*, double, int64_t, int*, int*, R*,   \
@@ -835,7 +864,9 @@ void launch_prep_batch(const PrepCurve* curves, int ncurves, double* moments, in
   template void launch_gather<R>(const C2<R>::type*, int64_t, int64_t, int64_t, int64_t, int,  \
                                  int, double, C2<R>::type*, const int*, cudaStream_t);         \
   template void launch_prep_batch<R>(const PrepCurve*, int, double*, int*, int*, int*, R*,      \
-                                     C2<R>::type*, int*, R*, C2<R>::type*, int*, cudaStream_t);
+                                     C2<R>::type*, int*, R*, C2<R>::type*, int*, cudaStream_t); \
+  template void launch_prep_one<R>(const PrepCurve&, double*, int*, int*, int*, R*,             \
+                                   C2<R>::type*, int*, R*, C2<R>::type*, int*, cudaStream_t);
 FTP_INST(float)
 FTP_INST(double)
 #undef FTP_INST
