@@ -886,6 +886,14 @@ def run_screen(args, world, rank, local, pg):
     clocks = clk.summary()
     launches = ftp.ftp_plan_info(plan)["last_launches"]
     stats = ftp.ftp_solver_stats(plan)
+    # one eager call with stage events: step (a) / screening / exact roots / re-solve
+    ftp.ftp_set_timing(plan, True)
+    call_sc()
+    torch.cuda.synchronize(dev)
+    st = ftp.ftp_stage_times(plan)
+    ftp.ftp_set_timing(plan, False)
+    stage = {"sums": round(st[0], 3), "screen": round(st[1], 3), "roots": round(st[4], 3),
+             "resolve": round(st[5], 3)}
     call_ex()
     ex_ms = _timed_calls(stream, flush, max(1, min(3, args.steps)), call_ex)
     P_ex, P_sc = ex[0].cpu().numpy(), sc[0].cpu().numpy()
@@ -921,7 +929,7 @@ def run_screen(args, world, rank, local, pg):
                                "loss_last": float(losses[-100:].mean())},
                      solver={"mean_iterations": round(stats["mean_iterations"], 3),
                              "items_last_call": stats["items"]},
-                     clocks=clocks, gpu_launches=args.steps * launches)
+                     stage_ms=stage, clocks=clocks, gpu_launches=args.steps * launches)
     net.close()
     ftp.ftp_destroy(plan)
     if rank == 0:

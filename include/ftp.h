@@ -307,8 +307,9 @@ ftp_status ftp_solver_stats(ftp_plan_t plan, int64_t* items, double* mean_iterat
  * [4] assembly + roots + candidates + polish (all template groups),
  * [5] re-solve of ill-conditioned frequencies from direct FP64 sums.
  * After ftp_batch (timed calls run eagerly, without a graph): [0] all of
- * step (a) for every curve, [1]-[3] zero, [4] and [5] as above, summed over
- * the chunks.
+ * step (a) for every curve, [1] features, surrogate scores and selection
+ * (screened and features-only batches; zero otherwise), [2]-[3] zero, [4]
+ * and [5] as above, summed over the chunks.
  */
 ftp_status ftp_set_timing(ftp_plan_t plan, int enable);
 ftp_status ftp_stage_times(ftp_plan_t plan, float* ms6);

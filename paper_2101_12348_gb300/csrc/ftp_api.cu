@@ -845,7 +845,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
   const bool tm = P->timing;
   for (size_t q = 0; q < chunks.size(); ++q) {
     const BChunk& ch = chunks[q];
-    if (tm) cudaEventRecord(P->bev[4 * q + 0], s);
+    if (tm) cudaEventRecord(P->bev[5 * q + 0], s);
     // step (a) preparation of every curve of the chunk in one launch
     // (moments, cells, tile order), then spreading, FFT and gather of each
     // curve, round-robin over the lanes (fork/join through events, so a
@@ -883,7 +883,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       FTP_CK(cudaEventRecord(L.done, L.s));
       FTP_CK(cudaStreamWaitEvent(s, L.done, 0));
     }
-    if (tm) cudaEventRecord(P->bev[4 * q + 1], s);
+    if (tm) cudaEventRecord(P->bev[5 * q + 1], s);
     if (scr && scr->moments_out)
       FTP_CK(cudaMemcpyAsync(scr->moments_out + (size_t)ch.c0 * MO_WORDS, P->d_bmom,
                              sizeof(double) * MO_WORDS * (size_t)(ch.c1 - ch.c0),
@@ -907,8 +907,9 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       *launches += r;
       if (!screened) {
         if (tm) {
-          cudaEventRecord(P->bev[4 * q + 2], s);
-          cudaEventRecord(P->bev[4 * q + 3], s);
+          cudaEventRecord(P->bev[5 * q + 2], s);
+          cudaEventRecord(P->bev[5 * q + 3], s);
+          cudaEventRecord(P->bev[5 * q + 4], s);
         }
         FTP_CK(cudaGetLastError());
         continue;
@@ -928,6 +929,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
                   P->d_status, s);
       *launches += 3;
     }
+    if (tm) cudaEventRecord(P->bev[5 * q + 2], s);
     FTP_CK(cudaMemsetAsync(P->d_bmark, 0, sizeof(int) * (size_t)ch.nf_total, s));
     FTP_CK(cudaMemsetAsync(P->d_bcount, 0, sizeof(int), s));
     for (const BLaunch& L : ch.launches) {
@@ -979,7 +981,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       if (r < 0) return FTP_ERR_CUDA;
       *launches += r;
     }
-    if (tm) cudaEventRecord(P->bev[4 * q + 2], s);
+    if (tm) cudaEventRecord(P->bev[5 * q + 3], s);
     const int ncc = (int)(ch.c1 - ch.c0);
     const CurveDesc* dcur = d_curves + ch.c0;
     launch_direct_sums_batch(dcur, ncc, P->d_bmom, P->d_status, P->d_blist, P->d_bcount,
@@ -1032,7 +1034,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       launch_redo_overflow(dcur, ncc, P->d_bmark, ch.nf_total, P->d_bcount, kBatchRedoCap, of, s);
       *launches += 1;
     }
-    if (tm) cudaEventRecord(P->bev[4 * q + 3], s);
+    if (tm) cudaEventRecord(P->bev[5 * q + 4], s);
     FTP_CK(cudaGetLastError());
   }
   return FTP_OK;
@@ -1346,7 +1348,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     }
   }
   if (P->timing) {
-    while (P->bev.size() < 4 * chunks.size()) {
+    while (P->bev.size() < 5 * chunks.size()) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) return FTP_ERR_CUDA;
       P->bev.push_back(e);
@@ -1496,11 +1498,13 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     for (int i = 0; i < 6; ++i) P->stage_ms[i] = 0.f;
     for (size_t q = 0; q < chunks.size(); ++q) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, P->bev[4 * q], P->bev[4 * q + 1]) == cudaSuccess)
+      if (cudaEventElapsedTime(&ms, P->bev[5 * q], P->bev[5 * q + 1]) == cudaSuccess)
         P->stage_ms[0] += ms;
-      if (cudaEventElapsedTime(&ms, P->bev[4 * q + 1], P->bev[4 * q + 2]) == cudaSuccess)
+      if (cudaEventElapsedTime(&ms, P->bev[5 * q + 1], P->bev[5 * q + 2]) == cudaSuccess)
+        P->stage_ms[1] += ms;
+      if (cudaEventElapsedTime(&ms, P->bev[5 * q + 2], P->bev[5 * q + 3]) == cudaSuccess)
         P->stage_ms[4] += ms;
-      if (cudaEventElapsedTime(&ms, P->bev[4 * q + 2], P->bev[4 * q + 3]) == cudaSuccess)
+      if (cudaEventElapsedTime(&ms, P->bev[5 * q + 3], P->bev[5 * q + 4]) == cudaSuccess)
         P->stage_ms[5] += ms;
     }
     cudaGetLastError();

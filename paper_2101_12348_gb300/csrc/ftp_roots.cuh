@@ -1079,16 +1079,30 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       // corrected phase.  One loop keeps a single copy of the sums' code.
       WC pe = psi;
       bool again = false;
+      W MM0 = w_zero<W>(), YM0 = w_zero<W>(), Mb0 = w_zero<W>();
 #pragma unroll 1
       for (int pass = 0; pass < 2; ++pass) {
         W v[8];
         trig_sums(pe, v);
         if (pass == 1) {
           if (again) {
-            MM = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
-            YM = w_mulf(v[3], 2.0f);
-            Mbar = w_mulf(v[6], 2.0f);
-            th1 = (w_f(MM) > 0.0f) ? w_div(YM, MM) : w_zero<W>();
+            const W MM1 = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
+            const W YM1 = w_mulf(v[3], 2.0f);
+            // keep the corrected phase unless it lowers P (a step that left
+            // the maximum's basin): P0 = YM0^2 / MM0 against P1
+            const double m0 = w_d(MM0), m1 = w_d(MM1), y0 = w_d(YM0), y1 = w_d(YM1);
+            if (m1 > 0.0 && y1 * y1 * m0 >= y0 * y0 * m1 * (1.0 - 1e-11)) {
+              MM = MM1;
+              YM = YM1;
+              Mbar = w_mulf(v[6], 2.0f);
+              th1 = w_div(YM, MM);
+            } else {
+              dl = w_zero<W>();
+              MM = MM0;
+              YM = YM0;
+              Mbar = Mb0;
+              th1 = (w_f(MM) > 0.0f) ? w_div(YM, MM) : w_zero<W>();
+            }
           }
           break;
         }
@@ -1098,9 +1112,15 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         const W YMt = w_mulf(v[4], -2.0f), YMtt = w_mulf(v[5], -2.0f);
         Mbar = w_mulf(v[6], 2.0f);
         const W Mbart = w_mulf(v[7], -2.0f);
+        MM0 = MM;
+        YM0 = YM;
+        Mb0 = Mbar;
         // The residual g is formed in the wide type; on the float-float path
-        // the correction itself only needs FP32 (|dl| < 1e-3, so its
-        // relative error of ~1e-7 is below 1e-10 absolute).
+        // the correction itself only needs FP32 (|dl| < 0.05, so its
+        // relative error of ~1e-7 is below 5e-9 absolute, and a Newton step
+        // from an FP32 root leaves an error of order dl^2).  A root of F near
+        // a flat maximum can be off by more than 1e-3 rad in FP32; larger
+        // steps are checked against P below.
         if (a.polish_steps > 0 && !constant) {
           const W g = w_sub(w_mulf(w_mul(MM, YMt), 2.0f), w_mul(YM, MMt));
           const W gt = w_sub(w_add(w_mul(MMt, YMt), w_mulf(w_mul(MM, YMtt), 2.0f)), w_mul(YM, MMtt));
@@ -1111,7 +1131,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
             d = w_div(g, gt);
           }
           const float df = w_f(d);
-          if (isfinite(df) && fabsf(df) < 1e-3f) dl = d;
+          if (isfinite(df) && fabsf(df) < 0.05f) dl = d;
         }
         if (w_f(MM) > 0.0f) {
           const W q = w_div(YM, MM);
@@ -1127,7 +1147,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         Mbar = w_sub(Mbar, w_mul(dl, Mbart));
         // A correction that is not tiny (an ill-conditioned item) makes the
         // O(dl^2) shortcut too coarse: evaluate again at the corrected phase
-        // psi e^{-i dl} (Taylor series of cos, sin; |dl| < 1e-3).
+        // psi e^{-i dl} (Taylor series of cos, sin to dl^5: truncation below
+        // 3e-11 for |dl| < 0.05).
         again = fabsf(w_f(dl)) > (kFast ? 1e-5f : 1e-9f);
         if (!__any_sync(0xffffffffu, again)) break;
         const W d2 = w_mul(dl, dl);
@@ -1136,6 +1157,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
                                                                   w_mul(d2, w_of<W>(1.0 / 120.0))))));
         pe = mkc(w_add(w_mul(re(psi), cs), w_mul(im(psi), sn)),
                  w_sub(w_mul(im(psi), cs), w_mul(re(psi), sn)));
+        {  // back onto |psi| = 1 (the truncated series leaves ~dl^6/720)
+          const W sfac = w_sub(w_of<W>(1.5), w_mulf(c_abs2<W>(pe), 0.5f));
+          pe = mkc(w_mul(re(pe), sfac), w_mul(im(pe), sfac));
+        }
       }
     }
     W theta;
