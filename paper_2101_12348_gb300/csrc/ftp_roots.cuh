@@ -556,9 +556,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     }
     return r;
   };
-  // Lane 0 stages the 3H sum rows of unit r into buffer `buf`.
+  // The warp stages the sum rows of unit r into buffer `buf`: lane 0 arms the
+  // mbarrier with the unit's byte count, then the lanes issue one row copy
+  // each (one lane issuing all 3H copies was a sixth of the second kernel's
+  // time).  Called by the whole warp.
   auto issue = [&](const URef& r, int buf) {
-    if (lane != 0) return;
     int64_t base = r.kfirst, stride = a.nf_pad;
     int Hs = a.Hs;
     if (batched && r.seg >= 0) {
@@ -569,12 +571,13 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       }
     }
     S2* dst = stage + (size_t)buf * (C::STAGE_BYTES / sizeof(S2));
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const int nrows = a.coef_mode ? C::CROWS : C::ROWS;
-    mbar_expect_tx(&mbar[buf], (unsigned)(nrows * C::ROW_BYTES));
+    if (lane == 0) mbar_expect_tx(&mbar[buf], (unsigned)(nrows * C::ROW_BYTES));
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     const S2* sums = reinterpret_cast<const S2*>(a.sums);
 #pragma unroll 1
-    for (int r2 = 0; r2 < nrows; ++r2) {
+    for (int r2 = lane; r2 < nrows; r2 += 32) {
       const int src_row = a.coef_mode ? r2 : (r2 < 2 * H) ? r2 : 2 * Hs + (r2 - 2 * H);
       const int64_t off = (int64_t)src_row * stride + base;
       if (!FTP_DCHECK(a.status, off >= 0 && off + NGW <= a.sums_elems, 11, off, a.sums_elems) ||
@@ -687,6 +690,27 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         C64[0] = c_zero<W>();
         Bw[0] = mk<R2>(0, 0);
       }
+      if constexpr (PH == 2) {
+        // the second kernel evaluates <M^2> - Mbar^2: a_e + S_e from the rows
+        __syncwarp();
+        for (int e = gl; e <= 2 * H; e += G) {
+          WC S = c_zero<W>();
+          if (e == 0) {
+            W q = w_zero<W>();
+            for (int n = 1; n <= H; ++n) q = w_add(q, c_abs2<W>(C64[n]));
+            S = mkc(w_mulf(q, 2.0f), w_zero<W>());
+          } else {
+            const int nlo = e - H > 1 ? e - H : 1;
+            for (int n = nlo; 2 * n <= e; ++n) {
+              const WC t = c_mul<W>(C64[n], C64[e - n]);
+              S = c_add<W>(S, (2 * n == e) ? t : c_mulf<W>(t, 2.0f));
+            }
+            for (int n = e + 1; n <= H; ++n)
+              S = c_add<W>(S, c_mulf<W>(c_mul<W>(C64[n], c_conj<W>(C64[n - e])), 2.0f));
+          }
+          A64[e] = c_add<W>(A64[e], S);
+        }
+      }
     } else {
       // ---- sums of this item into wide shared memory (one conversion each)
       for (int q = gl; q < C::ROWS; q += G) {
@@ -722,14 +746,19 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         }
       }
       __syncwarp();
-      // a_e = conj(Z_e) K_e - S_e over slots {0}, {e, 2H+1-e}
+      // a_e = conj(Z_e) K_e - S_e over slots {0}, {e, 2H+1-e}.  The second
+      // kernel keeps the raw part conj(Z_e) K_e (the coefficients of <M^2>)
+      // and subtracts Mbar^2 at the evaluation point instead of S_e (the
+      // coefficients of Mbar^2): O(H) products per item instead of O(H^2).
       for (int s = gl; s < C::NSLOT; s += G) {
   #pragma unroll
         for (int half = 0; half < 2; ++half) {
           if (s == 0 && half == 1) break;
           const int e = (s == 0) ? 0 : (half == 0 ? s : 2 * H + 1 - s);
           WC acc;
-          if (e == 0) {
+          if constexpr (PH == 2) {
+            acc = (e == 0) ? mkc(re(KE[0]), w_zero<W>()) : c_mul<W>(c_conj<W>(Z64[e]), KE[e]);
+          } else if (e == 0) {
             W q = w_zero<W>();
             for (int n = 1; n <= H; ++n) q = w_add(q, c_abs2<W>(C64[n]));
             acc = mkc(w_sub(re(KE[0]), w_mulf(q, 2.0f)), w_zero<W>());
@@ -1052,7 +1081,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       const WC pw0 = group_powers<G, W>(ps0, gl);  // psi^(gl+1)
       const WC stp = mkc(w_shfl(re(pw0), G - 1, G), w_shfl(im(pw0), G - 1, G));  // psi^G
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = w_zero<W>();
+      for (int i = 0; i < 9; ++i) v[i] = w_zero<W>();
       WC pw = pw0;
 #pragma unroll 1
       for (int e = gl + 1; e <= 2 * H; e += G) {
@@ -1068,10 +1097,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
           const WC tc = c_mul<W>(C64[e], pw);
           v[6] = w_add(v[6], re(tc));
           v[7] = w_add(v[7], w_mulf(im(tc), (float)e));
+          v[8] = w_add(v[8], w_mulf(re(tc), (float)(e * e)));
         }
         pw = c_mul<W>(pw, stp);
       }
       wsum8<G, W>(v, gl);
+      v[8] = wsum<G>(v[8]);
     };
     W MM, YM, Mbar, dl = w_zero<W>(), th1 = w_zero<W>();
     {
@@ -1082,11 +1113,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       W MM0 = w_zero<W>(), YM0 = w_zero<W>(), Mb0 = w_zero<W>();
 #pragma unroll 1
       for (int pass = 0; pass < 2; ++pass) {
-        W v[8];
+        W v[9];
         trig_sums(pe, v);
+        // <M^2> = Q, Mbar and their theta-derivatives; MM = Q - Mbar^2
+        const W Mb = w_mulf(v[6], 2.0f);
+        const W Q = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
         if (pass == 1) {
           if (again) {
-            const W MM1 = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
+            const W MM1 = w_sub(Q, w_mul(Mb, Mb));
             const W YM1 = w_mulf(v[3], 2.0f);
             // keep the corrected phase unless it lowers P (a step that left
             // the maximum's basin): P0 = YM0^2 / MM0 against P1
@@ -1094,7 +1128,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
             if (m1 > 0.0 && y1 * y1 * m0 >= y0 * y0 * m1 * (1.0 - 1e-11)) {
               MM = MM1;
               YM = YM1;
-              Mbar = w_mulf(v[6], 2.0f);
+              Mbar = Mb;
               th1 = w_div(YM, MM);
             } else {
               dl = w_zero<W>();
@@ -1106,12 +1140,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
           }
           break;
         }
-        MM = w_add(re(A64[0]), w_mulf(v[0], 2.0f));
-        const W MMt = w_mulf(v[1], -2.0f), MMtt = w_mulf(v[2], -2.0f);
+        Mbar = Mb;
+        const W Mbart = w_mulf(v[7], -2.0f), Mbartt = w_mulf(v[8], -2.0f);
+        MM = w_sub(Q, w_mul(Mbar, Mbar));
+        const W MMt = w_sub(w_mulf(v[1], -2.0f), w_mulf(w_mul(Mbar, Mbart), 2.0f));
+        const W MMtt = w_sub(w_mulf(v[2], -2.0f),
+                             w_mulf(w_add(w_mul(Mbart, Mbart), w_mul(Mbar, Mbartt)), 2.0f));
         YM = w_mulf(v[3], 2.0f);
         const W YMt = w_mulf(v[4], -2.0f), YMtt = w_mulf(v[5], -2.0f);
-        Mbar = w_mulf(v[6], 2.0f);
-        const W Mbart = w_mulf(v[7], -2.0f);
         MM0 = MM;
         YM0 = YM;
         Mb0 = Mbar;
