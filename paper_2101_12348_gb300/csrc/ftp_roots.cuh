@@ -852,15 +852,13 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     //      upper convex hull of the points (k, log2|F_k|^2), k = 0..D.  An
     //      edge from vertex a to vertex b stands for b - a roots of modulus
     //      about 2^(-slope/2).  F is anti-self-inversive (|F_k| = |F_{D-k}|),
-    //      so the hull is symmetric about D/2: only k <= D/2 are tested, slot
+    //      so the hull is symmetric about D/2: only k <= D/2 matter, slot
     //      m < D/2 takes the m-th root counted from the innermost circle and
     //      slot D/2 + m its mirror 1/conj(z), half a step further round.  The
     //      circles' angles are offset by golden-ratio multiples of their first
-    //      vertex, so that no two circles start aligned.  Every lane tests
-    //      vertices k = gl, gl + G, ... against all other points (strict test:
-    //      collinear points are not vertices), in FP32 for either precision.
+    //      vertex, so that no two circles start aligned.  FP32 for either
+    //      precision.
     constexpr int HD = D / 2;
-    constexpr int NKV = cdiv_i(HD + 1, G);
     __syncwarp();
     float* Lg = reinterpret_cast<float*>(Z64);  // the sums are dead after the assembly
     for (int q = gl; q <= HD; q += G) {
@@ -868,36 +866,35 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       Lg[q] = __log2f(fmaf(fx, fx, fmaf(fy, fy, 1.17549435e-38f)));
     }
     __syncwarp();
+    // Vertices: lane 0 of each group runs a monotone chain over the left half
+    // k = 0..D/2 (a point is popped unless strictly above the chord), and the
+    // hull's left half is that chain while it still rises — by symmetry the
+    // rest lies under the horizontal edge to the mirror vertex.  The same set
+    // as testing every point against all D + 1 points (strict: collinear
+    // points are not vertices), in O(D) instead of O(D^2) work per item.
     unsigned long long vmask = 1ull;  // k = 0 is always a vertex
-    {
-      float Lk[NKV], minl[NKV], maxr[NKV];
-#pragma unroll
-      for (int v = 0; v < NKV; ++v) {
-        const int k = gl + G * v;
-        Lk[v] = k <= HD ? Lg[k] : 0.0f;
-        minl[v] = __int_as_float(0x7f800000);
-        maxr[v] = -__int_as_float(0x7f800000);
+    if (gl == 0) {
+      unsigned char* stk = reinterpret_cast<unsigned char*>(Lg + (HD + 1));
+      int sz = 0;
+#pragma unroll 1
+      for (int k = 0; k <= HD; ++k) {
+        const float Lk = Lg[k];
+        while (sz >= 2) {
+          const int o = stk[sz - 2], q = stk[sz - 1];
+          const float cr = (float)(q - o) * (Lk - Lg[o]) - (float)(k - o) * (Lg[q] - Lg[o]);
+          if (cr >= 0.0f) --sz;  // q not strictly above the chord o -> k (NaN: kept)
+          else break;
+        }
+        stk[sz++] = (unsigned char)k;
       }
 #pragma unroll 1
-      for (int d = 1; d <= D; ++d) {
-        const float inv = fast_rcp((float)d);
-#pragma unroll
-        for (int v = 0; v < NKV; ++v) {
-          const int k = gl + G * v;
-          if (k > HD) continue;
-          if (d <= k) minl[v] = fminf(minl[v], (Lk[v] - Lg[k - d]) * inv);
-          const int j = k + d;
-          if (j <= D) maxr[v] = fmaxf(maxr[v], (Lg[j <= HD ? j : D - j] - Lk[v]) * inv);
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < NKV; ++v) {
-        const int k = gl + G * v;
-        if (k <= HD && minl[v] > maxr[v]) vmask |= 1ull << k;
+      for (int i = 1; i < sz; ++i) {
+        const int p = stk[i - 1], q = stk[i];
+        if (!(Lg[q] > Lg[p])) break;
+        vmask |= 1ull << q;
       }
     }
-#pragma unroll
-    for (int sh = G / 2; sh > 0; sh >>= 1) vmask |= __shfl_xor_sync(0xffffffffu, vmask, sh, G);
+    vmask = __shfl_sync(0xffffffffu, vmask, 0, G);
 
     // ---- (c) Aberth-Ehrlich on F (degree D), roots i = r*G + gl
     R2 z[RR];

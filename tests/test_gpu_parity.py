@@ -154,6 +154,32 @@ def test_device_and_host_pointers_agree(ftp, prec):
     assert np.mean(same) >= 0.99
 
 
+@pytest.mark.parametrize("n_obs", [300, 5000])
+def test_stage_timing_and_both_preparation_paths(ftp, n_obs):
+    """Stage events: the first root kernel's time is positive and inside the
+    root stage.  300 observations take the single-CTA step (a) preparation,
+    5000 the multi-kernel one; both agree with the oracle."""
+    rng = np.random.default_rng(40 + n_obs)
+    tpl = synth.make_template(4, 4040)
+    lc = synth.random_curve(rng, n_obs, T=60.0, signal=0.3, tpl=tpl, period=3.1, phase=0.4)
+    grid = synth.Grid(df=1 / (5 * 60.0), k0=1, nf=900)
+    dev = torch.device("cuda:0")
+    with ftp.Plan(n_obs, tpl.H, (grid.df, grid.k0, grid.nf), 1, "mixed") as plan:
+        td = [torch.from_numpy(a).to(dev) for a in (lc.t, lc.y, lc.dy)]
+        outs = [torch.empty(grid.nf, dtype=torch.float64, device=dev) for _ in range(4)]
+        ftp.ftp_set_timing(plan.h, True)
+        ftp.ftp_periodogram(plan.h, *td, n_obs, [(tpl.c, tpl.s)], *outs, None)
+        torch.cuda.synchronize()
+        st = ftp.ftp_stage_times(plan.h)
+        first = ftp.ftp_roots_first_phase_ms(plan.h)
+        ftp.ftp_set_timing(plan.h, False)
+    assert all(v >= 0 for v in st) and st[4] > 0
+    assert 0 < first <= st[4]
+    sel = np.arange(0, grid.nf, 7)
+    ref = oracle.periodogram(lc.t, lc.y, lc.dy, grid.freqs()[sel], tpl.c, tpl.s)
+    assert np.max(np.abs(outs[0].cpu().numpy()[sel] - ref["power"])) <= TOL_P["mixed"]
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_input_errors(ftp, prec):
     rng = np.random.default_rng(3)
