@@ -215,6 +215,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
+// ------------------------------------------------------------ packed FP32
+// Pairs of FP32 values in one 64-bit register pair, operated on by the
+// f32x2 instructions of sm_100-class GPUs: one instruction does the work of
+// two FP32 ones, and each element is rounded exactly as the scalar
+// instruction would round it.
+using f2p = unsigned long long;
+__device__ __forceinline__ f2p pk2(float lo, float hi) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f2p v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+  f2p d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+  f2p d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // ------------------------------------------------------------ Aberth step
 // One Aberth-Ehrlich iteration for the NS root slots of a lane.  Slot r holds
 // root idx[r] of the item (idx < 0: an empty slot, marked converged), z[r] its
@@ -235,6 +260,81 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
     dp[r] = mk<R2>(0, 0);
     S[r] = mk<R2>(0, 0);
   }
+  if constexpr (kFast && NS >= 2) {
+    // FP32: slots 2q and 2q+1 travel as packed pairs (real parts in one,
+    // imaginary parts in the other), the same FMAs in the same order as
+    // the scalar loops below, in half the instructions
+    constexpr int NP = NS / 2;
+    f2p UX[NP], UY[NP], UYn[NP], PX[NP], PY[NP], DX[NP], DY[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      UX[q] = pk2(uu[2 * q].x, uu[2 * q + 1].x);
+      UY[q] = pk2(uu[2 * q].y, uu[2 * q + 1].y);
+      UYn[q] = pk2(-uu[2 * q].y, -uu[2 * q + 1].y);
+      PX[q] = PY[q] = DX[q] = DY[q] = 0ull;
+    }
+#pragma unroll 2
+    for (int c = D; c >= 0; --c) {
+      const R2 f = Fs[c];
+      const f2p FX = pk2(f.x, f.x), FY = pk2(f.y, f.y);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        // dp = dp u + p, then p = p u + f (complex)
+        const f2p ndx = fma2(DX[q], UX[q], fma2(DY[q], UYn[q], PX[q]));
+        const f2p ndy = fma2(DX[q], UY[q], fma2(DY[q], UX[q], PY[q]));
+        const f2p npx = fma2(PX[q], UX[q], fma2(PY[q], UYn[q], FX));
+        const f2p npy = fma2(PX[q], UY[q], fma2(PY[q], UX[q], FY));
+        DX[q] = ndx;
+        DY[q] = ndy;
+        PX[q] = npx;
+        PY[q] = npy;
+      }
+      if constexpr (NS % 2 != 0) {
+        dp[NS - 1] = cfma(dp[NS - 1], uu[NS - 1], p[NS - 1]);
+        p[NS - 1] = cfma(p[NS - 1], uu[NS - 1], f);
+      }
+    }
+    f2p ZX[NP], ZY[NP], SX[NP], SYn[NP];  // SYn accumulates -Im S
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      ZX[q] = pk2(z[2 * q].x, z[2 * q + 1].x);
+      ZY[q] = pk2(z[2 * q].y, z[2 * q + 1].y);
+      SX[q] = SYn[q] = 0ull;
+    }
+    const f2p tiny2 = pk2(1e-30f, 1e-30f);
+#pragma unroll 2
+    for (int j = 0; j < D; ++j) {
+      const R2 zj = Zs[j];
+      const f2p JX = pk2(zj.x, zj.x), JY = pk2(zj.y, zj.y);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const f2p dx = sub2(ZX[q], JX), dy = sub2(ZY[q], JY);
+        float ma, mb;
+        upk2(fma2(dx, dx, fma2(dy, dy, tiny2)), ma, mb);
+        const f2p inv = pk2(fast_rcp(ma), fast_rcp(mb));
+        SX[q] = fma2(dx, inv, SX[q]);
+        SYn[q] = fma2(dy, inv, SYn[q]);
+      }
+      if constexpr (NS % 2 != 0) {
+        const R2 d = csub(z[NS - 1], zj);
+        const R inv = fast_rcp(fma(d.x, d.x, fma(d.y, d.y, R(1e-30))));
+        S[NS - 1].x = fma(d.x, inv, S[NS - 1].x);
+        S[NS - 1].y = fma(-d.y, inv, S[NS - 1].y);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      upk2(PX[q], p[2 * q].x, p[2 * q + 1].x);
+      upk2(PY[q], p[2 * q].y, p[2 * q + 1].y);
+      upk2(DX[q], dp[2 * q].x, dp[2 * q + 1].x);
+      upk2(DY[q], dp[2 * q].y, dp[2 * q + 1].y);
+      upk2(SX[q], S[2 * q].x, S[2 * q + 1].x);
+      float sa, sb;
+      upk2(SYn[q], sa, sb);
+      S[2 * q].y = -sa;
+      S[2 * q + 1].y = -sb;
+    }
+  } else {
 #pragma unroll 2
   for (int c = D; c >= 0; --c) {
     const R2 f = Fs[c];
@@ -256,6 +356,7 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
       S[r].x = fma(d.x, inv, S[r].x);
       S[r].y = fma(-d.y, inv, S[r].y);
     }
+  }
   }
 #pragma unroll
   for (int r = 0; r < NS; ++r) {
