@@ -1,16 +1,19 @@
-// Steps (b) and (c) of the Fast Template Periodogram, fused in one kernel:
-// polynomial assembly (Section 2: MM_nm, YM_k, Eq. finalpoly), all zeros of
-// the final polynomial by Aberth-Ehrlich iteration, candidates scaled onto
-// the unit circle (Section 2, end), the best one chosen and polished by a
-// Newton step on the phase in FP64, and (theta1, theta2, theta3, P).
+// Steps (b) and (c) of the Fast Template Periodogram in two kernels over the
+// same work units: polynomial assembly (Section 2: MM_nm, YM_k, Eq.
+// finalpoly), all zeros of the final polynomial by Aberth-Ehrlich iteration
+// from Newton-polygon initial guesses, candidates scaled onto the unit circle
+// (Section 2, end) and the best one chosen (first kernel); then the chosen
+// phase polished by a Newton step and (theta1, theta2, theta3, P) evaluated
+// at it in FP64-class arithmetic (second kernel).
 //
 // Work item = (frequency k, template tau).  A group of G lanes owns one item:
 // it assembles the coefficients, then each lane iterates R = ceil(D/G) of the
-// D = 6H-2 roots.  Each warp takes work units (32/G consecutive frequencies of
-// one template) from a global queue and stages their sum tiles (3H rows in the
-// [3H][nf_pad] layout) into its own shared memory with TMA bulk copies,
-// double-buffered so the next unit's copy overlaps this unit's arithmetic.
-// Warps never wait for each other.
+// D = 6H-2 roots, fewer once most have converged (compaction).  Each warp
+// takes work units (32/G consecutive frequencies of one template) from a
+// global queue and stages their sum tiles (3H rows in the [3H][nf_pad]
+// layout) into its own shared memory with TMA bulk copies, double-buffered so
+// the next unit's copy overlaps this unit's arithmetic.  Warps never wait for
+// each other.
 //
 // Notation.  Z_h = sum_i w_i e^{i h omega t_i} (Z_0 = 1, Z_{-h} = conj Z_h),
 // Y_h = sum_i w_i (y_i - ybar) e^{i h omega t_i}, alpha_n = (c_n + i s_n)/2.
@@ -28,12 +31,13 @@
 // The final polynomial F = 2 MM' d(YM') - YM' d(MM') is anti-self-inversive,
 // F_{D-p} = -conj(F_p), so only p = 0..3H-1 are formed and the rest mirrored.
 //
-// Precision.  a_e, b_k, c_n are always assembled in FP64 and the chosen phase
-// is always polished and evaluated in FP64.  F, the Aberth iteration and the
-// candidate screening run in the kernel's working precision R (float for the
-// mixed path, double for the FP64 path).  The sum tiles are float2 (mixed,
-// from the FP32 NFFT) or double2 (FP64 NFFT, or direct FP64 sums of the
-// re-solve pass).
+// Precision.  a_e, b_k, c_n are assembled, and the chosen phase is polished
+// and evaluated, in an FP64-class type W: native FP64 on the FP64 path and for
+// FP64 sums, float-float (ftp_wide.cuh) on the mixed path.  F, the Aberth
+// iteration and the candidate screening run in the kernel's working precision
+// R (float for the mixed path, double for the FP64 path).  The sum tiles are
+// float2 (mixed, from the FP32 NFFT) or double2 (FP64 NFFT, or direct FP64
+// sums of the re-solve pass).
 #pragma once
 
 #include <math.h>
