@@ -387,7 +387,7 @@ def run_ours(args, world, rank, local, pg):
 
 
 # ------------------------------------------------------------------ extra workloads
-SURVEY = ("batched survey: {n} lightcurves, N_obs lognormal (median 1000, clipped 50-20000), "
+BATCH_SURVEY = ("batched survey: {n} lightcurves, N_obs lognormal (median 1000, clipped 50-20000), "
           "baselines U(100,3000) d, bank of 16 templates H in (2,4,6), one per curve, "
           "df=1/(5T), f<=10/d")
 BANK = ("template bank over one long lightcurve: N_obs=1e5 over 4000 d with nightly gaps, "
@@ -526,7 +526,7 @@ def run_survey(args, world, rank, local, pg):
     e2e = {"value": round(sum_over_ranks(pg, float(e2e_steps * tot), dev) / e2e_s, 1),
            "unit": UNIT, "h2d_bytes_per_step": int(3 * sv.t.size * 8),
            "d2h_bytes_per_step": int(tot * 33), "steps": e2e_steps}
-    cfg = {"workload": SURVEY.format(n=sv.ncurves), "curves": sv.ncurves,
+    cfg = {"workload": BATCH_SURVEY.format(n=sv.ncurves), "curves": sv.ncurves,
            "n_obs_total": int(sv.t.size), "evals_per_step": tot, "templates_per_curve": 1,
            "l2": "flushed between steps (512 MiB write); sum tiles exceed L2",
            "graph": {0: "eager", 1: "captured", 2: "replayed"}[info["graph"]],
