@@ -11,3 +11,49 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="session")
+def orthogonal_grid():
+    """The hand-derived closed-form case in golden/orthogonal_grid.json:
+    uniform samples over whole cycles, so every harmonic product averages to
+    zero and P, |theta1|, theta3 and the phase relation follow exactly."""
+    import json
+
+    import numpy as np
+
+    with open(os.path.join(GOLDEN, "orthogonal_grid.json")) as fh:
+        g = json.load(fh)
+    N, T, sig = g["N"], g["T"], g["signal"]
+    t = np.arange(N) * T / N
+    y = sig["a"] * np.cos(2.0 * np.pi * sig["k_sig"] * t / T + sig["phi0"]) + sig["b"]
+    dy = np.full(N, g["dy"])
+    c = np.array(g["template"]["c"])
+    s = np.array(g["template"]["s"])
+    k0, nf = g["grid"]["k0"], g["grid"]["nf"]
+    return dict(g=g, t=t, y=y, dy=dy, c=c, s=s, df=1.0 / T, k0=k0, nf=nf,
+                freqs=(k0 + np.arange(nf)) / T, psi=np.arctan2(s, c), phi0=sig["phi0"])
+
+
+def check_orthogonal_grid(case, res, tol_p, tol_amp, tol_phase):
+    """Compare one template's outputs (arrays over the case's frequencies)
+    with the closed form: P everywhere; |theta1|, theta3 and
+    h theta2 + psi_h + phi0 = 0 (theta1 > 0) or pi (theta1 < 0), mod 2 pi,
+    where a harmonic matches the signal."""
+    import numpy as np
+
+    for e in case["g"]["expected"]:
+        q = e["k"] - case["k0"]
+        assert abs(res["power"][q] - e["P"]) <= tol_p, (e["k"], res["power"][q], e["P"])
+        if e["h"] is None:
+            continue
+        h = e["h"]
+        th1 = res["theta1"][q]
+        assert abs(abs(th1) - e["abs_theta1"]) <= tol_amp, (e["k"], th1)
+        assert abs(res["theta3"][q] - e["theta3"]) <= tol_amp, (e["k"], res["theta3"][q])
+        target = 0.0 if th1 > 0 else np.pi
+        rel = h * res["theta2"][q] + case["psi"][h - 1] + case["phi0"] - target
+        assert abs(np.angle(np.exp(1j * rel))) <= h * tol_phase, (e["k"], res["theta2"][q])

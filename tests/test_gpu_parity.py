@@ -63,6 +63,22 @@ def small_workload():
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_golden_orthogonal_grid(ftp, orthogonal_grid, prec):
+    """The hand-derived closed form in tests/golden/orthogonal_grid.json
+    (uniform samples over whole cycles, H = 3): P = A_h^2 / sum A_n^2 where
+    harmonic h of the template matches the signal, 0 elsewhere, with the
+    matching |theta1|, theta3 and phase; the h-fold tie of the optimum may
+    resolve to any of its members."""
+    from conftest import check_orthogonal_grid
+
+    cs = orthogonal_grid
+    with ftp.Plan(cs["t"].size, 3, (cs["df"], cs["k0"], cs["nf"]), 1, prec) as plan:
+        r = plan.periodogram(cs["t"], cs["y"], cs["dy"], [(cs["c"], cs["s"])])
+    g = {k: v[0] for k, v in r.items()}
+    check_orthogonal_grid(cs, g, TOL_P[prec], TOL_AMP[prec], TOL_PHASE[prec])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_small_workload_every_frequency(ftp, small_workload, prec):
     """N=200, H=3, 5000 frequencies: every frequency against the oracle."""
     lc, tpl, grid, ref = small_workload

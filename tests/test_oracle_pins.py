@@ -93,6 +93,20 @@ def small_case(seed, n_obs=40, H=3, signal=0.3, T=8.0):
 
 
 # ---------------------------------------------------------------- pins
+def test_golden_orthogonal_grid_closed_form(orthogonal_grid):
+    """tests/golden/orthogonal_grid.json: values derived by hand from Section 2's
+    definitions for uniform samples over whole cycles (every harmonic product
+    averages to zero): P = A_h^2 / sum A_n^2 at frequencies where harmonic h
+    matches the signal, 0 elsewhere, with the matching amplitude, offset and
+    phase.  Catches a wrong MM normalisation or a harmonic index slip, which
+    single-harmonic pins cannot see."""
+    from conftest import check_orthogonal_grid
+
+    cs = orthogonal_grid
+    r = oracle.periodogram(cs["t"], cs["y"], cs["dy"], cs["freqs"], cs["c"], cs["s"])
+    check_orthogonal_grid(cs, r, tol_p=1e-12, tol_amp=1e-10, tol_phase=1e-9)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_h1_is_floating_mean_lomb_scargle(seed):
     """H = 1: the template periodogram is the floating-mean LS periodogram
@@ -347,6 +361,24 @@ def test_planted_mistakes_fail_a_pin(monkeypatch, mutant):
             caught = True
             break
     assert caught
+
+
+def test_planted_mistake_conjugated_alpha_is_caught_by_the_golden_case(monkeypatch,
+                                                                      orthogonal_grid):
+    """The closed-form golden case fails when the oracle builds its
+    polynomials from alpha_n = (c_n - i s_n)/2 (the conjugate of Section 2's
+    alpha_n): the candidate phases then sit at h theta2 = psi_h - phi0
+    instead of -(psi_h + phi0), and the power evaluated there from the data
+    falls short of A_h^2 / sum A_n^2."""
+    from conftest import check_orthogonal_grid
+
+    cs = orthogonal_grid
+    mod = oracle.ftp_oracle
+    orig = mod.template_alpha
+    monkeypatch.setattr(mod, "template_alpha", lambda c, s: np.conj(orig(c, s)))
+    r = mod.periodogram(cs["t"], cs["y"], cs["dy"], cs["freqs"], cs["c"], cs["s"])
+    with pytest.raises(AssertionError):
+        check_orthogonal_grid(cs, r, tol_p=1e-6, tol_amp=1e-6, tol_phase=1e-6)
 
 
 # ---------------------------------------------------------------- positive amplitudes
