@@ -18,7 +18,8 @@
  *       (Section 2, Eq. finalpoly), of degree 6H-2;
  *   (c) all zeros of that polynomial by Aberth-Ehrlich iteration, scaled onto
  *       the unit circle (Section 2, end), P evaluated at every candidate,
- *       the best one polished by a Newton step in FP64.
+ *       the best one polished by a Newton step (FP64 on the FP64 path,
+ *       float-float on the mixed one).
  *
  * Conventions shared by every entry point
  *   - Frequencies are in cycles per unit time, omega = 2 pi f.  The grid is
@@ -69,10 +70,12 @@ typedef enum {
 
 typedef enum {
   FTP_FP64 = 0,  /* FP64 everywhere: sums, assembly, roots, candidates */
-  FTP_MIXED = 1  /* FP32 NFFT sums (FP64 phase reduction), FP64 assembly of
-                    MM' and YM', FP32 final polynomial, Aberth and screening,
-                    FP64 Newton polish and evaluation of the chosen phase;
-                    ill-conditioned frequencies re-solved from FP64 sums */
+  FTP_MIXED = 1  /* FP32 NFFT sums (FP64 phase reduction); assembly of MM'
+                    and YM' in float-float (FMA-based two-word FP32, about
+                    44 significant bits); FP32 final polynomial, Aberth and
+                    candidate screening; Newton polish and evaluation of the
+                    chosen phase in float-float; ill-conditioned frequencies
+                    re-solved from FP64 sums */
 } ftp_precision;
 
 /* Per-frequency flag bits (uint8). */
