@@ -157,9 +157,11 @@ ftp_status ftp_periodogram(ftp_plan_t plan, const double* t, const double* y, co
  * may be host or device.
  *
  * Execution: the curves are cut into chunks whose sum tiles fit the plan's
- * chunk budget (ftp_set_batch_options; 8 GiB by default).  Per chunk, step
- * (a) runs curve by curve, several curves at once on concurrent streams
- * (ftp_set_batch_tuning), into the chunk's sum tiles, then steps (b)-(c) run
+ * chunk budget (ftp_set_batch_options; 8 GiB by default).  Per chunk, one
+ * launch prepares every curve of step (a) (weights, moments, grid cells and
+ * tile order, one CTA per curve); spreading, FFT and gather then run curve by
+ * curve, several curves at once on concurrent streams (ftp_set_batch_tuning),
+ * into the chunk's sum tiles, then steps (b)-(c) run
  * as one persistent kernel launch per harmonic count H over every
  * (frequency, template) item of every curve of the chunk, and the chunk's
  * ill-conditioned frequencies are re-solved from direct FP64 sums in one more
