@@ -71,3 +71,27 @@ def test_build_compiles_every_translation_unit():
     from paper_2101_12348_gb300 import build as b
     cus = sorted(f for f in os.listdir(b.CSRC) if f.endswith(".cu"))
     assert sorted(b.SOURCES) == cus
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """The binding has no CPU fallback: loading a library that is not there
+    raises instead of returning something that computes elsewhere."""
+    with pytest.raises(FileNotFoundError, match="no CPU fallback"):
+        ftp.load(str(tmp_path / "libftp_gb300.so"))
+
+
+def test_product_path_never_touches_the_oracle():
+    """Neither the CUDA sources nor the Python binding import, include or
+    name the oracle package: the oracle is test infrastructure only."""
+    pkg = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2101_12348_gb300")
+    pattern = re.compile(r"(^\s*(import|from)\s+oracle\b)|(#include\s*[<\"][^>\"]*oracle)|"
+                         r"(import_module\(\s*[\"']oracle)", re.M)
+    checked = 0
+    for root, _, files in os.walk(pkg):
+        if "_build" in root or "__pycache__" in root:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                checked += 1
+                assert not pattern.search(open(os.path.join(root, f)).read()), f
+    assert checked >= 10
