@@ -57,3 +57,63 @@ def check_orthogonal_grid(case, res, tol_p, tol_amp, tol_phase):
         target = 0.0 if th1 > 0 else np.pi
         rel = h * res["theta2"][q] + case["psi"][h - 1] + case["phi0"] - target
         assert abs(np.angle(np.exp(1j * rel))) <= h * tol_phase, (e["k"], res["theta2"][q])
+
+
+def shared_orthogonal_case():
+    """tests/golden/shared_phase_orthogonal.json: two bands, each sampled
+    uniformly over whole cycles, with the closed-form power, amplitude, offset
+    and phase of the shared-phase fit at every trial frequency (derivation in
+    the file)."""
+    import json
+    import math
+
+    import numpy as np
+
+    with open(os.path.join(GOLDEN, "shared_phase_orthogonal.json")) as fh:
+        g = json.load(fh)
+    T, ks, d = g["T"], g["k_sig"], g["d"]
+    bands, lam, share = [], [], []
+    for b in g["bands"]:
+        t = b["t_start"] + np.arange(b["N"]) * T / b["N"]
+        y = b["a"] * np.cos(2.0 * np.pi * ks * t / T + b["phi"]) + b["lambda"] + d
+        bands.append((t, y, np.full(b["N"], b["dy"]), np.array(b["c"]), np.array(b["s"])))
+        lam.append(b["lambda"])
+        share.append(b["N"] / b["dy"] ** 2)
+    W = np.array(share) / np.sum(share)
+    YY = sum(W[i] * b["a"] ** 2 / 2 for i, b in enumerate(g["bands"]))
+    MM = sum(W[i] * np.sum(np.array(b["c"]) ** 2 + np.array(b["s"]) ** 2) / 2
+             for i, b in enumerate(g["bands"]))
+    ks_grid = g["grid"]["k0"] + np.arange(g["grid"]["nf"])
+    expect = []
+    for k in ks_grid:
+        h = ks // k if ks % k == 0 else 0
+        Z = 0j
+        matched = False
+        for i, b in enumerate(g["bands"]):
+            if 1 <= h <= len(b["c"]):
+                matched = True
+                A = math.hypot(b["c"][h - 1], b["s"][h - 1])
+                psi = math.atan2(b["s"][h - 1], b["c"][h - 1])
+                Z += W[i] * b["a"] * A * np.exp(1j * (psi + b["phi"])) / 2
+        h = h if matched else 0
+        expect.append(dict(h=h, P=abs(Z) ** 2 / (YY * MM), abs_theta1=abs(Z) / MM,
+                           theta3=d, argZ=np.angle(Z)))
+    return bands, np.array(lam), ks_grid / T, expect
+
+
+def check_shared_orthogonal(expect, res, tol_p, tol_amp, tol_phase):
+    """Compare shared-phase outputs with the closed form of
+    shared_orthogonal_case: P everywhere; |theta1|, theta3 and
+    h theta2 + arg Z = 0 (theta1 > 0) or pi (theta1 < 0), mod 2 pi, where a
+    harmonic matches."""
+    import numpy as np
+
+    for q, e in enumerate(expect):
+        assert abs(res["power"][q] - e["P"]) <= tol_p, (q, res["power"][q], e["P"])
+        if e["h"] == 0:
+            continue
+        th1 = res["theta1"][q]
+        assert abs(abs(th1) - e["abs_theta1"]) <= tol_amp, (q, th1)
+        assert abs(res["theta3"][q] - e["theta3"]) <= tol_amp, (q, res["theta3"][q])
+        rel = e["h"] * res["theta2"][q] + e["argZ"] - (0.0 if th1 > 0 else np.pi)
+        assert abs(np.angle(np.exp(1j * rel))) <= e["h"] * tol_phase, (q, res["theta2"][q])

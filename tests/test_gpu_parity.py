@@ -416,6 +416,25 @@ def test_multiband_periodogram(ftp, prec):
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_golden_shared_phase_orthogonal(ftp, prec):
+    """ftp_shared_multiband on the hand-derived two-band closed form of
+    tests/golden/shared_phase_orthogonal.json (Appendix A): P = |Z|^2/(YY MM)
+    where a harmonic matches, 0 elsewhere, with |theta1|, theta3 and phase."""
+    from conftest import check_shared_orthogonal, shared_orthogonal_case
+
+    bands, lam, freqs, expect = shared_orthogonal_case()
+    off = np.cumsum([0] + [b[0].size for b in bands]).astype(np.int64)
+    t, y, dy = (np.concatenate([b[i] for b in bands]) for i in range(3))
+    bank = [(b[3], b[4]) for b in bands]
+    nf = freqs.size
+    with ftp.Plan(int(np.max(np.diff(off))), 3, (freqs[0], 1, nf), 2, prec) as plan:
+        out = [np.empty(nf) for _ in range(4)]
+        ftp.ftp_shared_multiband(plan.h, off, t, y, dy, lam, bank, np.arange(2), *out)
+    r = dict(zip(("power", "theta1", "theta2", "theta3"), out))
+    check_shared_orthogonal(expect, r, TOL_P[prec], TOL_AMP[prec], TOL_PHASE[prec])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_shared_phase_multiband(ftp, prec):
     """ftp_shared_multiband: three bands with their own templates (H = 2, 3, 3)
     and fixed offsets sharing one amplitude, phase and offset, every frequency

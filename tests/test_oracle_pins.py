@@ -604,61 +604,15 @@ def test_shared_phase_single_band_and_noiseless_recovery():
     assert abs(np.angle(np.exp(1j * (r["theta2"][0] - 0.8)))) < 1e-8
 
 
-def shared_orthogonal_case():
-    """tests/golden/shared_phase_orthogonal.json: two bands, each sampled
-    uniformly over whole cycles, with the closed-form power, amplitude, offset
-    and phase of the shared-phase fit at every trial frequency (derivation in
-    the file)."""
-    import json
-    import os
-
-    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
-                                    "shared_phase_orthogonal.json")))
-    T, ks, d = g["T"], g["k_sig"], g["d"]
-    bands, lam, share = [], [], []
-    for b in g["bands"]:
-        t = b["t_start"] + np.arange(b["N"]) * T / b["N"]
-        y = b["a"] * np.cos(TWO_PI * ks * t / T + b["phi"]) + b["lambda"] + d
-        bands.append((t, y, np.full(b["N"], b["dy"]), np.array(b["c"]), np.array(b["s"])))
-        lam.append(b["lambda"])
-        share.append(b["N"] / b["dy"] ** 2)
-    W = np.array(share) / np.sum(share)
-    YY = sum(W[i] * b["a"] ** 2 / 2 for i, b in enumerate(g["bands"]))
-    MM = sum(W[i] * np.sum(np.array(b["c"]) ** 2 + np.array(b["s"]) ** 2) / 2
-             for i, b in enumerate(g["bands"]))
-    ks_grid = g["grid"]["k0"] + np.arange(g["grid"]["nf"])
-    expect = []
-    for k in ks_grid:
-        h = ks // k if ks % k == 0 else 0
-        Z = 0j
-        matched = False
-        for i, b in enumerate(g["bands"]):
-            if 1 <= h <= len(b["c"]):
-                matched = True
-                A = math.hypot(b["c"][h - 1], b["s"][h - 1])
-                psi = math.atan2(b["s"][h - 1], b["c"][h - 1])
-                Z += W[i] * b["a"] * A * np.exp(1j * (psi + b["phi"])) / 2
-        h = h if matched else 0
-        expect.append(dict(h=h, P=abs(Z) ** 2 / (YY * MM), abs_theta1=abs(Z) / MM,
-                           theta3=d, argZ=np.angle(Z)))
-    return bands, np.array(lam), ks_grid / T, expect
-
-
 def test_golden_shared_phase_orthogonal_closed_form():
     """Appendix A's pooled fit on two orthogonal bands with different
     templates, weights and phases equals the hand-derived closed form: the
     band shares W_b, the pooled mean and the phase sum all enter P."""
+    from conftest import check_shared_orthogonal, shared_orthogonal_case
+
     bands, lam, freqs, expect = shared_orthogonal_case()
     r = oracle.shared_phase_multiband(bands, freqs, lam)
-    for q, e in enumerate(expect):
-        assert abs(r["power"][q] - e["P"]) <= 1e-12, (q, r["power"][q], e["P"])
-        if e["h"] == 0:
-            continue
-        th1 = r["theta1"][q]
-        assert abs(abs(th1) - e["abs_theta1"]) <= 1e-10
-        assert abs(r["theta3"][q] - e["theta3"]) <= 1e-10
-        rel = e["h"] * r["theta2"][q] + e["argZ"] - (0.0 if th1 > 0 else math.pi)
-        assert abs(np.angle(np.exp(1j * rel))) <= 1e-9
+    check_shared_orthogonal(expect, r, tol_p=1e-12, tol_amp=1e-10, tol_phase=1e-9)
     assert any(e["h"] and e["P"] > 0.1 for e in expect)
 
 
@@ -666,6 +620,8 @@ def test_planted_mistake_unweighted_pooling_is_caught(monkeypatch):
     """With the sigma^-2 weights dropped in the oracle (every observation
     weighted 1/N), the band shares become N_b / N instead of W_b and the
     pooled fit misses the closed form."""
+    from conftest import shared_orthogonal_case
+
     bands, lam, freqs, expect = shared_orthogonal_case()
     mod = oracle.ftp_oracle
     monkeypatch.setattr(mod, "normalized_weights", lambda dy: np.full(len(dy), 1.0 / len(dy)))
