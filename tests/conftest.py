@@ -117,3 +117,27 @@ def check_shared_orthogonal(expect, res, tol_p, tol_amp, tol_phase):
         assert abs(res["theta3"][q] - e["theta3"]) <= tol_amp, (q, res["theta3"][q])
         rel = e["h"] * res["theta2"][q] + e["argZ"] - (0.0 if th1 > 0 else np.pi)
         assert abs(np.angle(np.exp(1j * rel))) <= e["h"] * tol_phase, (q, res["theta2"][q])
+
+
+def multiphase_orthogonal_expect():
+    """The multi-phase reading of the same two bands (derivation_multiphase
+    in shared_phase_orthogonal.json): per-band closed-form powers P_b [K][nf]
+    and the chi2_0-weighted combination P [nf]."""
+    import json
+    import math
+
+    import numpy as np
+
+    with open(os.path.join(GOLDEN, "shared_phase_orthogonal.json")) as fh:
+        g = json.load(fh)
+    ks = g["k_sig"]
+    ks_grid = g["grid"]["k0"] + np.arange(g["grid"]["nf"])
+    Pb = np.zeros((len(g["bands"]), ks_grid.size))
+    chi0 = np.array([b["N"] / b["dy"] ** 2 * b["a"] ** 2 / 2 for b in g["bands"]])
+    for i, b in enumerate(g["bands"]):
+        A2 = np.array(b["c"]) ** 2 + np.array(b["s"]) ** 2
+        for q, k in enumerate(ks_grid):
+            h = ks // k if ks % k == 0 else 0
+            if 1 <= h <= len(b["c"]):
+                Pb[i, q] = A2[h - 1] / A2.sum()
+    return Pb, (chi0[:, None] * Pb).sum(axis=0) / chi0.sum()

@@ -435,6 +435,27 @@ def test_golden_shared_phase_orthogonal(ftp, prec):
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_golden_multiphase_orthogonal(ftp, prec):
+    """ftp_multiband_periodogram on the same two orthogonal bands: per-band
+    powers and the chi2_0-weighted combination (Eq. multibandmultiphase)
+    equal the closed form."""
+    from conftest import multiphase_orthogonal_expect, shared_orthogonal_case
+
+    bands, _, freqs, _ = shared_orthogonal_case()
+    Pb, P = multiphase_orthogonal_expect()
+    off = np.cumsum([0] + [b[0].size for b in bands]).astype(np.int64)
+    t, y, dy = (np.concatenate([b[i] for b in bands]) for i in range(3))
+    bank = [(b[3], b[4]) for b in bands]
+    nf = freqs.size
+    with ftp.Plan(int(np.max(np.diff(off))), 3, (freqs[0], 1, nf), 2, prec) as plan:
+        p = np.empty(nf)
+        bp = np.empty((2, nf))
+        ftp.ftp_multiband_periodogram(plan.h, off, t, y, dy, bank, np.arange(2), p, bp)
+    assert np.max(np.abs(bp - Pb)) <= TOL_P[prec]
+    assert np.max(np.abs(p - P)) <= TOL_P[prec]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_shared_phase_multiband(ftp, prec):
     """ftp_shared_multiband: three bands with their own templates (H = 2, 3, 3)
     and fixed offsets sharing one amplitude, phase and offset, every frequency

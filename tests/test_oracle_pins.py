@@ -616,6 +616,19 @@ def test_golden_shared_phase_orthogonal_closed_form():
     assert any(e["h"] and e["P"] > 0.1 for e in expect)
 
 
+def test_golden_multiphase_orthogonal_closed_form():
+    """Eq. multibandmultiphase on the same two orthogonal bands: per-band
+    powers and their chi2_0-weighted combination equal the closed form."""
+    from conftest import multiphase_orthogonal_expect, shared_orthogonal_case
+
+    bands, _, freqs, _ = shared_orthogonal_case()
+    Pb, P = multiphase_orthogonal_expect()
+    r = oracle.multiband_periodogram(bands, freqs)
+    np.testing.assert_allclose(r["band_power"], Pb, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["power"], P, rtol=0, atol=1e-12)
+    assert np.max(P) > 0.5
+
+
 def test_planted_mistake_unweighted_pooling_is_caught(monkeypatch):
     """With the sigma^-2 weights dropped in the oracle (every observation
     weighted 1/N), the band shares become N_b / N instead of W_b and the
