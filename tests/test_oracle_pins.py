@@ -136,10 +136,12 @@ def test_single_harmonic_template_is_ls_at_harmonic(h):
     np.testing.assert_allclose(r["power"], ref, rtol=0, atol=1e-10)
 
 
-@pytest.mark.parametrize("seed,H", [(0, 2), (1, 3), (2, 4), (3, 3)])
+@pytest.mark.parametrize("seed,H", [(0, 2), (1, 3), (2, 4), (3, 3), (4, 8), (5, 16)])
 def test_brute_force_phase_scan(seed, H):
     """Dense theta2 scan + Brent with residual-based chi^2: the oracle's best
-    power is never below brute force and agrees to 1e-10."""
+    power is never below brute force and agrees to 1e-10, up to H = 16
+    (a final polynomial of degree 94, where the companion-matrix roots are
+    most exposed to rounding)."""
     lc, tpl = small_case(seed, H=H, signal=0.25 if seed % 2 else 0.0)
     rng = np.random.default_rng(100 + seed)
     for f in rng.uniform(0.1, 2.0, 3):
