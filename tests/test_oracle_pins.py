@@ -365,6 +365,51 @@ def test_planted_mistakes_fail_a_pin(monkeypatch, mutant):
     assert caught
 
 
+def test_tie_rule_on_constructed_candidates():
+    """The tie rule as a plain definition: among candidates within
+    rel_tie * Pmax of the best, theta1 > 0 first, then the smallest theta2;
+    outside the tolerance the larger P wins whatever its sign."""
+    cb = oracle.choose_best
+    assert cb(np.array([0.5, 0.5, 0.4]), np.array([-1.0, 1.0, 1.0]), np.array([0.1, 2.0, 0.0])) == 1
+    assert cb(np.array([0.5, 0.5]), np.array([1.0, 1.0]), np.array([3.0, 1.0])) == 1
+    assert cb(np.array([0.5, 0.5 - 1e-13]), np.array([-1.0, 1.0]), np.array([0.0, 1.0])) == 1
+    assert cb(np.array([0.5, 0.5 - 1e-9]), np.array([-1.0, 1.0]), np.array([0.0, 1.0])) == 0
+    assert cb(np.array([0.5, 0.5]), np.array([-1.0, -2.0]), np.array([2.0, 1.0])) == 1
+
+
+def test_tie_rule_on_natural_ties(orthogonal_grid):
+    """Ties the model itself creates.  An odd template (H = 1) satisfies
+    M(x - pi) = -M(x), so every optimum has a twin at theta2 + pi with the
+    opposite amplitude: the oracle reports the one with theta1 > 0.  On the
+    orthogonal grid, a match through harmonic h has h optima with theta1 > 0
+    (theta2 spaced by 2 pi / h): the smallest is reported, theta2 < 2 pi / h."""
+    rng = np.random.default_rng(31)
+    lc = synth.random_curve(rng, 60, T=12.0)
+    r = oracle.periodogram(lc.t, lc.y, lc.dy, rng.uniform(0.1, 2.0, 12), [0.8], [-0.5])
+    assert np.all(r["theta1"][r["power"] > 1e-9] > 0)
+    assert np.all((r["theta2"] >= 0) & (r["theta2"] < TWO_PI))
+    cs = orthogonal_grid
+    g = oracle.periodogram(cs["t"], cs["y"], cs["dy"], cs["freqs"], cs["c"], cs["s"])
+    for e in cs["g"]["expected"]:
+        if e["h"] is None:
+            continue
+        q = e["k"] - cs["k0"]
+        assert g["theta1"][q] > 0
+        assert g["theta2"][q] < TWO_PI / e["h"] + 1e-9
+
+
+def test_planted_mistake_plain_argmax_is_caught(monkeypatch):
+    """With the tie rule replaced by a plain argmax in the oracle, the odd
+    template's twin optima come out with negative amplitudes at some
+    frequencies, which the natural-tie pin rejects."""
+    mod = oracle.ftp_oracle
+    monkeypatch.setattr(mod, "choose_best", lambda P, th1, th2, rel_tie=1e-12: int(np.argmax(P)))
+    rng = np.random.default_rng(31)
+    lc = synth.random_curve(rng, 60, T=12.0)
+    r = mod.periodogram(lc.t, lc.y, lc.dy, rng.uniform(0.1, 2.0, 12), [0.8], [-0.5])
+    assert np.any(r["theta1"][r["power"] > 1e-9] < 0)
+
+
 def test_planted_mistake_conjugated_alpha_is_caught_by_the_golden_case(monkeypatch,
                                                                       orthogonal_grid):
     """The closed-form golden case fails when the oracle builds its
