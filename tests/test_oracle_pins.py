@@ -398,6 +398,33 @@ def test_tie_rule_on_natural_ties(orthogonal_grid):
         assert g["theta2"][q] < TWO_PI / e["h"] + 1e-9
 
 
+def test_candidate_margin_on_the_orthogonal_grid(orthogonal_grid):
+    """best_candidate_margin (which decides where the parity tests compare
+    phases) on the closed-form case.  Through harmonic 2 a second optimum
+    with theta1 > 0 sits pi away (a unit-circle root, so an exact candidate):
+    the margin is 0 and the phase is not compared.  Through harmonic 1,
+    P(theta2) = (2/3) cos^2(theta2 - theta*) in closed form, the opposite-
+    amplitude twin does not count, and the margin is 2/3 minus the closed-form
+    P of the best remaining candidate more than 0.05 rad away."""
+    cs = orthogonal_grid
+    g = oracle.periodogram(cs["t"], cs["y"], cs["dy"], cs["freqs"], cs["c"], cs["s"])
+    q = 3 - cs["k0"]
+    m = oracle.best_candidate_margin(cs["t"], cs["y"], cs["dy"], cs["freqs"][q], cs["c"],
+                                     cs["s"], g["theta2"][q])
+    assert abs(m) <= 1e-10
+    q = 6 - cs["k0"]
+    best = g["theta2"][q]
+    pol = oracle.polynomials_at(cs["t"], cs["y"], cs["dy"], cs["freqs"][q], cs["c"], cs["s"])
+    th = oracle.candidate_phases(pol["F"])
+    d = np.abs(np.angle(np.exp(1j * (th - best))))
+    twin = np.abs(d - math.pi) <= 1e-6
+    far = th[(d > 0.05) & ~twin]
+    want = 2.0 / 3.0 - np.max(2.0 / 3.0 * np.cos(far - best) ** 2)
+    m = oracle.best_candidate_margin(cs["t"], cs["y"], cs["dy"], cs["freqs"][q], cs["c"],
+                                     cs["s"], best)
+    assert abs(m - want) <= 1e-10, (m, want)
+
+
 def test_planted_mistake_plain_argmax_is_caught(monkeypatch):
     """With the tie rule replaced by a plain argmax in the oracle, the odd
     template's twin optima come out with negative amplitudes at some
