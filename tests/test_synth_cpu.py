@@ -57,3 +57,12 @@ def test_survey_recipe():
         assert 100 <= T <= 3000 and lc.t.max() <= T and g.k0 == 1
         assert g.nf == int(np.floor(10.0 / g.df))
         assert np.all((lc.dy >= 0.05) & (lc.dy <= 0.15))
+
+
+def test_bank_curve_recipe():
+    lc, bank, grid = synth.bank_curve()
+    assert lc.t.size == 100_000 and len(bank) == 32 and all(tp.H == 10 for tp in bank)
+    np.testing.assert_array_equal(bank[5].c, synth.make_template(10, 2005).c)
+    assert np.all(np.diff(lc.t) >= 0) and lc.t.max() < 4000
+    assert np.all(lc.t - np.floor(lc.t) <= 8 / 24 + 1e-12)
+    assert (grid.k0, grid.nf) == (1, 1_000_000) and abs(grid.df - 1 / 20000) < 1e-18
