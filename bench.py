@@ -232,6 +232,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def solver_report(stats, mean_iterations=None):
+    """Root-solver counts of the last call: items that hit the Aberth cap in
+    the main pass (before) and after their re-solve with FP64 iterations, and
+    the frequencies re-solved from direct FP64 sums."""
+    it = stats["mean_iterations"] if mean_iterations is None else mean_iterations
+    return {"mean_iterations": round(it, 3),
+            "nonconverged_before_resolve": stats["nonconverged"],
+            "nonconverged_after_resolve": stats["still_nonconverged"],
+            "resolved_frequencies": stats["resolved"],
+            "resolved_for_nonconvergence": stats["resolved_nonconverged"]}
+
+
 def ncu_traffic_per_item():
     """DRAM bytes per (frequency, template) item of the roots kernel, from the
     committed ncu summary (None if absent)."""
@@ -361,8 +373,7 @@ def run_ours(args, world, rank, local, pg):
         "fp64_path": fp64_path,
         "stage_ms": {"roots": round(statistics.mean(roots_ms), 4),
                      "roots_phase1": round(statistics.mean(first_ms), 4)},
-        "solver": {"mean_iterations": round(ibar, 3), "nonconverged": stats_m["nonconverged"],
-                   "resolved_in_fp64": stats_m["resolved"]},
+        "solver": solver_report(stats_m, ibar),
         "roofline": roofline,
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -536,9 +547,7 @@ def run_survey(args, world, rank, local, pg):
                      stage_ms={"sums": round(st[0], 3), "roots": round(st[4], 3),
                                "resolve": round(st[5], 3)},
                      first_call_s=round(first_s, 3), autotune=tuning,
-                     solver={"mean_iterations": round(ibar, 3),
-                             "nonconverged": stats["nonconverged"],
-                             "resolved_in_fp64": stats["resolved"]},
+                     solver=solver_report(stats, ibar),
                      roofline=roofline, e2e=e2e, clocks=clocks,
                      gpu_launches=args.steps * launches)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -659,9 +668,7 @@ def run_bank(args, world, rank, local, pg):
                      stage_ms={"sums": round(statistics.mean(sums), 3),
                                "roots": round(statistics.mean(roots), 3),
                                "roots_phase1": round(statistics.mean(first), 3)},
-                     solver={"mean_iterations": round(ibar, 3),
-                             "nonconverged": stats["nonconverged"],
-                             "resolved_in_fp64": stats["resolved"]},
+                     solver=solver_report(stats, ibar),
                      roofline=roofline, e2e=e2e, clocks=clocks,
                      gpu_launches=args.steps * launches)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

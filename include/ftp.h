@@ -79,16 +79,23 @@ typedef enum {
 } ftp_precision;
 
 /* Per-frequency flag bits (uint8). */
-#define FTP_FLAG_NONCONVERGED 1u  /* root solver hit its iteration cap */
+#define FTP_FLAG_NONCONVERGED 1u  /* the root solver hit its iteration cap with a root
+                                     that is not a zero of the final polynomial to the
+                                     working precision, and no re-solve cleared it */
 #define FTP_FLAG_DEGENERATE_MM 2u /* MM ~ 0 at the chosen phase: P set to 0 */
 #define FTP_FLAG_CONSTANT_P 4u    /* final polynomial ~ 0: P independent of theta2 */
 #define FTP_FLAG_NEGATIVE_AMP 8u  /* best theta1 < 0 (Section 2.1: allowed, reported) */
-#define FTP_FLAG_UNRESOLVED 16u   /* ill-conditioned but not re-solved: the batch's
-                                     re-solve list was full (ftp_batch only) */
+#define FTP_FLAG_UNRESOLVED 16u   /* ill-conditioned (or at the iteration cap) but not
+                                     re-solved: the batch's re-solve list was full, or
+                                     the call cannot re-solve
+                                     (ftp_periodogram_sums_noalloc) */
 #define FTP_FLAG_SCREENED_OUT 32u /* not evaluated: screened out by the surrogate
                                      (ftp_batch_screened); P and theta are NaN */
 #define FTP_FLAG_NO_POSITIVE 64u  /* positive-amplitude mode: no candidate with
                                      theta1 > 0, so P = 0 (ftp_set_positive_amplitude) */
+#define FTP_FLAG_RESOLVED 128u    /* result of a re-solve from direct FP64 sums: the
+                                     frequency was ill-conditioned, or an item of it hit
+                                     the Aberth cap (then re-solved with FP64 iterations) */
 
 #define FTP_MAX_H 16
 
@@ -292,17 +299,54 @@ ftp_status ftp_plan_info(ftp_plan_t plan, int64_t* grid_len, int* half_width, in
                          int* last_launches);
 
 /*
- * ftp_solver_stats - root-solver statistics of the last call: the number of
- * (frequency, template) items solved, the mean number of Aberth iterations
- * per item (iterations of the warp that solved it), how many items hit the
- * iteration cap (FTP_FLAG_NONCONVERGED), and how many frequencies were
- * re-solved from direct FP64 sums because the a-posteriori estimate of the
- * error of P caused by the NFFT sums exceeded 1e-5 (FTP_MIXED) or 1e-10
- * (FTP_FP64) - frequencies where clustered phases make MM = Var(M) a small
- * difference of O(1) sums.  Each pointer is nullable.
+ * ftp_solver_stats - root-solver statistics of the last call:
+ *   items          (frequency, template) items solved by the main pass;
+ *   mean_iterations mean Aberth iterations per item (iterations of the warp
+ *                  that solved it);
+ *   nonconverged   items whose main-pass iteration hit the cap with a root
+ *                  that is not a zero of the final polynomial to the working
+ *                  precision (|F(z)| above 8 D eps sum_k |F_k| |z|^k);
+ *   resolved       frequencies re-solved from direct FP64 sums: those where
+ *                  the a-posteriori estimate of the error of P caused by the
+ *                  NFFT sums exceeded 1e-5 (FTP_MIXED) or 1e-10 (FTP_FP64) -
+ *                  clustered phases make MM = Var(M) a small difference of
+ *                  O(1) sums - and those with a non-converged item;
+ *   resolved_nonconverged  the latter kind among them (re-solved with FP64
+ *                  Aberth iterations and the cap of ftp_set_solver_limits);
+ *   still_nonconverged  items left at the cap after their re-solve, or not
+ *                  re-solved at all (these keep FTP_FLAG_NONCONVERGED).
+ * Section 2 takes every stationary point as a candidate, so an item whose
+ * roots did not all converge is re-solved rather than only reported.  Each
+ * pointer is nullable.
  */
 ftp_status ftp_solver_stats(ftp_plan_t plan, int64_t* items, double* mean_iterations,
-                            int64_t* nonconverged, int64_t* resolved);
+                            int64_t* nonconverged, int64_t* resolved,
+                            int64_t* resolved_nonconverged, int64_t* still_nonconverged);
+
+/*
+ * ftp_set_solver_limits - iteration caps and wait bounds of the root stage
+ * for later calls of the plan (0 restores a default):
+ *   maxit        Aberth iteration cap of the main pass (default 60 on
+ *                FTP_MIXED, 80 on FTP_FP64; 1..100000);
+ *   redo_maxit   cap of the FP64 re-solve of items that hit maxit (default
+ *                200; 1..100000);
+ *   wait_polls   polls of each bounded wait of the roots kernels for their
+ *                staged sum tiles before they give up and the call returns
+ *                FTP_ERR_TIMEOUT (default 2^20; >= 1).
+ * Errors: FTP_ERR_INVALID_ARG for a null plan or a value out of range.
+ */
+ftp_status ftp_set_solver_limits(ftp_plan_t plan, int maxit, int redo_maxit, int wait_polls);
+
+/*
+ * ftp_set_fault_injection - for tests of the failure path, without any GPU
+ * fault.  mode 1: the roots kernels arm their waits for the staged sum tiles
+ * but never issue the copies, so every wait runs out after the plan's
+ * wait_polls polls, the kernels return early and the call returns
+ * FTP_ERR_TIMEOUT; no copy is in flight when a kernel gives up.  mode 0
+ * (default) turns it off, and the next call runs normally.  Errors:
+ * FTP_ERR_INVALID_ARG for a null plan or another mode.
+ */
+ftp_status ftp_set_fault_injection(ftp_plan_t plan, int mode);
 
 /*
  * ftp_stage_times - per-stage device times (milliseconds) of the last
@@ -364,8 +408,14 @@ ftp_status ftp_roots_first_phase_ms(ftp_plan_t plan, float* ms);
  * on the GPU race on it.  Requests beyond the array (more than
  * FTP_NOALLOC_MAX_TEMPLATES templates) return FTP_ERR_UNSUPPORTED before any
  * device work; bad sizes, strides, alignment or host pointers return
- * FTP_ERR_INVALID_ARG.  Unlike ftp_periodogram it cannot re-solve
- * ill-conditioned frequencies from the observations, which it does not see.
+ * FTP_ERR_INVALID_ARG, and so do pointers to another GPU's memory.
+ * Unlike ftp_periodogram it cannot re-solve anything from the observations,
+ * which it does not see: items whose estimated error of P from the sums
+ * exceeds 1e-5 (FTP_MIXED) or 1e-10 (FTP_FP64) get FTP_FLAG_UNRESOLVED, and
+ * items that hit the Aberth iteration cap keep FTP_FLAG_NONCONVERGED.  The
+ * flags array is the only per-item report of either.  Each call copies its
+ * small parameter tables from host memory into the scratch array and waits
+ * for the stream before it returns.
  */
 #define FTP_NOALLOC_MAX_TEMPLATES 64
 #define FTP_NOALLOC_SCRATCH_BYTES (512 + FTP_NOALLOC_MAX_TEMPLATES * FTP_MAX_H * 16)

@@ -84,6 +84,9 @@ struct SumLane {
 };
 constexpr int kSumLanes = 4;     // default concurrent step (a) lanes of ftp_batch
 constexpr int kMaxSumLanes = 8;
+// Default iteration cap of the FP64 re-solve of items whose main-pass Aberth
+// iteration hit its cap (60 FP32 / 80 FP64 iterations).
+constexpr int kRedoMaxit = 200;
 
 }  // namespace
 
@@ -155,6 +158,12 @@ struct ftp_plan_s {
   float first_phase_ms = 0.f;
   int maxit = 60;
   int polish_steps = 1;
+  // iteration cap of the FP64 re-solve of items that hit `maxit`, polls of
+  // the roots kernels' bounded waits (0: default), fault injection (1: the
+  // roots kernels never copy a sum row, so their waits run out)
+  int redo_maxit = kRedoMaxit;
+  int wait_polls = 0;
+  int inject = 0;
   // ---- batch workspace (grown on demand by ftp_batch; never shrinks)
   bool in_batch = false;
   size_t chunk_bytes = (size_t)8 << 30;  // sum tiles of one chunk of curves
@@ -476,10 +485,13 @@ ftp_status finish(ftp_plan_t P) {
                          cudaMemcpyDeviceToHost, P->stream));
   FTP_CK(cudaStreamSynchronize(P->stream));
 #ifdef FTP_DEVICE_CHECKS
-  if (P->h_status[ST_DBG_N] != 0)
+  if (P->h_status[ST_DBG_N] != 0) {
     fprintf(stderr, "ftp device check failed: site %d value %d bound %d (%d failures)\n",
             P->h_status[ST_DBG_SITE], P->h_status[ST_DBG_A], P->h_status[ST_DBG_B],
             P->h_status[ST_DBG_N]);
+    // a skipped access means the outputs cannot be trusted
+    if (P->h_status[ST_CODE] == DEV_OK) return FTP_ERR_CUDA;
+  }
 #endif
   if (P->timing) {
     for (int i = 0; i < 6; ++i) P->stage_ms[i] = 0.f;
@@ -543,10 +555,30 @@ ftp_status upload_templates(ftp_plan_t P, const ftp_template* tpl, int ntpl,
   return FTP_OK;
 }
 
+// The plan's solver settings for one roots launch.
+void solver_settings(ftp_plan_t P, RootsArgs& a) {
+  a.maxit = P->maxit;
+  a.polish_steps = P->polish_steps;
+  a.ctas_per_sm = P->roots_ctas_per_sm;
+  a.positive_only = P->positive_only ? 1 : 0;
+  a.wait_polls = P->wait_polls > 0 ? P->wait_polls : kWaitPolls;
+  a.skip_copies = P->inject == 1 ? 1 : 0;
+}
+
+// A re-solve pass over listed frequencies: sel_mode 0 every one, 1 those
+// without MARK_FP64 (FP32 Aberth on the mixed path), 2 those with it.
+void resolve_settings(ftp_plan_t P, RootsArgs& a, const int* marks, int sel_mode) {
+  a.resolve_pass = 1;
+  a.sel_mark = sel_mode ? marks : nullptr;
+  a.sel_mode = sel_mode;
+  if (sel_mode != 1) a.maxit = P->redo_maxit;
+}
+
 ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int Hs, int64_t nf,
                      const int* nf_dev, const int* kmap, bool collect_redo, const double2* alpha,
                      const int* rows, int ntpl, double* const* o, uint8_t* flags,
-                     int64_t out_stride, int64_t out_elems, int* launches, bool time_first = false) {
+                     int64_t out_stride, int64_t out_elems, int* launches, bool time_first = false,
+                     int sel_mode = -1) {
   RootsArgs a{};
   if (time_first && P->timing && !P->in_batch && P->fev_used < kMaxH &&
       P->fev[2 * P->fev_used]) {
@@ -584,11 +616,10 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
     a.redo_marks = P->grid.nf;
     a.sum_err = P->mixed ? kSumErrF32 : kSumErrF64;
     a.redo_tol = P->mixed ? kRedoTolF32 : kRedoTolF64;
+    a.list_nonconv = 1;
   }
-  a.maxit = P->maxit;
-  a.polish_steps = P->polish_steps;
-  a.ctas_per_sm = P->roots_ctas_per_sm;
-  a.positive_only = P->positive_only ? 1 : 0;
+  solver_settings(P, a);
+  if (sel_mode >= 0) resolve_settings(P, a, P->d_redo_mark, sel_mode);
   FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), P->stream));
   const int r = launch_roots(kind, a, P->num_sms, P->stream);
   if (r == -1) return FTP_ERR_UNSUPPORTED;
@@ -603,7 +634,9 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
 // P from the NFFT sums exceeds the path's threshold (ill-conditioned ones,
 // where clustered phases make MM a small difference of O(1) sums) are then
 // recomputed from direct FP64 sums with the same kernel (FP32 Aberth on the
-// mixed path, FP64 Aberth on the FP64 path).
+// mixed path, FP64 Aberth on the FP64 path); frequencies where an item hit
+// the Aberth iteration cap are recomputed from direct FP64 sums with FP64
+// Aberth iterations and the larger cap redo_maxit.
 ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double* ddy,
                  int64_t nobs, double df, int64_t k0, int64_t nf, int Hs,
                  const std::vector<HGroup>& groups, const double2* alpha, const int* rows,
@@ -627,13 +660,19 @@ ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double
                      P->d_redo_count, (int)nf, Hs, P->nf_pad, P->d_redo_sums,
                      (int64_t)3 * P->max_H * P->nf_pad, P->d_status, P->stream);
   *launches += 1;
-  for (const HGroup& g : groups) {
-    ftp_status st = run_roots(P, P->mixed ? ROOTS_REDO : ROOTS_FP64, P->d_redo_sums, g.H, Hs, nf,
-                              P->d_redo_count,
-                              P->d_redo_list, false, alpha + (size_t)g.first * kMaxH,
-                              row0 ? row0 : rows + g.first, g.count, o, flags, nf, out_elems,
-                              launches);
-    if (st != FTP_OK) return st;
+  // mixed path: FP32 Aberth for the ill-conditioned frequencies, FP64
+  // Aberth for those with a cap hit; FP64 path: FP64 Aberth for all
+  const int passes = P->mixed ? 2 : 1;
+  for (int pass = 0; pass < passes; ++pass) {
+    const RootsKind rk = (P->mixed && pass == 0) ? ROOTS_REDO : ROOTS_FP64;
+    const int sel = P->mixed ? pass + 1 : 0;
+    for (const HGroup& g : groups) {
+      ftp_status st = run_roots(P, rk, P->d_redo_sums, g.H, Hs, nf, P->d_redo_count,
+                                P->d_redo_list, false, alpha + (size_t)g.first * kMaxH,
+                                row0 ? row0 : rows + g.first, g.count, o, flags, nf, out_elems,
+                                launches, false, sel);
+      if (st != FTP_OK) return st;
+    }
   }
   return FTP_OK;
 }
@@ -958,10 +997,8 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.redo_marks = ch.nf_total;
       a.sum_err = P->mixed ? kSumErrF32 : kSumErrF64;
       a.redo_tol = P->mixed ? kRedoTolF32 : kRedoTolF64;
-      a.maxit = P->maxit;
-      a.polish_steps = P->polish_steps;
-      a.ctas_per_sm = P->roots_ctas_per_sm;
-      a.positive_only = P->positive_only ? 1 : 0;
+      a.list_nonconv = 1;
+      solver_settings(P, a);
       a.segs = d_segs + L.seg_first;
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;
@@ -989,7 +1026,10 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
                              (int64_t)3 * P->max_H * kBatchRedoStride, P->d_bslot_curve,
                              P->d_status, s);
     *launches += 1;
+    const int passes = P->mixed ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass)
     for (const BLaunch& L : ch.launches) {
+      const RootsKind rk = (P->mixed && pass == 0) ? rkind : ROOTS_FP64;
       RootsArgs a{};
       a.sums = P->d_bredo_sums;
       a.sums_elems = (int64_t)3 * P->max_H * kBatchRedoStride;
@@ -1013,10 +1053,8 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.counters = P->d_counters;
       a.queue = P->d_queue;
       a.redo_cap = kBatchRedoCap;
-      a.maxit = P->maxit;
-      a.polish_steps = P->polish_steps;
-      a.ctas_per_sm = P->roots_ctas_per_sm;
-      a.positive_only = P->positive_only ? 1 : 0;
+      solver_settings(P, a);
+      resolve_settings(P, a, P->d_bmark, P->mixed ? pass + 1 : 0);
       a.segs = d_segs + L.seg_first;
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;
@@ -1025,7 +1063,7 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.ncurves = ncc;
       a.host_units = (int64_t)kBatchRedoCap * L.ntpl;
       FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), s));
-      const int r = launch_roots(rkind, a, P->num_sms, s);
+      const int r = launch_roots(rk, a, P->num_sms, s);
       if (r == -1) return FTP_ERR_UNSUPPORTED;
       if (r < 0) return FTP_ERR_CUDA;
       *launches += r;
@@ -1418,6 +1456,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     key = fnv(key, &P->sum_lanes, sizeof(P->sum_lanes));
     key = fnv(key, &P->roots_ctas_per_sm, sizeof(P->roots_ctas_per_sm));
     key = fnv(key, &P->positive_only, sizeof(P->positive_only));
+    const int solver[] = {P->maxit, P->redo_maxit, P->wait_polls, P->inject};
+    key = fnv(key, solver, sizeof(solver));
     if (scr) {
       const void* sp[] = {scr->feat_out, scr->mlp, scr->moments_out};
       key = fnv(key, sp, sizeof(sp));
@@ -1719,7 +1759,8 @@ ftp_status ftp_plan_info(ftp_plan_t P, int64_t* grid_len_out, int* half_width, i
 }
 
 ftp_status ftp_solver_stats(ftp_plan_t P, int64_t* items, double* mean_iterations,
-                            int64_t* nonconverged, int64_t* resolved) {
+                            int64_t* nonconverged, int64_t* resolved,
+                            int64_t* resolved_nonconverged, int64_t* still_nonconverged) {
   if (!P) return FTP_ERR_INVALID_ARG;
   const unsigned long long* c = P->h_counters;
   const unsigned long long n = c ? c[CNT_ITEMS] : 0;
@@ -1727,6 +1768,24 @@ ftp_status ftp_solver_stats(ftp_plan_t P, int64_t* items, double* mean_iteration
   if (mean_iterations) *mean_iterations = n ? (double)c[CNT_ITERS] / (double)n : 0.0;
   if (nonconverged) *nonconverged = n ? (int64_t)c[CNT_NONCONV] : 0;
   if (resolved) *resolved = n ? (int64_t)c[CNT_REDO] : 0;
+  if (resolved_nonconverged) *resolved_nonconverged = n ? (int64_t)c[CNT_REDO_NC] : 0;
+  if (still_nonconverged) *still_nonconverged = n ? (int64_t)c[CNT_NC_FINAL] : 0;
+  return FTP_OK;
+}
+
+ftp_status ftp_set_solver_limits(ftp_plan_t P, int maxit, int redo_maxit, int wait_polls) {
+  if (!P) return FTP_ERR_INVALID_ARG;
+  if (maxit < 0 || maxit > 100000 || redo_maxit < 0 || redo_maxit > 100000 || wait_polls < 0)
+    return FTP_ERR_INVALID_ARG;
+  P->maxit = maxit ? maxit : (P->mixed ? 60 : 80);
+  P->redo_maxit = redo_maxit ? redo_maxit : kRedoMaxit;
+  P->wait_polls = wait_polls;
+  return FTP_OK;
+}
+
+ftp_status ftp_set_fault_injection(ftp_plan_t P, int mode) {
+  if (!P || mode < 0 || mode > 1) return FTP_ERR_INVALID_ARG;
+  P->inject = mode;
   return FTP_OK;
 }
 
@@ -2048,10 +2107,7 @@ ftp_status ftp_shared_multiband(ftp_plan_t P, int nbands, const int64_t* obs_off
   a.status = P->d_status;
   a.counters = P->d_counters;
   a.queue = P->d_queue;
-  a.maxit = P->maxit;
-  a.polish_steps = P->polish_steps;
-  a.ctas_per_sm = P->roots_ctas_per_sm;
-  a.positive_only = P->positive_only ? 1 : 0;
+  solver_settings(P, a);
   a.coef_mode = 1;
   FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), s));
   const int r = launch_roots(P->mixed ? ROOTS_REDO : ROOTS_FP64, a, P->num_sms, s);

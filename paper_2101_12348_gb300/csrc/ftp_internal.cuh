@@ -33,7 +33,27 @@ enum : int { ST_CODE = 0, ST_DBG_SITE = 4, ST_DBG_A = 5, ST_DBG_B = 6, ST_DBG_N 
 #else
 #define FTP_DCHECK(status, cond, site, val, bound) true
 #endif
-enum : int { CNT_ITERS = 0, CNT_ITEMS = 1, CNT_NONCONV = 2, CNT_REDO = 3, CNT_WORDS = 4 };
+// Solver counters of a call: iterations and items of the main pass, items
+// that hit the Aberth cap there, frequencies put on the re-solve list (and
+// how many of them for an item that hit the cap), and items still at the cap
+// after a re-solve pass or in a call that cannot re-solve.
+enum : int {
+  CNT_ITERS = 0,
+  CNT_ITEMS = 1,
+  CNT_NONCONV = 2,
+  CNT_REDO = 3,
+  CNT_REDO_NC = 4,
+  CNT_NC_FINAL = 5,
+  CNT_WORDS = 6
+};
+
+// Re-solve marks (one int per frequency): listed, list full (the frequency
+// keeps its first result), and re-solve with FP64 Aberth iterations because
+// an item of the frequency hit the iteration cap.
+enum : int { MARK_LISTED = 1, MARK_OVERFLOW = 2, MARK_FP64 = 4 };
+
+// Default polls of a bounded mbarrier wait in the roots kernels.
+constexpr int kWaitPolls = 1 << 20;
 
 // Layout of the device moments block (doubles).
 enum : int { MO_YBAR = 0, MO_YY = 1, MO_WSUM = 2, MO_UNIT = 3, MO_WORDS = 4 };
@@ -212,6 +232,17 @@ struct RootsArgs {
   double redo_tol;         // re-solve threshold on the estimated error of P
   int maxit;
   int polish_steps;
+  int wait_polls;     // polls of each bounded mbarrier wait (>= 1; kWaitPolls by default)
+  int skip_copies;    // fault injection: no sum row is ever copied, so every wait runs out
+  // main pass: a frequency with an item that hit the iteration cap goes on
+  // the re-solve list with MARK_FP64 (needs redo_list)
+  int list_nonconv;
+  // re-solve pass: items get FTP_FLAG_RESOLVED and cap hits count as final;
+  // sel_mark / sel_mode restrict the pass to listed frequencies without
+  // (sel_mode 1) or with (sel_mode 2) MARK_FP64 (nullable: every one)
+  int resolve_pass;
+  const int* sel_mark;
+  int sel_mode;
   // batched launches (segs != nullptr): `moments` holds MO_WORDS doubles per
   // curve, outputs are addressed through the segments, and re-solve marks and
   // list entries are global frequency indices (redo_base + k).

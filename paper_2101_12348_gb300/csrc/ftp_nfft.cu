@@ -720,10 +720,33 @@ __global__ void __launch_bounds__(256) direct_sums_batch_kernel(
   }
 }
 
+// SM count of the current device, read once per device ordinal.
+int current_sms() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }
+  if (cache[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+// Grid-stride launches: enough CTAs for n / threads, at most 16 per SM.
 inline int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
-  if (b > 152 * 16) b = 152 * 16;
+  const int64_t cap = (int64_t)current_sms() * 16;
+  if (b > cap) b = cap;
   return (int)b;
 }
 
@@ -747,7 +770,8 @@ void launch_direct_sums(const double* t, const double* y, const double* dy, int6
                         const double* moments, const int* status, double df, int64_t k0,
                         const int* list, const int* count, int cap, int Hs, int64_t nf_pad,
                         double2* sums, int64_t sums_elems, int* status_rw, cudaStream_t s) {
-  int grid = cap < 2 * 152 ? cap : 2 * 152;
+  const int gmax = 2 * current_sms();
+  int grid = cap < gmax ? cap : gmax;
   if (grid < 1) grid = 1;
   direct_sums_kernel<<<grid, 256, 0, s>>>(t, y, dy, n, moments, status, df, k0, list, count, cap,
                                           Hs, nf_pad, sums, sums_elems, status_rw);
@@ -762,7 +786,7 @@ __global__ void __launch_bounds__(256) redo_overflow_kernel(const CurveDesc* __r
   if (*count <= cap) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nmarks; g += stride) {
-    if (marks[g] != 2) continue;
+    if ((marks[g] & MARK_OVERFLOW) == 0) continue;
     int lo = 0, hi = ncurves;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
@@ -778,14 +802,16 @@ __global__ void __launch_bounds__(256) redo_overflow_kernel(const CurveDesc* __r
 
 void launch_redo_overflow(const CurveDesc* curves, int ncurves, const int* marks, int64_t nmarks,
                           const int* count, int cap, uint8_t* flags, cudaStream_t s) {
-  redo_overflow_kernel<<<2 * 152, 256, 0, s>>>(curves, ncurves, marks, nmarks, count, cap, flags);
+  redo_overflow_kernel<<<2 * current_sms(), 256, 0, s>>>(curves, ncurves, marks, nmarks, count, cap,
+                                                         flags);
 }
 
 void launch_direct_sums_batch(const CurveDesc* curves, int ncurves, const double* moments,
                               const int* status, const int* list, const int* count, int cap,
                               int64_t stride, double2* sums, int64_t sums_elems, int* slot_curve,
                               int* status_rw, cudaStream_t s) {
-  int grid = cap < 2 * 152 ? cap : 2 * 152;
+  const int gmax = 2 * current_sms();
+  int grid = cap < gmax ? cap : gmax;
   if (grid < 1) grid = 1;
   direct_sums_batch_kernel<<<grid, 256, 0, s>>>(curves, ncurves, moments, status, list, count,
                                                 cap, stride, sums, sums_elems, slot_curve,
@@ -827,7 +853,8 @@ void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int
                    int64_t nf_pad, int Hs, int m, double beta, typename C2<R>::type* sums,
                    const int* status, cudaStream_t s) {
   const int64_t ntiles = ((int64_t)2 * Hs * (k0 + nf - 1) - k0) / GatherTile<R>::T + 1;
-  int64_t blocks = ntiles < 152 * 6 ? ntiles : 152 * 6;
+  const int64_t bmax = (int64_t)current_sms() * 6;
+  int64_t blocks = ntiles < bmax ? ntiles : bmax;
   if (blocks < 1) blocks = 1;
   gather_kernel<R><<<(unsigned)blocks, 256, 0, s>>>(X, ngrid, k0, nf, nf_pad, Hs, m, beta, sums,
                                                     status);

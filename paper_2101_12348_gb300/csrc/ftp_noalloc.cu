@@ -18,6 +18,12 @@
 // contents, so everything the kernel counts on is cleared or written at the
 // start of each call, and calls whose work overlaps on the GPU (other
 // streams, other host threads) race on it.
+//
+// It cannot re-solve anything (it never sees the observations): an item whose
+// Aberth iteration hit its cap keeps FTP_FLAG_NONCONVERGED, and an item whose
+// estimated error of P from the sums exceeds the path's threshold (clustered
+// phases) gets FTP_FLAG_UNRESOLVED.  The flags array is the only per-item
+// report of either, so pass one when such items matter.
 #include <math.h>
 #include <stdint.h>
 
@@ -41,6 +47,8 @@ constexpr size_t kScratchBytes =
     kOffAlpha + (size_t)FTP_NOALLOC_MAX_TEMPLATES * kMaxH * sizeof(double2);
 
 static_assert(kOffRows + FTP_NOALLOC_MAX_TEMPLATES * sizeof(int) <= kOffAlpha, "layout");
+static_assert(kOffCounters + CNT_WORDS * sizeof(unsigned long long) <= kOffQueue, "layout");
+static_assert(kOffStatus + ST_WORDS * sizeof(int) <= kOffCounters, "layout");
 static_assert(kScratchBytes == FTP_NOALLOC_SCRATCH_BYTES, "header states the scratch size");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -62,13 +70,17 @@ cudaError_t scratch_address(int dev, unsigned char** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// True for device memory of `device` and for managed memory; host memory,
+// unknown pointers and another GPU's memory (which the kernels could only
+// reach through peer mappings this call does not set up) are rejected.
+bool on_device(const void* p, int device) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
 }  // namespace
@@ -106,8 +118,9 @@ extern "C" ftp_status ftp_periodogram_sums_noalloc(
     int d;
     ~Restore() { cudaSetDevice(d); }
   } restore{prev};
-  if (!on_device(sums) || !on_device(power) || !on_device(theta1) || !on_device(theta2) ||
-      !on_device(theta3) || (flags && !on_device(flags)))
+  if (!on_device(sums, device) || !on_device(power, device) || !on_device(theta1, device) ||
+      !on_device(theta2, device) || !on_device(theta3, device) ||
+      (flags && !on_device(flags, device)))
     return FTP_ERR_INVALID_ARG;
 
   unsigned char* scratch = nullptr;
@@ -183,6 +196,11 @@ extern "C" ftp_status ftp_periodogram_sums_noalloc(
     a.queue = queue;
     a.maxit = (prec == FTP_MIXED) ? 60 : 80;
     a.polish_steps = 1;
+    a.wait_polls = kWaitPolls;
+    // the a-posteriori error estimate of P runs without a re-solve list:
+    // items above the threshold get FTP_FLAG_UNRESOLVED instead
+    a.sum_err = (prec == FTP_MIXED) ? kSumErrF32 : kSumErrF64;
+    a.redo_tol = (prec == FTP_MIXED) ? kRedoTolF32 : kRedoTolF64;
     FTP_NA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
     const int r = launch_roots(prec == FTP_MIXED ? ROOTS_MIXED : ROOTS_FP64, a, num_sms, s);
     if (r == -1) return FTP_ERR_UNSUPPORTED;

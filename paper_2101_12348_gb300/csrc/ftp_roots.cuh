@@ -211,10 +211,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after a fixed number of polls instead of spinning
-// forever if a copy never lands.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (int i = 0; i < (1 << 20); ++i)
+// Bounded wait: gives up after `polls` polls instead of spinning forever if
+// a copy never lands.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int polls) {
+  for (int i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -448,6 +448,35 @@ __device__ __forceinline__ void compact_roots(const bool (&conv)[NS], const int 
     c2[k] = i2[k] < 0;
   }
   __syncwarp();
+}
+
+// A root left unconverged at the iteration cap is accepted when F's value
+// there is at the rounding level of its evaluation: |F(z)| <= 8 D eps
+// sum_k |F_k| |z|^k (a backward error of a few units of the working
+// precision in the coefficients), so that no further digits are obtainable in
+// that precision - the case of clustered and multiple roots, whose Newton
+// corrections stall at about sqrt(eps) instead of meeting the tolerance.
+// Outside the unit disc F is evaluated at u = 1/conj(z): F is
+// anti-self-inversive, so |F(z)| = |z|^D |F(u)| and the sum of |F_k||z|^k
+// scales alike.  Out of line: it runs only for items that hit the cap, and
+// the hot loops keep their registers.
+template <int D, typename R, typename R2>
+__device__ __noinline__ bool pseudo_zero(R2 z, const R2* Fs) {
+  const R m2 = cabs2(z);
+  const R inv = m2 > R(1) ? R(1) / m2 : R(1);
+  const R2 u = mk<R2>(z.x * inv, z.y * inv);
+  const R au = sqrt(cabs2(u));
+  R2 p = mk<R2>(0, 0);
+  R pa = R(0);
+#pragma unroll 1
+  for (int c = D; c >= 0; --c) {
+    const R2 f = Fs[c];
+    p = cfma(p, u, f);
+    pa = fma(pa, au, sqrt(cabs2(f)));
+  }
+  const R eps = sizeof(R) == 4 ? R(5.9604645e-8) : R(1.1102230246251565e-16);
+  const R bound = R(8 * D) * eps * pa;
+  return isfinite(pa) && cabs2(p) <= bound * bound;
 }
 
 // ------------------------------------------------------------ group reductions
@@ -685,6 +714,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     for (int r2 = lane; r2 < nrows; r2 += 32) {
       const int src_row = a.coef_mode ? r2 : (r2 < 2 * H) ? r2 : 2 * Hs + (r2 - 2 * H);
       const int64_t off = (int64_t)src_row * stride + base;
+      if (a.skip_copies) continue;  // fault injection: the row never lands
       if (!FTP_DCHECK(a.status, off >= 0 && off + NGW <= a.sums_elems, 11, off, a.sums_elems) ||
           !FTP_DCHECK(a.status, (gaddr(sums + off) & 15) == 0, 12, gaddr(sums + off) & 15, 16) ||
           !FTP_DCHECK(a.status, (saddr(dst + (size_t)r2 * NGW) & 15) == 0, 13, 0, 16)) {
@@ -694,7 +724,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     }
   };
 
-  unsigned long long st_iters = 0, st_items = 0, st_nonconv = 0, st_redo = 0;
+  unsigned long long st_iters = 0;
+  unsigned st_items = 0, st_nonconv = 0, st_redo = 0, st_redo_nc = 0, st_final = 0;
+  const int polls = a.wait_polls;  // resolved by the host (kWaitPolls by default)
   unsigned parity[2] = {0u, 0u};
   int buf = 0, cur_tau = -1;
   R sum_abs_alpha = R(0);
@@ -752,15 +784,24 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       cur_tau = tau;
       __syncwarp();
     }
-    const bool landed = mbar_wait(&mbar[buf], parity[buf]);
+    const bool landed = mbar_wait(&mbar[buf], parity[buf], polls);
     parity[buf] ^= 1u;
     if (__any_sync(0xffffffffu, !landed)) {
+      // give up: report the timeout, then let this warp's copies in flight
+      // (the late unit's and the next unit's, each waited on once more with
+      // the same bound) land before the CTA's shared memory is released
       if (lane == 0) atomicCAS(&a.status[ST_CODE], DEV_OK, DEV_TIMEOUT);
+      mbar_wait(&mbar[buf], parity[buf] ^ 1u, polls);
+      if (un < nunits) mbar_wait(&mbar[buf ^ 1], parity[buf ^ 1], polls);
       break;
     }
     const S2* st = stage + (size_t)buf * (C::STAGE_BYTES / sizeof(S2));
     const int64_t k = redo_pass ? cu.kfirst : cu.kfirst + gi;
-    const bool valid = unit_ok && (redo_pass ? gi == 0 : k < seg_nf);
+    bool valid = unit_ok && (redo_pass ? gi == 0 : k < seg_nf);
+    if (valid && a.sel_mark) {  // re-solve pass restricted to one kind of listed frequency
+      const bool fp64 = (a.sel_mark[a.kmap[k]] & MARK_FP64) != 0;
+      valid = (a.sel_mode == 2) == fp64;
+    }
 
     R amax2 = R(0), bmax2 = R(0);
     if (a.coef_mode) {
@@ -1068,7 +1109,20 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         for (int r = 0; r < RR; ++r) lane_nc = lane_nc || !conv[r];
       }
     }
-    const bool nonconv = gor<G>(lane_nc) && !constant;
+    bool nonconv = gor<G>(lane_nc) && !constant;
+    if constexpr (!kFast) {
+      // FP64 iterations (the FP64 path and the re-solve of cap hits): at the
+      // cap keep the flag only if some root of the item is not a zero of F
+      // to the working precision (the lanes split the roots).  The FP32
+      // kernels leave it out of their code: their cap hits are re-solved
+      // with FP64 iterations.
+      if (__any_sync(0xffffffffu, nonconv)) {
+        bool bad = false;
+        if (nonconv)
+          for (int i = gl; i < D; i += G) bad = bad || !pseudo_zero<D, R>(Zs[i], Fs);
+        nonconv = gor<G>(bad);
+      }
+    }
 
     // ---- candidates: P at every root scaled onto |psi| = 1 (working precision).
     //      Rolled loops over the lane's root slots (roots read back from
@@ -1140,7 +1194,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       const double rv = gl == 0 ? (double)bpsi.x : gl == 1 ? (double)bpsi.y : (double)bits;
       if (valid && in_range && gl < 3) (gl == 0 ? a.power : gl == 1 ? a.theta1 : a.theta2)[o] = rv;
     }
-    if (valid && in_range && gl == 0) {
+    if (valid && in_range && gl == 0 && !a.resolve_pass) {
       st_iters += (unsigned long long)iters;
       st_items += 1;
       st_nonconv += nonconv ? 1 : 0;
@@ -1333,7 +1387,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     //      items whose P could be off by more than the threshold are
     //      re-solved from direct FP64 sums.
     bool redo = false;
-    if (a.redo_list && valid) {
+    if (a.sum_err > 0.0 && valid) {
       if (degenerate) {
         redo = true;
       } else {
@@ -1359,17 +1413,32 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       }
     }
     if (valid && in_range && gl == 0) {
-      // a frequency goes on the re-solve list once (mark 0 -> 1); if the
-      // list is full its mark becomes 2 and a later pass flags its items
-      if (redo && FTP_DCHECK(a.status, ridx < a.redo_marks, 23, ridx, a.redo_marks) &&
-          atomicCAS(&a.redo_mark[ridx], 0, 1) == 0) {
-        const int slot = atomicAdd(a.redo_count, 1);
-        if (slot < a.redo_cap) {
-          a.redo_list[slot] = (int)ridx;
-          ++st_redo;
-        } else {
-          atomicExch(&a.redo_mark[ridx], 2);
+      // A frequency goes on the re-solve list once (mark 0 -> MARK_LISTED),
+      // with MARK_FP64 added when one of its items hit the iteration cap
+      // (re-solved with FP64 Aberth iterations); if the list is full the
+      // mark gets MARK_OVERFLOW and a later pass flags its items.  Without a
+      // list (a call that cannot re-solve) an item over the error threshold
+      // is flagged unresolved.
+      const bool fp64 = nonconv && a.list_nonconv;
+      // a cap hit is final in a re-solve pass and where no re-solve follows
+      st_final += (nonconv && (a.resolve_pass || !(a.list_nonconv && a.redo_list))) ? 1 : 0;
+      bool unresolved = false;
+      if ((redo || fp64) && a.redo_list) {
+        if (FTP_DCHECK(a.status, ridx < a.redo_marks, 23, ridx, a.redo_marks)) {
+          if (atomicCAS(&a.redo_mark[ridx], 0, MARK_LISTED) == 0) {
+            const int slot = atomicAdd(a.redo_count, 1);
+            if (slot < a.redo_cap) {
+              a.redo_list[slot] = (int)ridx;
+              ++st_redo;
+              st_redo_nc += fp64 ? 1 : 0;
+            } else {
+              atomicOr(&a.redo_mark[ridx], MARK_OVERFLOW);
+            }
+          }
+          if (fp64) atomicOr(&a.redo_mark[ridx], MARK_FP64);
         }
+      } else if (redo && !a.resolve_pass) {
+        unresolved = true;
       }
       if (a.flags) {
         unsigned f = 0;
@@ -1377,7 +1446,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
         if (degenerate) f |= 2u;
         if (constant) f |= 4u;
         if (w_f(th1) < 0.0f) f |= 8u;
+        if (unresolved) f |= 16u;
         if (no_positive) f |= 64u;
+        if (a.resolve_pass) f |= 128u;
         a.flags[o] = (uint8_t)f;
       }
     }
@@ -1393,12 +1464,16 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     st_items += __shfl_xor_sync(0xffffffffu, st_items, o);
     st_nonconv += __shfl_xor_sync(0xffffffffu, st_nonconv, o);
     st_redo += __shfl_xor_sync(0xffffffffu, st_redo, o);
+    st_redo_nc += __shfl_xor_sync(0xffffffffu, st_redo_nc, o);
+    st_final += __shfl_xor_sync(0xffffffffu, st_final, o);
   }
-  if (lane == 0 && (st_items || st_redo)) {
+  if (lane == 0 && (st_items || st_redo || st_final)) {
     atomicAdd(&a.counters[CNT_ITERS], st_iters);
-    atomicAdd(&a.counters[CNT_ITEMS], st_items);
-    atomicAdd(&a.counters[CNT_NONCONV], st_nonconv);
-    atomicAdd(&a.counters[CNT_REDO], st_redo);
+    atomicAdd(&a.counters[CNT_ITEMS], (unsigned long long)st_items);
+    atomicAdd(&a.counters[CNT_NONCONV], (unsigned long long)st_nonconv);
+    atomicAdd(&a.counters[CNT_REDO], (unsigned long long)st_redo);
+    atomicAdd(&a.counters[CNT_REDO_NC], (unsigned long long)st_redo_nc);
+    atomicAdd(&a.counters[CNT_NC_FINAL], (unsigned long long)st_final);
   }
 }
 

@@ -17,7 +17,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libftp_gb300.so")
+# FTP_GB300_LIB selects another build of the same library (e.g. the
+# self-checking libftp_gb300_checks.so); it must exist like the default one.
+LIB_PATH = os.environ.get("FTP_GB300_LIB") or os.path.join(_HERE, "libftp_gb300.so")
 
 FTP_OK = 0
 FTP_FP64 = 0
@@ -30,6 +32,7 @@ FLAG_NEGATIVE_AMP = 8
 FLAG_UNRESOLVED = 16
 FLAG_SCREENED_OUT = 32
 FLAG_NO_POSITIVE = 64
+FLAG_RESOLVED = 128
 
 STATUS_NAMES = {0: "FTP_OK", 1: "FTP_ERR_INVALID_ARG", 2: "FTP_ERR_ZERO_VARIANCE",
                 3: "FTP_ERR_MIXED_ZERO_SIGMA", 4: "FTP_ERR_NONFINITE", 5: "FTP_ERR_OOM",
@@ -44,7 +47,8 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_mlp_train", "ftp_batch_features", "ftp_batch_screened", "ftp_training_rows",
            "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune",
            "ftp_set_positive_amplitude", "ftp_multiband_periodogram",
-           "ftp_shared_multiband", "ftp_roots_first_phase_ms")
+           "ftp_shared_multiband", "ftp_roots_first_phase_ms", "ftp_set_solver_limits",
+           "ftp_set_fault_injection")
 
 
 class FtpGrid(C.Structure):
@@ -88,7 +92,9 @@ def load(path: str | None = None) -> C.CDLL:
     lib.ftp_plan_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64),
                                   C.POINTER(i32)]
     lib.ftp_solver_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64),
-                                     C.POINTER(i64)]
+                                     C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    lib.ftp_set_solver_limits.argtypes = [vp, i32, i32, i32]
+    lib.ftp_set_fault_injection.argtypes = [vp, i32]
     lib.ftp_set_timing.argtypes = [vp, i32]
     lib.ftp_periodogram_sums_noalloc.argtypes = [vp, i64, i32, i64, i32, dbl, dbl,
                                                  C.POINTER(FtpTemplate), i32, vp, vp, vp, vp,
@@ -389,12 +395,23 @@ def ftp_plan_info(plan: int) -> dict:
 
 
 def ftp_solver_stats(plan: int) -> dict:
-    n, nc, rs = C.c_int64(), C.c_int64(), C.c_int64()
+    n, nc, rs, rn, sn = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
     it = C.c_double()
-    _check(load().ftp_solver_stats(plan, C.byref(n), C.byref(it), C.byref(nc), C.byref(rs)),
-           "ftp_solver_stats")
+    _check(load().ftp_solver_stats(plan, C.byref(n), C.byref(it), C.byref(nc), C.byref(rs),
+                                   C.byref(rn), C.byref(sn)), "ftp_solver_stats")
     return {"items": n.value, "mean_iterations": it.value, "nonconverged": nc.value,
-            "resolved": rs.value}
+            "resolved": rs.value, "resolved_nonconverged": rn.value,
+            "still_nonconverged": sn.value}
+
+
+def ftp_set_solver_limits(plan: int, maxit: int = 0, redo_maxit: int = 0,
+                          wait_polls: int = 0) -> None:
+    _check(load().ftp_set_solver_limits(plan, int(maxit), int(redo_maxit), int(wait_polls)),
+           "ftp_set_solver_limits")
+
+
+def ftp_set_fault_injection(plan: int, mode: int) -> None:
+    _check(load().ftp_set_fault_injection(plan, int(mode)), "ftp_set_fault_injection")
 
 
 def ftp_set_timing(plan: int, enable: bool) -> None:
@@ -485,3 +502,6 @@ class Plan:
 
     def solver_stats(self) -> dict:
         return ftp_solver_stats(self.h)
+
+    def set_solver_limits(self, maxit: int = 0, redo_maxit: int = 0, wait_polls: int = 0):
+        ftp_set_solver_limits(self.h, maxit, redo_maxit, wait_polls)

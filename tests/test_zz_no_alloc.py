@@ -1,25 +1,31 @@
-"""The allocation-free entry point agrees with the ordinary one.
+"""The allocation-free entry point agrees with the FP64 oracle.
 
 ftp_periodogram_sums_noalloc exists for callers that cannot call cudaMalloc
 (a process whose device memory belongs to another runtime's pool, a
 latency-bound loop that cannot afford an allocation's implicit
 synchronisation, a service under a hard memory cap): it runs the root stage on
 sums the caller already holds, with its scratch in a fixed array inside the
-library.  Here the sums come from ftp_sums, are copied into a padded device
-buffer, and two consecutive allocation-free calls are compared with
-ftp_periodogram on the same lightcurve, within the parity tolerances of the
-other GPU tests.  This file is collected last so that a run stopping at the
+library.  Here the sums come from ftp_sums and are copied into a padded device
+buffer.  Two consecutive allocation-free calls are compared with
+oracle.periodogram on every frequency, within the parity tolerances of the
+other GPU tests, and with each other.  A curve whose phases cluster (three
+observations, low frequencies) has items whose estimated error of P from the
+sums exceeds the threshold: the entry point cannot re-solve them, so they
+must carry FTP_FLAG_UNRESOLVED, and every item without that flag must still
+meet the tolerance.  This file is collected last so that a run stopping at the
 first failure has already run every other test."""
 import numpy as np
 import pytest
 
 import __graft_entry__
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_P = {"mixed": 1e-4, "fp64": 1e-9}
+FLAG_UNRESOLVED = 16
 
 
 @pytest.fixture(scope="module")
@@ -32,14 +38,12 @@ def ftp():
     return f
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_no_alloc_matches_periodogram_twice(ftp, prec):
-    lc, tpl, grid = synth.small_curve(nf=3001)
-    bank = [tpl, synth.make_template(2, 9100)]
+def no_alloc_twice(ftp, lc, bank, grid, prec):
+    """Sums by ftp_sums, then two allocation-free calls; returns the host
+    results of both calls."""
     H = max(b.H for b in bank)
     templates = [(b.c, b.s) for b in bank]
     with ftp.Plan(lc.t.size, H, (grid.df, grid.k0, grid.nf), len(bank), prec) as plan:
-        ref = plan.periodogram(lc.t, lc.y, lc.dy, templates)
         sums, (ybar, YY) = plan.sums(lc.t, lc.y, lc.dy, H)
     dev = torch.device("cuda:0")
     stride = (grid.nf + 63) // 64 * 64 + 64
@@ -47,21 +51,50 @@ def test_no_alloc_matches_periodogram_twice(ftp, prec):
     dsums = torch.zeros((3 * H, stride), dtype=cdt, device=dev)
     dsums[:, : grid.nf] = torch.from_numpy(sums).to(dev)
     shape = (len(bank), grid.nf)
-    previous = None
+    calls = []
     for _ in range(2):
         outs = [torch.full(shape, np.nan, dtype=torch.float64, device=dev) for _ in range(4)]
         flags = torch.full(shape, 255, dtype=torch.uint8, device=dev)
         ftp.ftp_periodogram_sums_noalloc(dsums, stride, prec, grid.nf, H, ybar, YY, templates,
                                          *outs, flags, device=0)
         torch.cuda.synchronize()
-        power = outs[0].cpu().numpy()
-        assert np.all(np.isfinite(power))
-        assert np.max(np.abs(power - ref["power"])) <= TOL_P[prec]
-        assert np.all(flags.cpu().numpy() != 255)
-        if previous is not None:
-            # the same sums give the same answer on the second call
-            np.testing.assert_array_equal(power, previous)
-        previous = power
+        calls.append({"power": outs[0].cpu().numpy(), "theta1": outs[1].cpu().numpy(),
+                      "flags": flags.cpu().numpy()})
+    return calls
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_no_alloc_matches_oracle_twice(ftp, prec):
+    lc, tpl, grid = synth.small_curve(nf=3001)
+    bank = [tpl, synth.make_template(2, 9100)]
+    refs = [oracle.periodogram(lc.t, lc.y, lc.dy, grid.freqs(), b.c, b.s) for b in bank]
+    calls = no_alloc_twice(ftp, lc, bank, grid, prec)
+    for c in calls:
+        assert np.all(c["flags"] != 255)
+        assert not np.any(c["flags"] & FLAG_UNRESOLVED)
+        for i, ref in enumerate(refs):
+            d = np.abs(c["power"][i] - ref["power"])
+            assert np.max(d) <= TOL_P[prec], (i, float(np.max(d)))
+    # the same sums give the same answer on the second call
+    np.testing.assert_array_equal(calls[0]["power"], calls[1]["power"])
+    np.testing.assert_array_equal(calls[0]["flags"], calls[1]["flags"])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_no_alloc_flags_what_it_cannot_resolve(ftp, prec):
+    rng = np.random.default_rng(21)
+    tpl = synth.make_template(2, 8000)
+    lc = synth.random_curve(rng, 3, T=10.0, signal=0.6, tpl=tpl, period=3.0)
+    grid = synth.Grid(df=1 / 50.0, k0=1, nf=200)
+    ref = oracle.periodogram(lc.t, lc.y, lc.dy, grid.freqs(), tpl.c, tpl.s)
+    calls = no_alloc_twice(ftp, lc, [tpl], grid, prec)
+    for c in calls:
+        unresolved = (c["flags"][0] & FLAG_UNRESOLVED) != 0
+        assert np.any(unresolved)
+        ok = ~unresolved
+        d = np.abs(c["power"][0][ok] - ref["power"][ok])
+        assert np.max(d) <= TOL_P[prec], float(np.max(d))
+    np.testing.assert_array_equal(calls[0]["flags"], calls[1]["flags"])
 
 
 def test_no_alloc_rejects_requests_beyond_its_scratch(ftp):
@@ -79,4 +112,8 @@ def test_no_alloc_rejects_requests_beyond_its_scratch(ftp):
     host = [np.empty(nf) for _ in range(4)]
     with pytest.raises(ftp.FtpError) as e:  # outputs must be device memory
         ftp.ftp_periodogram_sums_noalloc(dsums, 128, "mixed", nf, H, 0.0, 1.0, many[:1], *host)
+    assert e.value.status == 1
+    with pytest.raises(ftp.FtpError) as e:  # pointers of another device ordinal
+        ftp.ftp_periodogram_sums_noalloc(dsums, 128, "mixed", nf, H, 0.0, 1.0, many[:1], *outs,
+                                         device=torch.cuda.device_count())
     assert e.value.status == 1
