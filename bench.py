@@ -34,10 +34,9 @@ METRIC = ("FTP freq·template evals/s on 1 GB300, mixed vs FP64 at |ΔP|≤1e-4;
 UNIT = "evals/s"
 WORKLOAD = ("single long lightcurve: N_obs=1e4 over 3000 d with nightly gaps (8 h windows, "
             "30% nights dropped), H=6 template, N_f=2.5e5, df=1/(5*3000 d)")
-# Peaks of the plain ALUs (no tensor cores): 152 SMs x 128 FP32 lanes x 2 flop
-# at the 2070 MHz maximum SM clock; FP64 at the nominal 1.25 TFLOP/s.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# HBM copy rate when no measured value is at hand (the profiling recipe's
+# fallback for these GPUs); the ALU peaks are measured by every run.
+HBM_FALLBACK_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 # batch tuning cache (ftp_batch_autotune), outside the repository
 TUNING_CACHE = os.environ.get("FTP_TUNING_CACHE",
@@ -234,7 +233,7 @@ class ClockSampler:
 
 def solver_report(stats, mean_iterations=None):
     """Root-solver counts of the last call: items that hit the Aberth cap in
-    the main pass (before) and after their re-solve with FP64 iterations, and
+    the main pass (before) and after their re-solve, and
     the frequencies re-solved from direct FP64 sums."""
     it = stats["mean_iterations"] if mean_iterations is None else mean_iterations
     return {"mean_iterations": round(it, 3),
@@ -259,6 +258,51 @@ def ncu_traffic_per_item():
     return None
 
 
+# ------------------------------------------------------------------ peaks
+def hbm_peak():
+    """(GB/s, source) of the HBM copy rate measured on this machine's GPUs, else
+    the recipe's fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def measure_alu_peaks(ftp, local):
+    """Peak FP32, packed-FP32 and FP64 FMA rates of this GPU (TFLOP/s, best of
+    three launches of ftp_alu_peak), with the SM clock sampled meanwhile."""
+    iters = {0: 40_000, 1: 20_000, 2: 3_000}
+    best = {}
+    with ClockSampler(local) as clk:
+        for kind, n in iters.items():
+            rates = []
+            for _ in range(3):
+                flops, ms = ftp.ftp_alu_peak(local, kind, n)
+                rates.append(flops / (ms / 1e3) / 1e12)
+            best[kind] = max(rates)
+    c = clk.summary() or {}
+    out = {"fp32_tflops": round(best[0], 2), "fp32x2_tflops": round(best[1], 2),
+           "fp64_tflops": round(best[2], 3), "sm_mhz": c.get("sm_mhz"),
+           "how": "ftp_alu_peak: independent FMA chains on every SM (32 warps each), best of 3 "
+                  "launches, CUDA events"}
+    # the root kernels issue both scalar and packed FP32 FMAs: the larger rate bounds them
+    out["fp32_peak_tflops"] = max(out["fp32_tflops"], out["fp32x2_tflops"])
+    return out
+
+
+def alu_roofline(achieved, peaks, kernel, traffic=None, traffic_note=None):
+    peak = peaks["fp32_peak_tflops"]
+    r = {"bound": "alu", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
+         "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kernel,
+         "peak_source": f"measured in this run (FP32 FMA chains, ftp_alu_peak) at "
+                        f"{peaks.get('sm_mhz')} MHz SM clock"}
+    if traffic_note:
+        r["traffic_note"] = traffic_note
+    return r
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, world, rank, local, pg):
     import numpy as np
@@ -267,41 +311,45 @@ def run_ours(args, world, rank, local, pg):
     import __graft_entry__
     import synth
     __graft_entry__.build()
-    from paper_2101_12348_gb300 import ftp
+    from paper_2101_12348_gb300 import ftp, shard
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    lc, tpl, grid = synth.long_curve(nf=args.n_freq)
+    # one lightcurve per rank: rank r analyses its own seeded curve of the
+    # workload's shape (curves are independent: no data exchange)
+    lc, tpl, grid = synth.long_curve(nf=args.n_freq, seed=1002 + 1000 * rank)
     nf, D = grid.nf, 6 * tpl.H - 2
     stream = torch.cuda.Stream(device=dev)
     tpls = [(tpl.c, tpl.s)]
     dt_, dy_, ds_ = (torch.from_numpy(a).to(dev) for a in (lc.t, lc.y, lc.dy))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    peaks = measure_alu_peaks(ftp, local)
+    hbm, hbm_src = hbm_peak()
 
     def outputs():
         return ([torch.empty(nf, dtype=torch.float64, device=dev) for _ in range(4)],
                 torch.empty(nf, dtype=torch.uint8, device=dev))
 
     def timed(plan, steps, warmup, outs, fl):
+        """Device time of each of `steps` calls (stage timing off)."""
         for _ in range(warmup):
             ftp.ftp_periodogram(plan, dt_, dy_, ds_, lc.t.size, tpls, *outs, fl)
+        return _timed_calls(stream, flush, steps, lambda: ftp.ftp_periodogram(
+            plan, dt_, dy_, ds_, lc.t.size, tpls, *outs, fl))
+
+    def staged(plan, calls, outs, fl):
+        """Stage times, first-kernel time and iterations of `calls` timed calls."""
         ftp.ftp_set_timing(plan, True)
-        step_ms, roots_ms, first_ms, iters = [], [], [], []
+        st, first, iters = [], [], []
         with torch.cuda.stream(stream):
-            for _ in range(steps):
+            for _ in range(calls):
                 flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
                 ftp.ftp_periodogram(plan, dt_, dy_, ds_, lc.t.size, tpls, *outs, fl)
-                e1.record(stream)
-                e1.synchronize()
-                step_ms.append(e0.elapsed_time(e1))
-                st = ftp.ftp_stage_times(plan)
-                roots_ms.append(st[4])
-                first_ms.append(ftp.ftp_roots_first_phase_ms(plan))
+                st.append(ftp.ftp_stage_times(plan))
+                first.append(ftp.ftp_roots_first_phase_ms(plan))
                 iters.append(ftp.ftp_solver_stats(plan)["mean_iterations"])
         ftp.ftp_set_timing(plan, False)
-        return step_ms, roots_ms, first_ms, iters
+        return np.array(st), first, iters
 
     sh = stream.cuda_stream
     mixed = ftp.ftp_plan(lc.t.size, tpl.H, (grid.df, grid.k0, grid.nf), 1, "mixed", local, sh)
@@ -309,11 +357,11 @@ def run_ours(args, world, rank, local, pg):
     out_m, fl_m = outputs()
     out_d, fl_d = outputs()
 
-    # ---- mixed, device-resident inputs: the headline
+    # ---- mixed, device-resident inputs: the headline (stage timing off)
     barrier(pg)
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
-        step_ms, roots_ms, first_ms, iters = timed(mixed, args.steps, args.warmup, out_m, fl_m)
+        step_ms = timed(mixed, args.steps, args.warmup, out_m, fl_m)
     torch.cuda.synchronize(dev)
     barrier(pg)
     clocks = clk.summary()
@@ -324,10 +372,16 @@ def run_ours(args, world, rank, local, pg):
     evals_all = sum_over_ranks(pg, float(args.steps * nf), dev)
     value = evals_all / (total_ms_max / 1e3)
 
+    # ---- the stages, in separate calls with stage timing on
+    st, first_ms, iters = staged(mixed, max(3, min(args.steps, 10)), out_m, fl_m)
+    st_med = np.median(st, axis=0)
+    first = statistics.median(first_ms)
+    ibar = statistics.mean(iters)
+
     # ---- FP64 path beside it, and the mixed-vs-FP64 error on every frequency
     fp64_path = None
     if args.fp64_steps > 0:
-        d_ms, d_roots, _, _ = timed(fp64, args.fp64_steps, 1, out_d, fl_d)
+        d_ms = timed(fp64, args.fp64_steps, 1, out_d, fl_d)
         fp64_path = {"value": round(nf * len(d_ms) / (sum(d_ms) / 1e3), 1), "unit": UNIT,
                      "steps": len(d_ms), "ms_per_step": round(statistics.mean(d_ms), 3),
                      "max_abs_dP_mixed_vs_fp64":
@@ -349,37 +403,79 @@ def run_ours(args, world, rank, local, pg):
 
     # ---- roofline of the dominant kernel: the first root-stage kernel
     #      (assembly, Aberth iterations, candidates), timed with events
-    roots_s = statistics.mean(first_ms) / 1e3
-    ibar = statistics.mean(iters)
     fp32_flops = nf * 26.0 * D * D * ibar          # Aberth: 26 D^2 flops per iteration
-    achieved = fp32_flops / roots_s / 1e12
+    achieved = fp32_flops / (first / 1e3) / 1e12
     tpi = ncu_traffic_per_item()
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
-                "traffic": (round(tpi * nf) if tpi else None),
-                "kernel": "roots_kernel phase 1 (assembly + Aberth + candidates; "
-                          "FP32 Aberth flops 26*D^2*iterations)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    roofline = alu_roofline(
+        achieved, peaks, "roots_kernel phase 1 (assembly + Aberth + candidates; FP32 Aberth "
+        "flops 26*D^2*iterations)", round(tpi * nf) if tpi else None,
+        "DRAM bytes per item from an ncu capture of the same kernel on the first 2e4 "
+        "frequencies of this workload, scaled to the launch's 2.5e5 items" if tpi else None)
+
+    # ---- whole step: T* = sum over stages of the time at their bound
+    info = ftp.ftp_plan_info(mixed)
+    n_grid, H = info["grid_len"], tpl.H
+    b_a = 8 * n_grid + 16 * n_grid + 16 * 2 * H * (grid.k0 + nf) + 24 * H * nf
+    b_p2 = (24 * H + 24 + 33) * nf
+    t_a = b_a / (hbm * 1e9) * 1e3
+    t_1 = fp32_flops / (peaks["fp32_peak_tflops"] * 1e12) * 1e3
+    t_2 = b_p2 / (hbm * 1e9) * 1e3
+    m_a = float(np.sum(st_med[:4]))
+    m_1, m_2 = first, float(st_med[4]) - first
+    t_step = statistics.median(step_ms)
+    whole = {
+        "t_star_ms": round(t_a + t_1 + t_2, 4), "t_ms": round(t_step, 4),
+        "frac": round((t_a + t_1 + t_2) / t_step, 4),
+        "stages": {"step_a_sums": {"t_star_ms": round(t_a, 4), "t_ms": round(m_a, 4),
+                                   "bound": "hbm"},
+                   "roots_phase1": {"t_star_ms": round(t_1, 4), "t_ms": round(m_1, 4),
+                                    "bound": "alu"},
+                   "roots_phase2": {"t_star_ms": round(t_2, 4), "t_ms": round(m_2, 4),
+                                    "bound": "hbm"}},
+        "model": "step (a): spread writes 8 B per grid cell, FFT one read + one write "
+                 "(16 B per cell), gather reads 16 B per needed grid index and writes 24H B "
+                 "per frequency; phase 1: 26 D^2 iterations FP32 flops per item at the "
+                 "measured FP32 peak; phase 2: (24H + 57) B per item at the HBM peak "
+                 f"({hbm:.0f} GB/s, {hbm_src}); stage times from separate calls with stage "
+                 "timing on, T from the headline steps (median)"}
+
+    # ---- host merge of the ranks' results: each curve's best peak
+    k_best = int(torch.argmax(out_m[0]).item())
+    best = {"rank": rank, "f_best": float(grid.freqs()[k_best]),
+            "P_best": float(out_m[0][k_best].item())}
+    merged = shard.gather_to_root(pg, best, rank, world)
+    torch.cuda.synchronize(dev)
 
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
+        "ms_per_step": round(statistics.mean(step_ms), 4),
+        "ms_per_step_median": round(t_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_obs": int(lc.t.size), "H": tpl.H, "n_freq": nf,
                    "templates": 1, "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "stage_timing": "off in the timed steps; stages from separate calls",
+                   "parallelism": (f"{world} ranks, one distinct seeded lightcurve each "
+                                   "(independent problems, no data exchange)")
+                   if world > 1 else "single GPU"},
         "fp64_path": fp64_path,
-        "stage_ms": {"roots": round(statistics.mean(roots_ms), 4),
-                     "roots_phase1": round(statistics.mean(first_ms), 4)},
+        "stage_ms": {"moments_binning": round(float(st_med[0]), 4),
+                     "spread": round(float(st_med[1]), 4), "fft": round(float(st_med[2]), 4),
+                     "gather": round(float(st_med[3]), 4),
+                     "roots": round(float(st_med[4]), 4), "roots_phase1": round(first, 4),
+                     "resolve": round(float(st_med[5]), 4)},
         "solver": solver_report(stats_m, ibar),
         "roofline": roofline,
+        "whole_step": whole,
+        "alu_peaks": peaks,
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
         "gpu_launches": args.steps * launches_per_call,
     }
+    if world > 1 and rank == 0:
+        result["ranks"] = merged
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
@@ -405,6 +501,21 @@ BANK = ("template bank over one long lightcurve: N_obs=1e5 over 4000 d with nigh
         "32 templates H=10, N_f=1e6, df=1/(5*4000 d)")
 
 
+def subset_survey(sv, idx):
+    """The curves `idx` of a synthetic survey, as a survey of their own."""
+    import numpy as np
+
+    import synth
+    idx = np.asarray(idx, dtype=np.int64)
+    n = np.diff(sv.obs_off)[idx]
+    off = np.zeros(idx.size + 1, dtype=np.int64)
+    off[1:] = np.cumsum(n)
+    sl = [np.arange(sv.obs_off[c], sv.obs_off[c + 1]) for c in idx]
+    cat = np.concatenate(sl) if sl else np.zeros(0, dtype=np.int64)
+    return synth.Survey(off, sv.t[cat], sv.y[cat], sv.dy[cat], [sv.grids[c] for c in idx],
+                        sv.bank, sv.tpl_of_curve[idx], sv.injected[idx], sv.period[idx])
+
+
 def _timed_calls(stream, flush, steps, call):
     """CUDA-event times (ms) of `steps` calls on `stream`, L2 flushed before each."""
     import torch
@@ -421,11 +532,12 @@ def _timed_calls(stream, flush, steps, call):
     return out
 
 
-def _result(args, world, metric_value, step_ms, cfg, **extra):
+def _result(args, world, metric_value, step_ms, cfg, scaling="weak", **extra):
     r = {"metric": METRIC, "value": round(metric_value, 1), "unit": UNIT, "n_gpus": world,
          "steps": args.steps, "warmup": args.warmup,
-         "ms_per_step": round(statistics.mean(step_ms), 4), "higher_is_better": True,
-         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+         "ms_per_step": round(statistics.mean(step_ms), 4),
+         "ms_per_step_median": round(statistics.median(step_ms), 4), "higher_is_better": True,
+         "scaling": scaling, "vs_baseline": None, "dtype": "f32+f64 (mixed)",
          "data": "synthetic", "config": cfg}
     r.update(extra)
     return r
@@ -441,9 +553,19 @@ def run_survey(args, world, rank, local, pg):
     __graft_entry__.build()
     from paper_2101_12348_gb300 import ftp
 
+    from paper_2101_12348_gb300 import shard
+
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    sv = synth.survey(ncurves=args.ncurves, seed=1003)
+    full = synth.survey(ncurves=args.ncurves, seed=1003)
+    # curves shared out across ranks, balanced by the root stage's cost
+    # (frequencies x D^2); a single rank takes them all
+    cost = np.array([g.nf * (6 * full.bank[full.tpl_of_curve[c]].H - 2) ** 2
+                     for c, g in enumerate(full.grids)], dtype=np.float64)
+    parts = shard.partition_by_cost(cost, world)
+    mine = parts[rank]
+    sv = subset_survey(full, mine)
+    peaks = measure_alu_peaks(ftp, local)
     bank = [(b.c, b.s) for b in sv.bank]
     grids = [(g.df, g.k0, g.nf) for g in sv.grids]
     nfs = np.array([g.nf for g in sv.grids], dtype=np.int64)
@@ -495,11 +617,9 @@ def run_survey(args, world, rank, local, pg):
     ibar = stats["mean_iterations"]
     flops = float(np.sum(nfs * 26.0 * (6 * Hc - 2) ** 2)) * ibar
     achieved = flops / (st[4] / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-                "kernel": "roots_kernel (FP32 Aberth flops 26*D^2*iterations, summed over "
-                          "curves with the batch's mean iteration count)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    roofline = alu_roofline(achieved, peaks, "roots stage, both kernels (FP32 Aberth flops "
+                            "26*D^2*iterations, summed over curves with the batch's mean "
+                            "iteration count)")
     # FP64 path on the first 64 curves, and the mixed-vs-FP64 error there
     nsub = min(64, sv.ncurves)
     sub_tot = int(out_off[nsub])
@@ -537,12 +657,25 @@ def run_survey(args, world, rank, local, pg):
     e2e = {"value": round(sum_over_ranks(pg, float(e2e_steps * tot), dev) / e2e_s, 1),
            "unit": UNIT, "h2d_bytes_per_step": int(3 * sv.t.size * 8),
            "d2h_bytes_per_step": int(tot * 33), "steps": e2e_steps}
-    cfg = {"workload": BATCH_SURVEY.format(n=sv.ncurves), "curves": sv.ncurves,
+    # host merge: each curve's best power, back in survey order on rank 0
+    best_c = np.array([float(outs[0][out_off[c]:out_off[c + 1]].max().item())
+                       for c in range(sv.ncurves)])
+    got = shard.gather_to_root(pg, (mine, best_c), rank, world)
+    cfg = {"workload": BATCH_SURVEY.format(n=full.ncurves), "curves": full.ncurves,
+           "curves_this_rank": sv.ncurves,
            "n_obs_total": int(sv.t.size), "evals_per_step": tot, "templates_per_curve": 1,
            "l2": "flushed between steps (512 MiB write); sum tiles exceed L2",
            "graph": {0: "eager", 1: "captured", 2: "replayed"}[info["graph"]],
-           "chunks": info["chunks"], "parallelism": "single GPU"}
+           "chunks": info["chunks"],
+           "parallelism": (f"{world} ranks, curves balanced by N_f*D^2 (no data exchange; "
+                           "host merge of results)") if world > 1 else "single GPU"}
+    if rank == 0 and world > 1:
+        merged = shard.merge_parts(full.ncurves, got)
+        cfg["merged_curves"] = int(merged.size)
+        cfg["rank_loads"] = [round(float(x) / float(cost.sum()), 4)
+                             for x in shard.part_loads(cost, parts)]
     result = _result(args, world, value, step_ms, cfg,
+                     scaling="strong" if world > 1 else "weak", alu_peaks=peaks,
                      fp64_path=fp64_path,
                      stage_ms={"sums": round(st[0], 3), "roots": round(st[4], 3),
                                "resolve": round(st[5], 3)},
@@ -582,9 +715,16 @@ def run_bank(args, world, rank, local, pg):
     __graft_entry__.build()
     from paper_2101_12348_gb300 import ftp
 
+    from paper_2101_12348_gb300 import shard
+
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    lc, bank_t, grid = synth.bank_curve()
+    lc, bank_all, grid = synth.bank_curve()
+    # templates shared out across ranks (r, r + world, ...): each rank runs
+    # its templates on the whole grid; the sums are recomputed per rank
+    mine = shard.partition_strided(len(bank_all), world)[rank]
+    bank_t = [bank_all[i] for i in mine]
+    peaks = measure_alu_peaks(ftp, local)
     bank = [(b.c, b.s) for b in bank_t]
     H, ntpl, nf = bank_t[0].H, len(bank), grid.nf
     D = 6 * H - 2
@@ -603,35 +743,29 @@ def run_bank(args, world, rank, local, pg):
     for _ in range(args.warmup):
         call()
     barrier(pg)
-    ftp.ftp_set_timing(plan, True)
-    roots, sums, first = [], [], []
-
-    def call_t():
-        call()
-
     with ClockSampler(local) as clk:
-        step_ms = []
-        for _ in range(args.steps):
-            step_ms += _timed_calls(stream, flush, 1, call_t)
-            st = ftp.ftp_stage_times(plan)
-            roots.append(st[4])
-            first.append(ftp.ftp_roots_first_phase_ms(plan))
-            sums.append(st[0] + st[1] + st[2] + st[3])
+        step_ms = _timed_calls(stream, flush, args.steps, call)
     barrier(pg)
-    ftp.ftp_set_timing(plan, False)
     clocks = clk.summary()
     stats = ftp.ftp_solver_stats(plan)
+    # stage split in separate calls with stage timing on
+    ftp.ftp_set_timing(plan, True)
+    roots, sums, first = [], [], []
+    for _ in range(max(2, min(args.steps, 5))):
+        _timed_calls(stream, flush, 1, call)
+        st = ftp.ftp_stage_times(plan)
+        roots.append(st[4])
+        first.append(ftp.ftp_roots_first_phase_ms(plan))
+        sums.append(st[0] + st[1] + st[2] + st[3])
+    ftp.ftp_set_timing(plan, False)
     launches = ftp.ftp_plan_info(plan)["last_launches"]
     total_ms = max_over_ranks(pg, sum(step_ms), dev)
     evals = ntpl * nf
     value = sum_over_ranks(pg, float(args.steps * evals), dev) / (total_ms / 1e3)
     ibar = stats["mean_iterations"]
     achieved = evals * 26.0 * D * D * ibar / (statistics.mean(first) / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-                "kernel": "roots_kernel phase 1 (assembly + Aberth + candidates; "
-                          "FP32 Aberth flops 26*D^2*iterations)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    roofline = alu_roofline(achieved, peaks, "roots_kernel phase 1 (assembly + Aberth + "
+                            "candidates; FP32 Aberth flops 26*D^2*iterations)")
     # FP64 path on the first 20000 frequencies (all 32 templates)
     nf64 = min(20_000, nf)
     p64 = ftp.ftp_plan(lc.t.size, H, (grid.df, grid.k0, nf64), ntpl, "fp64", local, sh)
@@ -661,10 +795,17 @@ def run_bank(args, world, rank, local, pg):
     e2e = {"value": round(sum_over_ranks(pg, float(e2e_steps * evals), dev) / e2e_s, 1),
            "unit": UNIT, "h2d_bytes_per_step": int(3 * lc.t.size * 8),
            "d2h_bytes_per_step": int(evals * 33), "steps": e2e_steps}
-    cfg = {"workload": BANK, "n_obs": int(lc.t.size), "H": H, "templates": ntpl, "n_freq": nf,
+    best_t = outs[0].view(ntpl, nf).max(dim=1).values.cpu().numpy()
+    got = shard.gather_to_root(pg, (mine, best_t), rank, world)
+    cfg = {"workload": BANK, "n_obs": int(lc.t.size), "H": H, "templates": len(bank_all),
+           "templates_this_rank": ntpl, "n_freq": nf,
            "l2": "flushed between steps (512 MiB write); sum tiles exceed L2",
-           "parallelism": "single GPU"}
+           "parallelism": (f"{world} ranks, templates r, r+{world}, ... per rank (no data "
+                           "exchange; host merge of results)") if world > 1 else "single GPU"}
+    if rank == 0 and world > 1:
+        cfg["merged_templates"] = int(shard.merge_parts(len(bank_all), got).size)
     result = _result(args, world, value, step_ms, cfg, fp64_path=fp64_path,
+                     scaling="strong" if world > 1 else "weak", alu_peaks=peaks,
                      stage_ms={"sums": round(statistics.mean(sums), 3),
                                "roots": round(statistics.mean(roots), 3),
                                "roots_phase1": round(statistics.mean(first), 3)},

@@ -95,7 +95,7 @@ typedef enum {
                                      theta1 > 0, so P = 0 (ftp_set_positive_amplitude) */
 #define FTP_FLAG_RESOLVED 128u    /* result of a re-solve from direct FP64 sums: the
                                      frequency was ill-conditioned, or an item of it hit
-                                     the Aberth cap (then re-solved with FP64 iterations) */
+                                     the Aberth cap */
 
 #define FTP_MAX_H 16
 
@@ -311,13 +311,16 @@ ftp_status ftp_plan_info(ftp_plan_t plan, int64_t* grid_len, int* half_width, in
  *                  NFFT sums exceeded 1e-5 (FTP_MIXED) or 1e-10 (FTP_FP64) -
  *                  clustered phases make MM = Var(M) a small difference of
  *                  O(1) sums - and those with a non-converged item;
- *   resolved_nonconverged  the latter kind among them (re-solved with FP64
- *                  Aberth iterations and the cap of ftp_set_solver_limits);
+ *   resolved_nonconverged  the latter kind among them;
  *   still_nonconverged  items left at the cap after their re-solve, or not
  *                  re-solved at all (these keep FTP_FLAG_NONCONVERGED).
  * Section 2 takes every stationary point as a candidate, so an item whose
- * roots did not all converge is re-solved rather than only reported.  Each
- * pointer is nullable.
+ * roots did not all converge is re-solved rather than only reported: from
+ * direct FP64 sums with the re-solve cap of ftp_set_solver_limits, accepting
+ * a root whose correction has stalled once F's value there is at the rounding
+ * level of its evaluation (clustered and multiple roots); on FTP_MIXED the
+ * re-solve iterates in FP32 and items still at the cap after it get one more
+ * re-solve with FP64 iterations.  Each pointer is nullable.
  */
 ftp_status ftp_solver_stats(ftp_plan_t plan, int64_t* items, double* mean_iterations,
                             int64_t* nonconverged, int64_t* resolved,
@@ -328,8 +331,7 @@ ftp_status ftp_solver_stats(ftp_plan_t plan, int64_t* items, double* mean_iterat
  * for later calls of the plan (0 restores a default):
  *   maxit        Aberth iteration cap of the main pass (default 60 on
  *                FTP_MIXED, 80 on FTP_FP64; 1..100000);
- *   redo_maxit   cap of the FP64 re-solve of items that hit maxit (default
- *                200; 1..100000);
+ *   redo_maxit   cap of the re-solve passes (default 200; 1..100000);
  *   wait_polls   polls of each bounded wait of the roots kernels for their
  *                staged sum tiles before they give up and the call returns
  *                FTP_ERR_TIMEOUT (default 2^20; >= 1).
@@ -425,6 +427,20 @@ ftp_status ftp_periodogram_sums_noalloc(const void* sums, int64_t row_stride,
                                         double* power, double* theta1, double* theta2,
                                         double* theta3, uint8_t* flags, int device,
                                         void* cuda_stream);
+
+/*
+ * ftp_alu_peak - a measurement utility, not part of the paper's method: the
+ * peak rate of the plain ALUs on `device`, the denominator of the root
+ * stage's roofline.  One launch of independent fused multiply-add chains
+ * (every SM, 32 warps each) runs `iters` outer iterations (1..2^26) after a
+ * short warm-up launch; *flops receives the floating-point operations it
+ * performed (2 per FMA) and *ms its device time (CUDA events).  kind 0: FP32
+ * fma.rn.f32; 1: packed FP32 pairs fma.rn.f32x2; 2: FP64 fma.rn.f64.  It
+ * allocates a few bytes of device memory for the kernel's guarded store.
+ * Errors: FTP_ERR_INVALID_ARG for a bad kind, count, pointer or device;
+ * FTP_ERR_CUDA if the launch fails.
+ */
+ftp_status ftp_alu_peak(int device, int kind, int iters, double* flops, float* ms);
 
 /* ------------------------------------------------------------------------
  * Learned screening.  The paper has no surrogate: these entry points rank the

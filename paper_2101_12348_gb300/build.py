@@ -26,7 +26,7 @@ BUILD_CHECKS = os.path.join(PKG, "_build_checks")
 LIB_CHECKS = os.path.join(PKG, "libftp_gb300_checks.so")
 SOURCES = ["ftp_api.cu", "ftp_nfft.cu", "ftp_roots_mixed.cu", "ftp_roots_fp64.cu",
            "ftp_roots_redo.cu", "ftp_noalloc.cu", "ftp_screen.cu", "ftp_mlp.cu",
-           "ftp_mlp_api.cu", "ftp_shared.cu"]
+           "ftp_mlp_api.cu", "ftp_shared.cu", "ftp_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

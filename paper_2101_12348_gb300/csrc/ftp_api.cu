@@ -565,20 +565,24 @@ void solver_settings(ftp_plan_t P, RootsArgs& a) {
   a.skip_copies = P->inject == 1 ? 1 : 0;
 }
 
-// A re-solve pass over listed frequencies: sel_mode 0 every one, 1 those
-// without MARK_FP64 (FP32 Aberth on the mixed path), 2 those with it.
-void resolve_settings(ftp_plan_t P, RootsArgs& a, const int* marks, int sel_mode) {
-  a.resolve_pass = 1;
-  a.sel_mark = sel_mode ? marks : nullptr;
+// A re-solve pass over listed frequencies from direct FP64 sums.  Mixed
+// path: pass 1 (FP32 iterations, rounding-level acceptance of stalled roots)
+// over every listed frequency, whose items still at the cap mark their
+// frequency for pass 2 (FP64 iterations, sel_mode 2: those frequencies only).
+// FP64 path: pass 2 over every listed frequency (sel_mode 0).  Both passes
+// iterate up to redo_maxit.
+void resolve_settings(ftp_plan_t P, RootsArgs& a, int* marks, int pass, int sel_mode) {
+  a.resolve_pass = pass;
+  a.sel_mark = marks;
   a.sel_mode = sel_mode;
-  if (sel_mode != 1) a.maxit = P->redo_maxit;
+  a.maxit = P->redo_maxit;
 }
 
 ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int Hs, int64_t nf,
                      const int* nf_dev, const int* kmap, bool collect_redo, const double2* alpha,
                      const int* rows, int ntpl, double* const* o, uint8_t* flags,
                      int64_t out_stride, int64_t out_elems, int* launches, bool time_first = false,
-                     int sel_mode = -1) {
+                     int resolve_pass = 0, int sel_mode = 0) {
   RootsArgs a{};
   if (time_first && P->timing && !P->in_batch && P->fev_used < kMaxH &&
       P->fev[2 * P->fev_used]) {
@@ -619,7 +623,7 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
     a.list_nonconv = 1;
   }
   solver_settings(P, a);
-  if (sel_mode >= 0) resolve_settings(P, a, P->d_redo_mark, sel_mode);
+  if (resolve_pass) resolve_settings(P, a, P->d_redo_mark, resolve_pass, sel_mode);
   FTP_CK(cudaMemsetAsync(P->d_queue, 0, sizeof(unsigned long long), P->stream));
   const int r = launch_roots(kind, a, P->num_sms, P->stream);
   if (r == -1) return FTP_ERR_UNSUPPORTED;
@@ -635,8 +639,9 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
 // where clustered phases make MM a small difference of O(1) sums) are then
 // recomputed from direct FP64 sums with the same kernel (FP32 Aberth on the
 // mixed path, FP64 Aberth on the FP64 path); frequencies where an item hit
-// the Aberth iteration cap are recomputed from direct FP64 sums with FP64
-// Aberth iterations and the larger cap redo_maxit.
+// the Aberth iteration cap are recomputed the same way with the larger cap
+// redo_maxit and a rounding-level acceptance of stalled roots, and on the
+// mixed path items still at the cap then once more with FP64 iterations.
 ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double* ddy,
                  int64_t nobs, double df, int64_t k0, int64_t nf, int Hs,
                  const std::vector<HGroup>& groups, const double2* alpha, const int* rows,
@@ -659,18 +664,18 @@ ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double
   launch_direct_sums(dt, dyv, ddy, nobs, P->d_moments, P->d_status, df, k0, P->d_redo_list,
                      P->d_redo_count, (int)nf, Hs, P->nf_pad, P->d_redo_sums,
                      (int64_t)3 * P->max_H * P->nf_pad, P->d_status, P->stream);
-  *launches += 1;
-  // mixed path: FP32 Aberth for the ill-conditioned frequencies, FP64
-  // Aberth for those with a cap hit; FP64 path: FP64 Aberth for all
+  *launches += 2;  // zeroing + direct sums
+  // mixed path: FP32 iterations for every listed frequency, then FP64
+  // iterations for those still at the cap; FP64 path: FP64 for all
   const int passes = P->mixed ? 2 : 1;
   for (int pass = 0; pass < passes; ++pass) {
-    const RootsKind rk = (P->mixed && pass == 0) ? ROOTS_REDO : ROOTS_FP64;
-    const int sel = P->mixed ? pass + 1 : 0;
+    const bool fp32 = P->mixed && pass == 0;
+    const RootsKind rk = fp32 ? ROOTS_REDO : ROOTS_FP64;
     for (const HGroup& g : groups) {
       ftp_status st = run_roots(P, rk, P->d_redo_sums, g.H, Hs, nf, P->d_redo_count,
                                 P->d_redo_list, false, alpha + (size_t)g.first * kMaxH,
                                 row0 ? row0 : rows + g.first, g.count, o, flags, nf, out_elems,
-                                launches, false, sel);
+                                launches, false, fp32 ? 1 : 2, P->mixed && !fp32 ? 2 : 0);
       if (st != FTP_OK) return st;
     }
   }
@@ -1022,10 +1027,11 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
     const int ncc = (int)(ch.c1 - ch.c0);
     const CurveDesc* dcur = d_curves + ch.c0;
     launch_direct_sums_batch(dcur, ncc, P->d_bmom, P->d_status, P->d_blist, P->d_bcount,
-                             kBatchRedoCap, kBatchRedoStride, P->d_bredo_sums,
+                             kBatchRedoCap, P->max_nobs, P->max_H, kBatchRedoStride,
+                             P->d_bredo_sums,
                              (int64_t)3 * P->max_H * kBatchRedoStride, P->d_bslot_curve,
                              P->d_status, s);
-    *launches += 1;
+    *launches += 2;  // zeroing + direct sums
     const int passes = P->mixed ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass)
     for (const BLaunch& L : ch.launches) {
@@ -1054,7 +1060,8 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
       a.queue = P->d_queue;
       a.redo_cap = kBatchRedoCap;
       solver_settings(P, a);
-      resolve_settings(P, a, P->d_bmark, P->mixed ? pass + 1 : 0);
+      const bool fp32 = P->mixed && pass == 0;
+      resolve_settings(P, a, P->d_bmark, fp32 ? 1 : 2, P->mixed && !fp32 ? 2 : 0);
       a.segs = d_segs + L.seg_first;
       a.seg_units = d_units + L.units_first;
       a.nseg = L.nseg;

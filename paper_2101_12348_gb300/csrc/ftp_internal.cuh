@@ -48,9 +48,10 @@ enum : int {
 };
 
 // Re-solve marks (one int per frequency): listed, list full (the frequency
-// keeps its first result), and re-solve with FP64 Aberth iterations because
-// an item of the frequency hit the iteration cap.
-enum : int { MARK_LISTED = 1, MARK_OVERFLOW = 2, MARK_FP64 = 4 };
+// keeps its first result), listed because an item hit the main pass's
+// iteration cap, and still at the cap after the FP32 re-solve (then re-solved
+// once more with FP64 Aberth iterations).
+enum : int { MARK_LISTED = 1, MARK_OVERFLOW = 2, MARK_CAP = 4, MARK_FP64 = 8 };
 
 // Default polls of a bounded mbarrier wait in the roots kernels.
 constexpr int kWaitPolls = 1 << 20;
@@ -173,10 +174,12 @@ void launch_prep_one(const PrepCurve& pc, double* moments, int* tile_cnt, int* t
 void launch_redo_overflow(const CurveDesc* curves, int ncurves, const int* marks, int64_t nmarks,
                           const int* count, int cap, uint8_t* flags, cudaStream_t s);
 
+// max_n bounds the curves' observation counts and Hs_max their harmonics.
 void launch_direct_sums_batch(const CurveDesc* curves, int ncurves, const double* moments,
                               const int* status, const int* list, const int* count, int cap,
-                              int64_t stride, double2* sums, int64_t sums_elems, int* slot_curve,
-                              int* status_rw, cudaStream_t s);
+                              int64_t max_n, int Hs_max, int64_t stride, double2* sums,
+                              int64_t sums_elems, int* slot_curve, int* status_rw,
+                              cudaStream_t s);
 
 // Steps (b)-(c): assembly, roots, candidates, polish.
 //
@@ -235,13 +238,14 @@ struct RootsArgs {
   int wait_polls;     // polls of each bounded mbarrier wait (>= 1; kWaitPolls by default)
   int skip_copies;    // fault injection: no sum row is ever copied, so every wait runs out
   // main pass: a frequency with an item that hit the iteration cap goes on
-  // the re-solve list with MARK_FP64 (needs redo_list)
+  // the re-solve list with MARK_CAP (needs redo_list)
   int list_nonconv;
-  // re-solve pass: items get FTP_FLAG_RESOLVED and cap hits count as final;
-  // sel_mark / sel_mode restrict the pass to listed frequencies without
-  // (sel_mode 1) or with (sel_mode 2) MARK_FP64 (nullable: every one)
+  // re-solve pass: items get FTP_FLAG_RESOLVED; resolve_pass 1: an item
+  // still at the cap marks its frequency MARK_FP64 in sel_mark for a later
+  // FP64 pass; resolve_pass 2: cap hits are final.  sel_mode 2 restricts
+  // the pass to listed frequencies marked MARK_FP64 (0: every one).
   int resolve_pass;
-  const int* sel_mark;
+  int* sel_mark;
   int sel_mode;
   // batched launches (segs != nullptr): `moments` holds MO_WORDS doubles per
   // curve, outputs are addressed through the segments, and re-solve marks and

@@ -609,55 +609,91 @@ __global__ void __launch_bounds__(256) gather_kernel(const typename C2<R>::type*
 // for listed frequency index k, f = (k0 + k) df,
 //   Z_h = sum_i w_i e^{i h 2 pi f t_i} (h <= 2 Hs),  Y_h = sum_i w_i (y_i - ybar) e^{...} (h <= Hs),
 // with the phase f t_i reduced modulo one cycle in FP64 and the harmonics
-// formed by repeated multiplication.  One CTA per listed frequency; each warp
-// reduces its lanes' terms with shuffles into shared accumulators.
-//
-// direct_sums_block: the block-wide sums of one curve at frequency f into
-// acc[3 Hs] (Z_1..Z_2Hs, then Y_1..Y_Hs); acc must be zero on entry and every
-// thread of the block calls it.
-__device__ void direct_sums_block(const double* __restrict__ t, const double* __restrict__ y,
-                                  const double* __restrict__ dy, int64_t n, double ybar,
-                                  double wsum, bool unit, double f, int Hs, double2* acc) {
+// formed by repeated multiplication.  A listed frequency's observations are
+// cut into chunks of kDirectChunk; a work item is one (frequency, chunk)
+// pair, so even a single listed frequency spreads over many SMs.  Each thread
+// sums the terms of its kDirectPerThread observations in registers, each warp
+// reduces them with shuffles into the CTA's shared accumulators, and the CTA
+// adds those to the frequency's sums in global memory (FP64 atomics; the
+// sums are zeroed by a first launch).
+constexpr int kDirectThreads = 256;
+constexpr int kDirectPerThread = 4;
+constexpr int kDirectChunk = kDirectThreads * kDirectPerThread;
+
+// The chunk of observations [i0, i0 + kDirectChunk) of one curve at frequency
+// f, added into acc[3 Hs] (Z_1..Z_2Hs, then Y_1..Y_Hs); every thread of the
+// CTA calls it.
+__device__ void direct_sums_chunk(const double* __restrict__ t, const double* __restrict__ y,
+                                  const double* __restrict__ dy, int64_t n, int64_t i0,
+                                  double ybar, double wsum, bool unit, double f, int Hs,
+                                  double2* acc) {
   const int lane = threadIdx.x & 31;
-  for (int64_t base = 0; base < n; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    double w = 0.0, r = 0.0, c1 = 1.0, s1 = 0.0;
+  double w[kDirectPerThread], r[kDirectPerThread], c1[kDirectPerThread], s1[kDirectPerThread];
+  double pc[kDirectPerThread], ps[kDirectPerThread];  // e^{i h phi} of each observation
+#pragma unroll
+  for (int j = 0; j < kDirectPerThread; ++j) {
+    const int64_t i = i0 + threadIdx.x + (int64_t)j * kDirectThreads;
+    w[j] = 0.0;
+    r[j] = 0.0;
+    c1[j] = 1.0;
+    s1[j] = 0.0;
     if (i < n) {
       const double si = dy[i];
-      w = (unit ? 1.0 : 1.0 / (si * si)) / wsum;
-      r = w * (y[i] - ybar);
+      w[j] = (unit ? 1.0 : 1.0 / (si * si)) / wsum;
+      r[j] = w[j] * (y[i] - ybar);
       double cyc = f * t[i];
       cyc -= floor(cyc);
-      sincospi(2.0 * cyc, &s1, &c1);
+      sincospi(2.0 * cyc, &s1[j], &c1[j]);
     }
-    double pc = c1, ps = s1;  // e^{i h phi}
-    for (int h = 1; h <= 2 * Hs; ++h) {
-      double zx = w * pc, zy = w * ps, yx = r * pc, yy = r * ps;
+    pc[j] = c1[j];
+    ps[j] = s1[j];
+  }
+  for (int h = 1; h <= 2 * Hs; ++h) {
+    double zx = 0.0, zy = 0.0, yx = 0.0, yy = 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        zx += __shfl_xor_sync(0xffffffffu, zx, o);
-        zy += __shfl_xor_sync(0xffffffffu, zy, o);
-        if (h <= Hs) {
-          yx += __shfl_xor_sync(0xffffffffu, yx, o);
-          yy += __shfl_xor_sync(0xffffffffu, yy, o);
-        }
+    for (int j = 0; j < kDirectPerThread; ++j) {
+      zx = fma(w[j], pc[j], zx);
+      zy = fma(w[j], ps[j], zy);
+      yx = fma(r[j], pc[j], yx);
+      yy = fma(r[j], ps[j], yy);
+      const double nc = pc[j] * c1[j] - ps[j] * s1[j];
+      ps[j] = pc[j] * s1[j] + ps[j] * c1[j];
+      pc[j] = nc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      zx += __shfl_xor_sync(0xffffffffu, zx, o);
+      zy += __shfl_xor_sync(0xffffffffu, zy, o);
+      if (h <= Hs) {
+        yx += __shfl_xor_sync(0xffffffffu, yx, o);
+        yy += __shfl_xor_sync(0xffffffffu, yy, o);
       }
-      if (lane == 0) {
-        atomicAdd(&acc[h - 1].x, zx);
-        atomicAdd(&acc[h - 1].y, zy);
-        if (h <= Hs) {
-          atomicAdd(&acc[2 * Hs + h - 1].x, yx);
-          atomicAdd(&acc[2 * Hs + h - 1].y, yy);
-        }
+    }
+    if (lane == 0) {
+      atomicAdd(&acc[h - 1].x, zx);
+      atomicAdd(&acc[h - 1].y, zy);
+      if (h <= Hs) {
+        atomicAdd(&acc[2 * Hs + h - 1].x, yx);
+        atomicAdd(&acc[2 * Hs + h - 1].y, yy);
       }
-      const double nc = pc * c1 - ps * s1;
-      ps = pc * s1 + ps * c1;
-      pc = nc;
     }
   }
 }
 
-__global__ void __launch_bounds__(256) direct_sums_kernel(
+// Zero the sums of the listed slots (rows of `stride` elements).
+__global__ void __launch_bounds__(256) zero_listed_kernel(const int* __restrict__ count, int cap,
+                                                          int rows, int64_t stride,
+                                                          double2* __restrict__ sums,
+                                                          int64_t sums_elems) {
+  const int64_t total = min(*count, cap);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total * rows;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = (q / total) * stride + q % total;
+    if (e < sums_elems) sums[e] = make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void __launch_bounds__(kDirectThreads) direct_sums_kernel(
     const double* __restrict__ t, const double* __restrict__ y, const double* __restrict__ dy,
     int64_t n, const double* __restrict__ moments, const int* __restrict__ status, double df,
     int64_t k0, const int* __restrict__ list, const int* __restrict__ count, int cap, int Hs,
@@ -665,34 +701,42 @@ __global__ void __launch_bounds__(256) direct_sums_kernel(
   __shared__ double2 acc[3 * kMaxH];
   if (status[ST_CODE] != DEV_OK) return;
   if (!FTP_DCHECK(status_rw, Hs >= 1 && Hs <= kMaxH, 31, Hs, kMaxH)) return;
-  const int total = min(*count, cap);
+  const int64_t total = min(*count, cap);
+  const int64_t nchunk = (n + kDirectChunk - 1) / kDirectChunk;
   const double ybar = moments[MO_YBAR], wsum = moments[MO_WSUM];
   const bool unit = moments[MO_UNIT] != 0.0;
-  for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
+  for (int64_t item = blockIdx.x; item < total * nchunk; item += gridDim.x) {
+    const int64_t idx = item / nchunk, chunk = item % nchunk;
     if (!FTP_DCHECK(status_rw, list[idx] >= 0 && list[idx] < nf_pad, 32, list[idx], nf_pad)) break;
     const double f = (double)(k0 + list[idx]) * df;
     for (int q = threadIdx.x; q < 3 * Hs; q += blockDim.x) acc[q] = make_double2(0.0, 0.0);
     __syncthreads();
-    direct_sums_block(t, y, dy, n, ybar, wsum, unit, f, Hs, acc);
+    direct_sums_chunk(t, y, dy, n, chunk * kDirectChunk, ybar, wsum, unit, f, Hs, acc);
     __syncthreads();
     for (int q = threadIdx.x; q < 3 * Hs; q += blockDim.x)
-      if (FTP_DCHECK(status_rw, (int64_t)q * nf_pad + idx < sums_elems, 33, q, idx))
-        sums[(int64_t)q * nf_pad + idx] = acc[q];
+      if (FTP_DCHECK(status_rw, (int64_t)q * nf_pad + idx < sums_elems, 33, q, idx)) {
+        atomicAdd(&sums[(int64_t)q * nf_pad + idx].x, acc[q].x);
+        atomicAdd(&sums[(int64_t)q * nf_pad + idx].y, acc[q].y);
+      }
     __syncthreads();
   }
 }
 
 // Batched form: slot idx holds a global frequency index g of the batch; its
-// curve is the last one with redo_base <= g.
-__global__ void __launch_bounds__(256) direct_sums_batch_kernel(
+// curve is the last one with redo_base <= g.  Work items are (slot, chunk)
+// over the chunks of the longest curve (max_n observations); chunks past a
+// curve's end are skipped.
+__global__ void __launch_bounds__(kDirectThreads) direct_sums_batch_kernel(
     const CurveDesc* __restrict__ curves, int ncurves, const double* __restrict__ moments,
     const int* __restrict__ status, const int* __restrict__ list, const int* __restrict__ count,
-    int cap, int64_t stride, double2* __restrict__ sums, int64_t sums_elems,
+    int cap, int64_t max_n, int64_t stride, double2* __restrict__ sums, int64_t sums_elems,
     int* __restrict__ slot_curve, int* status_rw) {
   __shared__ double2 acc[3 * kMaxH];
   if (status[ST_CODE] != DEV_OK) return;
-  const int total = min(*count, cap);
-  for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
+  const int64_t total = min(*count, cap);
+  const int64_t nchunk = (max_n + kDirectChunk - 1) / kDirectChunk;
+  for (int64_t item = blockIdx.x; item < total * nchunk; item += gridDim.x) {
+    const int64_t idx = item / nchunk, chunk = item % nchunk;
     const int64_t g = list[idx];
     int lo = 0, hi = ncurves;
     while (hi - lo > 1) {
@@ -701,6 +745,8 @@ __global__ void __launch_bounds__(256) direct_sums_batch_kernel(
       else hi = mid;
     }
     const CurveDesc cd = curves[lo];
+    if (chunk == 0 && threadIdx.x == 0) slot_curve[idx] = lo;
+    if (chunk * kDirectChunk >= cd.n) continue;  // uniform over the CTA
     const int64_t k = g - cd.redo_base;
     if (!FTP_DCHECK(status_rw, k >= 0 && k < cd.nf, 34, k, cd.nf) ||
         !FTP_DCHECK(status_rw, cd.Hs >= 1 && cd.Hs <= kMaxH, 35, cd.Hs, kMaxH))
@@ -709,13 +755,14 @@ __global__ void __launch_bounds__(256) direct_sums_batch_kernel(
     const double f = (double)(cd.k0 + k) * cd.df;
     for (int q = threadIdx.x; q < 3 * cd.Hs; q += blockDim.x) acc[q] = make_double2(0.0, 0.0);
     __syncthreads();
-    direct_sums_block(cd.t, cd.y, cd.dy, cd.n, mo[MO_YBAR], mo[MO_WSUM], mo[MO_UNIT] != 0.0, f,
-                      cd.Hs, acc);
+    direct_sums_chunk(cd.t, cd.y, cd.dy, cd.n, chunk * kDirectChunk, mo[MO_YBAR], mo[MO_WSUM],
+                      mo[MO_UNIT] != 0.0, f, cd.Hs, acc);
     __syncthreads();
     for (int q = threadIdx.x; q < 3 * cd.Hs; q += blockDim.x)
-      if (FTP_DCHECK(status_rw, (int64_t)q * stride + idx < sums_elems, 36, q, idx))
-        sums[(int64_t)q * stride + idx] = acc[q];
-    if (threadIdx.x == 0) slot_curve[idx] = lo;
+      if (FTP_DCHECK(status_rw, (int64_t)q * stride + idx < sums_elems, 36, q, idx)) {
+        atomicAdd(&sums[(int64_t)q * stride + idx].x, acc[q].x);
+        atomicAdd(&sums[(int64_t)q * stride + idx].y, acc[q].y);
+      }
     __syncthreads();
   }
 }
@@ -770,11 +817,11 @@ void launch_direct_sums(const double* t, const double* y, const double* dy, int6
                         const double* moments, const int* status, double df, int64_t k0,
                         const int* list, const int* count, int cap, int Hs, int64_t nf_pad,
                         double2* sums, int64_t sums_elems, int* status_rw, cudaStream_t s) {
-  const int gmax = 2 * current_sms();
-  int grid = cap < gmax ? cap : gmax;
-  if (grid < 1) grid = 1;
-  direct_sums_kernel<<<grid, 256, 0, s>>>(t, y, dy, n, moments, status, df, k0, list, count, cap,
-                                          Hs, nf_pad, sums, sums_elems, status_rw);
+  const int sms = current_sms();
+  zero_listed_kernel<<<sms, 256, 0, s>>>(count, cap, 3 * Hs, nf_pad, sums, sums_elems);
+  direct_sums_kernel<<<4 * sms, kDirectThreads, 0, s>>>(t, y, dy, n, moments, status, df, k0,
+                                                        list, count, cap, Hs, nf_pad, sums,
+                                                        sums_elems, status_rw);
 }
 
 __global__ void __launch_bounds__(256) redo_overflow_kernel(const CurveDesc* __restrict__ curves,
@@ -808,14 +855,15 @@ void launch_redo_overflow(const CurveDesc* curves, int ncurves, const int* marks
 
 void launch_direct_sums_batch(const CurveDesc* curves, int ncurves, const double* moments,
                               const int* status, const int* list, const int* count, int cap,
-                              int64_t stride, double2* sums, int64_t sums_elems, int* slot_curve,
-                              int* status_rw, cudaStream_t s) {
-  const int gmax = 2 * current_sms();
-  int grid = cap < gmax ? cap : gmax;
-  if (grid < 1) grid = 1;
-  direct_sums_batch_kernel<<<grid, 256, 0, s>>>(curves, ncurves, moments, status, list, count,
-                                                cap, stride, sums, sums_elems, slot_curve,
-                                                status_rw);
+                              int64_t max_n, int Hs_max, int64_t stride, double2* sums,
+                              int64_t sums_elems, int* slot_curve, int* status_rw,
+                              cudaStream_t s) {
+  const int sms = current_sms();
+  zero_listed_kernel<<<sms, 256, 0, s>>>(count, cap, 3 * Hs_max, stride, sums, sums_elems);
+  direct_sums_batch_kernel<<<4 * sms, kDirectThreads, 0, s>>>(curves, ncurves, moments, status,
+                                                              list, count, cap, max_n, stride,
+                                                              sums, sums_elems, slot_curve,
+                                                              status_rw);
 }
 
 template <typename R>

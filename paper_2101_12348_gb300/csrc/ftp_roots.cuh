@@ -62,6 +62,11 @@ template <typename S2, typename R, int H, int G>
 struct Cfg {
   using R2 = typename R2T<R>::type;
   static constexpr bool kFast = sizeof(R) == 4;   // FP32 Aberth
+  // Rounding-level acceptance of stalled roots during the iterations (from
+  // the 12th, every 4th): every kernel except the mixed path's main one (FP32
+  // sums and iterations), whose hot loop stays as it is; that kernel checks
+  // its items only once they hit the cap.
+  static constexpr bool kAccept = !kFast || sizeof(S2) == 16;
   // FP64-class steps: float-float on the mixed path (FP32 sums and Aberth),
   // native FP64 on the FP64 path and the re-solve pass (FP64 sums)
   static constexpr bool kDD = kFast && sizeof(S2) == 8;
@@ -244,6 +249,35 @@ __device__ __forceinline__ f2p sub2(f2p a, f2p b) {
   return d;
 }
 
+// A root whose correction has stalled is accepted when F's value there is
+// at the rounding level of its evaluation: |F(z)| <= 8 D eps
+// sum_k |F_k| |z|^k (a backward error of a few units of the working
+// precision in the coefficients), so that no further digits are obtainable in
+// that precision - the case of clustered and multiple roots, whose Newton
+// corrections stall at about sqrt(eps) instead of meeting the tolerance.
+// Outside the unit disc F is evaluated at u = 1/conj(z): F is
+// anti-self-inversive, so |F(z)| = |z|^D |F(u)| and the sum of |F_k||z|^k
+// scales alike.  Out of line: it runs only for roots still unconverged after
+// many iterations, and the hot loops keep their registers.
+template <int D, typename R, typename R2>
+__device__ __noinline__ bool pseudo_zero(R2 z, const R2* Fs) {
+  const R m2 = cabs2(z);
+  const R inv = m2 > R(1) ? R(1) / m2 : R(1);
+  const R2 u = mk<R2>(z.x * inv, z.y * inv);
+  const R au = sqrt(cabs2(u));
+  R2 p = mk<R2>(0, 0);
+  R pa = R(0);
+#pragma unroll 1
+  for (int c = D; c >= 0; --c) {
+    const R2 f = Fs[c];
+    p = cfma(p, u, f);
+    pa = fma(pa, au, sqrt(cabs2(f)));
+  }
+  const R eps = sizeof(R) == 4 ? R(5.9604645e-8) : R(1.1102230246251565e-16);
+  const R bound = R(8 * D) * eps * pa;
+  return isfinite(pa) && cabs2(p) <= bound * bound;
+}
+
 // ------------------------------------------------------------ Aberth step
 // One Aberth-Ehrlich iteration for the NS root slots of a lane.  Slot r holds
 // root idx[r] of the item (idx < 0: an empty slot, marked converged), z[r] its
@@ -392,11 +426,22 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
 // Iterations over NS slots per lane until every root converged (false) or,
 // if NT < NS, until every group of the warp has at most NT * G unconverged
 // roots (true: time to compact).
-template <int G, int NS, int NT, int D, bool kFast, typename R, typename R2>
+template <int G, int NS, int NT, int D, bool kAccept, typename R, typename R2>
 __device__ __forceinline__ bool aberth_run(R2 (&z)[NS], bool (&conv)[NS], const int (&idx)[NS],
                                            const R2* Fs, R2* Zs, R tol, int& iters, int maxit) {
 #pragma unroll 1
   for (; iters < maxit; ++iters) {
+    if constexpr (kAccept) {
+      // from the 12th iteration on, every 4th, a root that is a zero of F to
+      // the working precision is accepted - the corrections of clustered and
+      // multiple roots stall near sqrt(eps) and would otherwise run to the
+      // cap (well-separated roots converge in ~11)
+      if (iters >= 12 && (iters & 3) == 0) {
+#pragma unroll  // static indices keep z and conv in registers
+        for (int r = 0; r < NS; ++r)
+          if (!conv[r] && idx[r] >= 0 && pseudo_zero<D, R>(z[r], Fs)) conv[r] = true;
+      }
+    }
     int nact = 0;
 #pragma unroll
     for (int r = 0; r < NS; ++r) nact += conv[r] ? 0 : 1;
@@ -413,7 +458,7 @@ __device__ __forceinline__ bool aberth_run(R2 (&z)[NS], bool (&conv)[NS], const 
       for (int sh = G; sh < 32; sh <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, sh));
       if (wmax <= NT * G) return true;
     }
-    aberth_step<NS, D, kFast>(z, conv, idx, Fs, Zs, tol);
+    aberth_step<NS, D, sizeof(R) == 4>(z, conv, idx, Fs, Zs, tol);
   }
   return false;
 }
@@ -448,35 +493,6 @@ __device__ __forceinline__ void compact_roots(const bool (&conv)[NS], const int 
     c2[k] = i2[k] < 0;
   }
   __syncwarp();
-}
-
-// A root left unconverged at the iteration cap is accepted when F's value
-// there is at the rounding level of its evaluation: |F(z)| <= 8 D eps
-// sum_k |F_k| |z|^k (a backward error of a few units of the working
-// precision in the coefficients), so that no further digits are obtainable in
-// that precision - the case of clustered and multiple roots, whose Newton
-// corrections stall at about sqrt(eps) instead of meeting the tolerance.
-// Outside the unit disc F is evaluated at u = 1/conj(z): F is
-// anti-self-inversive, so |F(z)| = |z|^D |F(u)| and the sum of |F_k||z|^k
-// scales alike.  Out of line: it runs only for items that hit the cap, and
-// the hot loops keep their registers.
-template <int D, typename R, typename R2>
-__device__ __noinline__ bool pseudo_zero(R2 z, const R2* Fs) {
-  const R m2 = cabs2(z);
-  const R inv = m2 > R(1) ? R(1) / m2 : R(1);
-  const R2 u = mk<R2>(z.x * inv, z.y * inv);
-  const R au = sqrt(cabs2(u));
-  R2 p = mk<R2>(0, 0);
-  R pa = R(0);
-#pragma unroll 1
-  for (int c = D; c >= 0; --c) {
-    const R2 f = Fs[c];
-    p = cfma(p, u, f);
-    pa = fma(pa, au, sqrt(cabs2(f)));
-  }
-  const R eps = sizeof(R) == 4 ? R(5.9604645e-8) : R(1.1102230246251565e-16);
-  const R bound = R(8 * D) * eps * pa;
-  return isfinite(pa) && cabs2(p) <= bound * bound;
 }
 
 // ------------------------------------------------------------ group reductions
@@ -798,10 +814,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
     const S2* st = stage + (size_t)buf * (C::STAGE_BYTES / sizeof(S2));
     const int64_t k = redo_pass ? cu.kfirst : cu.kfirst + gi;
     bool valid = unit_ok && (redo_pass ? gi == 0 : k < seg_nf);
-    if (valid && a.sel_mark) {  // re-solve pass restricted to one kind of listed frequency
-      const bool fp64 = (a.sel_mark[a.kmap[k]] & MARK_FP64) != 0;
-      valid = (a.sel_mode == 2) == fp64;
-    }
+    if (valid && a.sel_mode == 2)  // FP64 re-solve: only frequencies still at the cap
+      valid = (a.sel_mark[a.kmap[k]] & MARK_FP64) != 0;
 
     R amax2 = R(0), bmax2 = R(0);
     if (a.coef_mode) {
@@ -1083,19 +1097,19 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       int idx[RR];
 #pragma unroll
       for (int r = 0; r < RR; ++r) idx[r] = r * G + gl < D ? r * G + gl : -1;
-      if (aberth_run<G, RR, RS, D, kFast>(z, conv, idx, Fs, Zs, tol, iters, a.maxit)) {
+      if (aberth_run<G, RR, RS, D, C::kAccept>(z, conv, idx, Fs, Zs, tol, iters, a.maxit)) {
         if constexpr (RS < RR) {
           R2 z2[RS];
           bool c2[RS];
           int i2[RS];
           compact_roots<G, RR, RS>(conv, idx, act, Zs, gl, z2, c2, i2);
-          if (aberth_run<G, RS, RT, D, kFast>(z2, c2, i2, Fs, Zs, tol, iters, a.maxit)) {
+          if (aberth_run<G, RS, RT, D, C::kAccept>(z2, c2, i2, Fs, Zs, tol, iters, a.maxit)) {
             if constexpr (RT < RS) {
               R2 z3[RT];
               bool c3[RT];
               int i3[RT];
               compact_roots<G, RS, RT>(c2, i2, act, Zs, gl, z3, c3, i3);
-              aberth_run<G, RT, RT, D, kFast>(z3, c3, i3, Fs, Zs, tol, iters, a.maxit);
+              aberth_run<G, RT, RT, D, C::kAccept>(z3, c3, i3, Fs, Zs, tol, iters, a.maxit);
 #pragma unroll
               for (int k = 0; k < RT; ++k) lane_nc = lane_nc || !c3[k];
             }
@@ -1110,18 +1124,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       }
     }
     bool nonconv = gor<G>(lane_nc) && !constant;
-    if constexpr (!kFast) {
-      // FP64 iterations (the FP64 path and the re-solve of cap hits): at the
-      // cap keep the flag only if some root of the item is not a zero of F
-      // to the working precision (the lanes split the roots).  The FP32
-      // kernels leave it out of their code: their cap hits are re-solved
-      // with FP64 iterations.
-      if (__any_sync(0xffffffffu, nonconv)) {
-        bool bad = false;
-        if (nonconv)
-          for (int i = gl; i < D; i += G) bad = bad || !pseudo_zero<D, R>(Zs[i], Fs);
-        nonconv = gor<G>(bad);
-      }
+    if (__any_sync(0xffffffffu, nonconv)) {
+      // at the cap keep the flag only if some root of the item is not a zero
+      // of F to the working precision (the lanes split the roots): stalled
+      // clusters are accepted here and need no re-solve
+      bool bad = false;
+      if (nonconv)
+        for (int i = gl; i < D; i += G) bad = bad || !pseudo_zero<D, R>(Zs[i], Fs);
+      nonconv = gor<G>(bad);
     }
 
     // ---- candidates: P at every root scaled onto |psi| = 1 (working precision).
@@ -1419,23 +1429,28 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
       // mark gets MARK_OVERFLOW and a later pass flags its items.  Without a
       // list (a call that cannot re-solve) an item over the error threshold
       // is flagged unresolved.
-      const bool fp64 = nonconv && a.list_nonconv;
-      // a cap hit is final in a re-solve pass and where no re-solve follows
-      st_final += (nonconv && (a.resolve_pass || !(a.list_nonconv && a.redo_list))) ? 1 : 0;
+      const bool cap = nonconv && a.list_nonconv;
+      // a cap hit is final in the last re-solve pass and where no re-solve
+      // follows; in the FP32 re-solve pass it sends its frequency on to the
+      // FP64 one
+      st_final += (nonconv && (a.resolve_pass == 2 ||
+                               (!a.resolve_pass && !(a.list_nonconv && a.redo_list)))) ? 1 : 0;
+      if (nonconv && a.resolve_pass == 1 && a.sel_mark)
+        atomicOr(&a.sel_mark[a.kmap[k]], MARK_FP64);
       bool unresolved = false;
-      if ((redo || fp64) && a.redo_list) {
+      if ((redo || cap) && a.redo_list) {
         if (FTP_DCHECK(a.status, ridx < a.redo_marks, 23, ridx, a.redo_marks)) {
           if (atomicCAS(&a.redo_mark[ridx], 0, MARK_LISTED) == 0) {
             const int slot = atomicAdd(a.redo_count, 1);
             if (slot < a.redo_cap) {
               a.redo_list[slot] = (int)ridx;
               ++st_redo;
-              st_redo_nc += fp64 ? 1 : 0;
             } else {
               atomicOr(&a.redo_mark[ridx], MARK_OVERFLOW);
             }
           }
-          if (fp64) atomicOr(&a.redo_mark[ridx], MARK_FP64);
+          // counted once per frequency: by the item that sets the bit
+          if (cap && (atomicOr(&a.redo_mark[ridx], MARK_CAP) & MARK_CAP) == 0) ++st_redo_nc;
         }
       } else if (redo && !a.resolve_pass) {
         unresolved = true;

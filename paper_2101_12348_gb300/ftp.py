@@ -48,7 +48,7 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune",
            "ftp_set_positive_amplitude", "ftp_multiband_periodogram",
            "ftp_shared_multiband", "ftp_roots_first_phase_ms", "ftp_set_solver_limits",
-           "ftp_set_fault_injection")
+           "ftp_set_fault_injection", "ftp_alu_peak")
 
 
 class FtpGrid(C.Structure):
@@ -95,6 +95,7 @@ def load(path: str | None = None) -> C.CDLL:
                                      C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.ftp_set_solver_limits.argtypes = [vp, i32, i32, i32]
     lib.ftp_set_fault_injection.argtypes = [vp, i32]
+    lib.ftp_alu_peak.argtypes = [i32, i32, i32, C.POINTER(dbl), C.POINTER(C.c_float)]
     lib.ftp_set_timing.argtypes = [vp, i32]
     lib.ftp_periodogram_sums_noalloc.argtypes = [vp, i64, i32, i64, i32, dbl, dbl,
                                                  C.POINTER(FtpTemplate), i32, vp, vp, vp, vp,
@@ -408,6 +409,14 @@ def ftp_set_solver_limits(plan: int, maxit: int = 0, redo_maxit: int = 0,
                           wait_polls: int = 0) -> None:
     _check(load().ftp_set_solver_limits(plan, int(maxit), int(redo_maxit), int(wait_polls)),
            "ftp_set_solver_limits")
+
+
+def ftp_alu_peak(device: int, kind: int, iters: int) -> tuple:
+    """(flops, ms) of one FMA-chain launch: kind 0 FP32, 1 FP32 pairs, 2 FP64."""
+    f, ms = C.c_double(), C.c_float()
+    _check(load().ftp_alu_peak(int(device), int(kind), int(iters), C.byref(f), C.byref(ms)),
+           "ftp_alu_peak")
+    return f.value, float(ms.value)
 
 
 def ftp_set_fault_injection(plan: int, mode: int) -> None:

@@ -263,20 +263,30 @@ def test_screened_batch_equals_exhaustive_where_evaluated(ftp, prec, tol):
     assert evaluated.sum() <= 2 * nsel
 
 
+HELDOUT = 1200
+
+
 def test_screening_gains_over_exhaustive_with_high_recall(ftp):
     """Trained on exact FTP output of one set of curves, the surrogate keeps
-    the best peak of held-out curves (recall) while the exact solve runs on a
-    small fraction of the frequencies; an untrained network keeps fewer."""
+    the best peak of held-out curves (recall >= 0.995, the screening target)
+    while the exact solve runs on a small fraction of the frequencies; an
+    untrained network keeps no more.
+
+    With 1200 held-out curves the bar allows at most 6 misses, so one miss
+    does not decide it: at a true miss rate of 1.5 % (three times the allowed
+    0.5 %) the chance of 6 or fewer misses is about 1e-3 (binomial, mean 18),
+    and at the 0.05 % rate measured on the full screening workload the chance
+    of more than 6 is about 3e-6."""
     H = 4
-    train = synth.survey(ncurves=384, n_bank=8, median_obs=300, min_obs=50, max_obs=3000,
+    train = synth.survey(ncurves=1024, n_bank=8, median_obs=300, min_obs=50, max_obs=3000,
                          f_max=5.0, baseline=(50.0, 400.0), Hs=(H,), seed=404)
-    test = synth.survey(ncurves=256, n_bank=8, median_obs=300, min_obs=50, max_obs=3000,
+    test = synth.survey(ncurves=HELDOUT, n_bank=8, median_obs=300, min_obs=50, max_obs=3000,
                         f_max=5.0, baseline=(50.0, 400.0), Hs=(H,), seed=405)
     gmax = max(train.grids + test.grids, key=lambda g: g.k0 + g.nf)
     nfmax = max(g.nf for g in train.grids + test.grids)
     nmax = int(max(np.max(np.diff(train.obs_off)), np.max(np.diff(test.obs_off))))
     with ftp.Plan(nmax, H, (gmax.df, gmax.k0, nfmax), 8, "mixed") as plan:
-        cap = 4_000_000
+        cap = 12_000_000
         Xt = torch.empty((cap, 2 * H + 2), dtype=torch.float32, device="cuda")
         yt = torch.empty(cap, dtype=torch.float32, device="cuda")
         bank = [(b.c, b.s) for b in train.bank]
@@ -308,8 +318,10 @@ def test_screening_gains_over_exhaustive_with_high_recall(ftp):
         with screen.Surrogate(H, seed=3) as raw:
             r_raw, _ = recall(raw)
         with screen.Surrogate(H, seed=3) as net:
-            net.train(Xt, yt, n, steps=1500, batch=2048, lr=2e-3, seed=9)
+            net.train(Xt, yt, n, steps=3000, batch=2048, lr=2e-3, seed=9)
             r_net, frac = recall(net)
+    print(f"recall {r_net:.4f} on {test.ncurves} held-out curves (untrained {r_raw:.4f}), "
+          f"{frac:.3%} of the frequencies solved exactly")
     assert frac < 0.15, frac
-    assert r_net >= 0.99, (r_net, r_raw)
+    assert r_net >= 0.995, (r_net, r_raw)
     assert r_net >= r_raw

@@ -2,9 +2,9 @@
 
 - An Aberth iteration cap of 1 leaves (nearly) every item unconverged: the
   items are counted, their frequencies re-solved from direct FP64 sums with
-  FP64 iterations (Section 2 needs every stationary point as a candidate, so a
-  root that did not converge is not just reported), and the results meet the
-  oracle's tolerance.
+  the re-solve cap (Section 2 needs every stationary point as a candidate, so
+  a root that did not converge is not just reported), and the results meet
+  the oracle's tolerance.
 - A cap of 1 in the re-solve too leaves FTP_FLAG_NONCONVERGED on the items
   and counts them as still unconverged; the plan works normally afterwards.
 - Fault injection: the roots kernels arm their waits for the staged sum tiles
@@ -63,7 +63,7 @@ def check_parity(r, refs, prec):
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_iteration_cap_hits_are_resolved_in_fp64(ftp, case, prec):
+def test_iteration_cap_hits_are_resolved(ftp, case, prec):
     lc, bank, grid, refs = case
     with ftp.Plan(lc.t.size, 3, (grid.df, grid.k0, grid.nf), 2, prec) as plan:
         plan.set_solver_limits(maxit=1)
