@@ -106,7 +106,9 @@ struct Cfg {
   static constexpr size_t W_MBAR = rup(2 * STAGE_BYTES, 16);             // 2 mbarriers
   static constexpr size_t W_KE = W_MBAR + 16;                            // K_e, e = 0..2H
   static constexpr size_t W_AL = W_KE + NA * 16;                         // alpha_n
-  static constexpr size_t W_GROUPS = rup(W_AL + H * 16, 128);
+  static constexpr size_t W_KER = W_AL + H * 16;                         // K_e, working precision
+  static constexpr size_t W_ALR = W_KER + rup(NA * sizeof(R2), 16);      // alpha_n, working precision
+  static constexpr size_t W_GROUPS = rup(W_ALR + rup(H * sizeof(R2), 16), 128);
   static constexpr size_t WARP_BYTES = rup(W_GROUPS + NGW * GROUP_BYTES, 128) + 16;
   static constexpr size_t SMEM = WARPS * WARP_BYTES;
 };
@@ -591,8 +593,16 @@ __device__ __forceinline__ T trig_eval(const T2* c, int n, T2 psi, T v0) {
 // Each kernel's code is a fraction of the whole, so the warps of an SM, which
 // are at different points of their items, share far fewer instructions in the
 // instruction caches than one fused kernel would make them fetch.
+// Resident CTAs per SM the launch bounds ask for: FP32 kernels 5 (94-96
+// registers), the first kernel at H >= 8 six (80 registers; measured at
+// H = 10: -2.6 %, at H = 6: +1 %), FP64 kernels 3.
+template <typename R, int H, int PH>
+constexpr int roots_min_blocks() {
+  return sizeof(R) == 4 ? ((PH == 1 && H >= 8) ? 6 : 5) : 3;
+}
+
 template <typename S2, typename R, int H, int G, int PH>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(const RootsArgs a) {
+__global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kernel(const RootsArgs a) {
   using namespace wide;
   using C = Cfg<S2, R, H, G>;
   using R2 = typename C::R2;
@@ -613,6 +623,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
   uint64_t* mbar = reinterpret_cast<uint64_t*>(wb + C::W_MBAR);
   WC* KE = reinterpret_cast<WC*>(wb + C::W_KE);
   WC* AL = reinterpret_cast<WC*>(wb + C::W_AL);
+  R2* KER = reinterpret_cast<R2*>(wb + C::W_KER);
+  R2* ALR = reinterpret_cast<R2*>(wb + C::W_ALR);
   const int gl = lane % G, gi = lane / G;
   unsigned char* gb = wb + C::W_GROUPS + (size_t)gi * C::GROUP_BYTES;
   WC* Z64 = reinterpret_cast<WC*>(gb + C::G_Z64);
@@ -792,8 +804,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
           if (n - e >= 1) k = cfma(cscale(al[n - 1], 2.0), cconj(al[n - e - 1]), k);
         }
         KE[e] = mkc(w_of<W>(k.x), w_of<W>(k.y));
+        KER[e] = mk<R2>(k.x, k.y);
       }
-      if (lane < H) AL[lane] = mkc(w_of<W>(al[lane].x), w_of<W>(al[lane].y));
+      if (lane < H) {
+        AL[lane] = mkc(w_of<W>(al[lane].x), w_of<W>(al[lane].y));
+        ALR[lane] = mk<R2>(al[lane].x, al[lane].y);
+      }
       double sa = 0.0;
       for (int n = 0; n < H; ++n) sa += sqrt(cabs2(al[n]));
       sum_abs_alpha = (R)sa;
@@ -869,6 +885,66 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) roots_kernel(cons
               S = c_add<W>(S, c_mulf<W>(c_mul<W>(C64[n], c_conj<W>(C64[n - e])), 2.0f));
           }
           A64[e] = c_add<W>(A64[e], S);
+        }
+      }
+    } else if constexpr (PH == 1 && C::kDD) {
+      // ---- (b) assembly in FP32 for the mixed path's first kernel.  Its final
+      //      polynomial, root search and candidate screening run in FP32, and
+      //      an FP32 assembly errs by ~6e-8 of its terms, below the ~4e-7
+      //      error of the FP32 NFFT sums it starts from; the second kernel
+      //      assembles again in float-float for the polish and the outputs.
+      R2* Zr = reinterpret_cast<R2*>(Z64);
+      R2* Yr = reinterpret_cast<R2*>(Y64);
+      R2* Cr = reinterpret_cast<R2*>(C64);
+      for (int q = gl; q < C::ROWS; q += G) {
+        const S2 v = st[q * NGW + gi];
+        const R2 rv = mk<R2>((R)v.x, (R)v.y);
+        if (q < 2 * H) Zr[q + 1] = rv;
+        else Yr[q - 2 * H + 1] = rv;
+      }
+      if (gl == 0) {
+        Zr[0] = mk<R2>(1, 0);
+        Yr[0] = mk<R2>(0, 0);
+      }
+      __syncwarp();
+      for (int kk = gl; kk <= H; kk += G) {
+        R2 bv = mk<R2>(0, 0), cv = mk<R2>(0, 0);
+        if (kk > 0) {
+          const R2 al = ALR[kk - 1];
+          bv = cmul(al, cconj(Yr[kk]));
+          cv = cmul(al, cconj(Zr[kk]));
+        }
+        Bw[kk] = bv;
+        Cr[kk] = cv;
+        bmax2 = fmax(bmax2, cabs2(bv));
+      }
+      __syncwarp();
+      for (int s = gl; s < C::NSLOT; s += G) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          if (s == 0 && half == 1) break;
+          const int e = (s == 0) ? 0 : (half == 0 ? s : 2 * H + 1 - s);
+          R2 acc;
+          if (e == 0) {
+            R q = R(0);
+            for (int n = 1; n <= H; ++n) q += cabs2(Cr[n]);
+            acc = mk<R2>(KER[0].x - R(2) * q, 0);
+          } else {
+            R2 S = mk<R2>(0, 0);
+            const int nlo = e - H > 1 ? e - H : 1;
+            for (int n = nlo; 2 * n <= e; ++n) {  // sum_{n+m=e} c_n c_m, symmetric
+              const R2 t = cmul(Cr[n], Cr[e - n]);
+              S = (2 * n == e) ? mk<R2>(S.x + t.x, S.y + t.y)
+                               : mk<R2>(fma(R(2), t.x, S.x), fma(R(2), t.y, S.y));
+            }
+            for (int n = e + 1; n <= H; ++n) {  // 2 sum_{n-m=e} c_n conj(c_m)
+              const R2 t = cmul(Cr[n], cconj(Cr[n - e]));
+              S = mk<R2>(fma(R(2), t.x, S.x), fma(R(2), t.y, S.y));
+            }
+            acc = csub(cmul(cconj(Zr[e]), KER[e]), S);
+          }
+          Aw[e] = acc;
+          amax2 = fmax(amax2, cabs2(acc));
         }
       }
     } else {
