@@ -576,6 +576,9 @@ void resolve_settings(ftp_plan_t P, RootsArgs& a, int* marks, int pass, int sel_
   a.sel_mark = marks;
   a.sel_mode = sel_mode;
   a.maxit = P->redo_maxit;
+  // re-solve lists are short (usually empty): one CTA per SM keeps an empty
+  // pass cheap and still runs four warps per SM on a long list
+  a.ctas_per_sm = 1;
 }
 
 ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int Hs, int64_t nf,
