@@ -60,9 +60,10 @@ struct FftEntry {
   size_t work = 0;
 };
 
-// Workspace of one step (a) pipeline: ftp_batch runs the step (a) of
-// several curves at once, one lane each, on their own streams.  Lane 0 is the
-// plan's own workspace and stream; extra lanes own their buffers.
+// Workspace of one step (a) pipeline.  Lane 0 is the plan's own workspace
+// and stream (single curves); ftp_batch runs the batched FFTs of different
+// grid-size classes on the lanes' streams at once, each lane with its own
+// cuFFT plans and work area (extra lanes own only a stream and an event).
 struct SumLane {
   cudaStream_t s = nullptr;
   bool owned = false;  // buffers (and the stream) belong to this lane
@@ -80,6 +81,7 @@ struct SumLane {
   void* fftwork = nullptr;
   size_t fftwork_bytes = 0;
   std::map<int64_t, FftEntry> ffts;
+  std::map<std::pair<int64_t, int>, FftEntry> bffts;  // batched plans by (length, batch)
   cudaEvent_t done = nullptr;  // end of the lane's share of a chunk
 };
 constexpr int kSumLanes = 4;     // default concurrent step (a) lanes of ftp_batch
@@ -180,6 +182,8 @@ struct ftp_plan_s {
   size_t bout_cap = 0;
   uint8_t* d_bflags = nullptr;
   size_t bflags_cap = 0;
+  void* d_bgrid = nullptr;  // NFFT grids of one group of a chunk's curves (batched step (a))
+  size_t bgrid_cap = 0;
   int* d_bmark = nullptr;  // re-solve marks, one per frequency of a chunk
   size_t bmark_cap = 0;
   int* d_blist = nullptr;  // re-solve list [kBatchRedoCap]
@@ -281,6 +285,28 @@ ftp_status dalloc(T** p, size_t count) {
   return cuda_err(cudaMalloc((void**)p, count * sizeof(T)));
 }
 
+// The lane's shared cuFFT work area, grown to plan e's need (a plan being
+// made may need more than the ones before it; queued transforms may still use
+// the old area, so growing waits for the lane's stream), and set on e.
+ftp_status lane_fft_work(SumLane& L, const FftEntry& e) {
+  if (e.work > L.fftwork_bytes) {
+    // queued transforms may still use the old work area
+    if (L.s) cudaStreamSynchronize(L.s);
+    if (L.fftwork) cudaFree(L.fftwork);
+    L.fftwork = nullptr;
+    L.fftwork_bytes = 0;
+    if (cudaMalloc(&L.fftwork, e.work) != cudaSuccess) {
+      cudaGetLastError();
+      return FTP_ERR_OOM;
+    }
+    L.fftwork_bytes = e.work;
+    for (auto& kv : L.ffts) cufftSetWorkArea(kv.second.h, L.fftwork);
+    for (auto& kv : L.bffts) cufftSetWorkArea(kv.second.h, L.fftwork);
+  }
+  cufftSetWorkArea(e.h, L.fftwork);
+  return FTP_OK;
+}
+
 ftp_status get_fft(ftp_plan_t P, SumLane& L, int64_t n, cufftHandle* out) {
   auto it = L.ffts.find(n);
   if (it != L.ffts.end()) {
@@ -295,21 +321,40 @@ ftp_status get_fft(ftp_plan_t P, SumLane& L, int64_t n, cufftHandle* out) {
     cufftDestroy(e.h);
     return FTP_ERR_CUDA;
   }
-  if (e.work > L.fftwork_bytes) {
-    // queued transforms may still use the old work area
-    if (L.s) cudaStreamSynchronize(L.s);
-    if (L.fftwork) cudaFree(L.fftwork);
-    L.fftwork = nullptr;
-    L.fftwork_bytes = 0;
-    if (cudaMalloc(&L.fftwork, e.work) != cudaSuccess) {
-      cufftDestroy(e.h);
-      return FTP_ERR_OOM;
-    }
-    L.fftwork_bytes = e.work;
-    for (auto& kv : L.ffts) cufftSetWorkArea(kv.second.h, L.fftwork);
+  const ftp_status st = lane_fft_work(L, e);
+  if (st != FTP_OK) {
+    cufftDestroy(e.h);
+    return st;
   }
-  cufftSetWorkArea(e.h, L.fftwork);
   L.ffts[n] = e;
+  *out = e.h;
+  return FTP_OK;
+}
+
+// A batched transform: `batch` grids of length n, back to back.
+ftp_status get_fft_many(ftp_plan_t P, SumLane& L, int64_t n, int batch, cufftHandle* out) {
+  const auto key = std::make_pair(n, batch);
+  auto it = L.bffts.find(key);
+  if (it != L.bffts.end()) {
+    *out = it->second.h;
+    return FTP_OK;
+  }
+  FftEntry e;
+  if (cufftCreate(&e.h) != CUFFT_SUCCESS) return FTP_ERR_CUDA;
+  cufftSetAutoAllocation(e.h, 0);
+  const cufftType ty = P->mixed ? CUFFT_C2C : CUFFT_Z2Z;
+  long long len = n;
+  if (cufftMakePlanMany64(e.h, 1, &len, nullptr, 1, len, nullptr, 1, len, ty, batch, &e.work) !=
+      CUFFT_SUCCESS) {
+    cufftDestroy(e.h);
+    return FTP_ERR_CUDA;
+  }
+  const ftp_status st = lane_fft_work(L, e);
+  if (st != FTP_OK) {
+    cufftDestroy(e.h);
+    return st;
+  }
+  L.bffts[key] = e;
   *out = e.h;
   return FTP_OK;
 }
@@ -392,45 +437,6 @@ ftp_status run_sums(ftp_plan_t P, SumLane& L, const double* t, const double* y, 
   }
   ev_rec(P, 4);
   *launches += 7;
-  FTP_CK(cudaGetLastError());
-  return FTP_OK;
-}
-
-// Spreading, FFT and gather of one batched curve on lane L, from its
-// observations already in tile order (tile offsets relative to cell_s).
-ftp_status run_sums_prepped(ftp_plan_t P, SumLane& L, int64_t k0, int64_t nf, int Hs,
-                            int64_t ngrid, int64_t ntiles, const int* tile_off,
-                            const int* cell_s, const void* frac_s, const void* coef_s,
-                            void* sums, int64_t nf_pad, int* launches) {
-  if (ngrid > P->ngrid || ntiles > P->ntiles) return FTP_ERR_UNSUPPORTED;
-  cufftHandle fft;
-  ftp_status st = get_fft(P, L, ngrid, &fft);
-  if (st != FTP_OK) return st;
-  cudaStream_t s = L.s;
-  if (P->mixed) {
-    launch_spread<float>(tile_off, cell_s, (const float*)frac_s, (const float2*)coef_s, ngrid,
-                         ntiles, P->m, P->beta, (float2*)L.grid, P->d_status, s);
-  } else {
-    launch_spread<double>(tile_off, cell_s, (const double*)frac_s, (const double2*)coef_s,
-                          ngrid, ntiles, P->m, P->beta, (double2*)L.grid, P->d_status, s);
-  }
-  if (cufftSetStream(fft, s) != CUFFT_SUCCESS) return FTP_ERR_CUDA;
-  cufftResult fr;
-  if (P->mixed) {
-    fr = cufftExecC2C(fft, (cufftComplex*)L.grid, (cufftComplex*)L.grid, CUFFT_INVERSE);
-  } else {
-    fr = cufftExecZ2Z(fft, (cufftDoubleComplex*)L.grid, (cufftDoubleComplex*)L.grid,
-                      CUFFT_INVERSE);
-  }
-  if (fr != CUFFT_SUCCESS) return FTP_ERR_CUDA;
-  if (P->mixed) {
-    launch_gather<float>((const float2*)L.grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
-                         (float2*)sums, P->d_status, s);
-  } else {
-    launch_gather<double>((const double2*)L.grid, ngrid, k0, nf, nf_pad, Hs, P->m, P->beta,
-                          (double2*)sums, P->d_status, s);
-  }
-  *launches += 2;
   FTP_CK(cudaGetLastError());
   return FTP_OK;
 }
@@ -770,6 +776,8 @@ void free_lane(SumLane* L) {
   if (L->s) cudaStreamSynchronize(L->s);
   for (auto& kv : L->ffts) cufftDestroy(kv.second.h);
   L->ffts.clear();
+  for (auto& kv : L->bffts) cufftDestroy(kv.second.h);
+  L->bffts.clear();
   if (L->fftwork) cudaFree(L->fftwork);
   L->fftwork = nullptr;
   if (!L->owned) return;
@@ -789,24 +797,8 @@ ftp_status ensure_lanes(ftp_plan_t P, int want, bool* grew) {
   while ((int)P->xlanes.size() + 1 < want) {
     SumLane* L = new SumLane();
     L->owned = true;
-    const size_t nobs = (size_t)P->max_nobs;
-    bool ok = cudaStreamCreateWithFlags(&L->s, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming) == cudaSuccess &&
-              dalloc(&L->mom_scratch, kMomentScratchBytes) == FTP_OK &&
-              dalloc(&L->tile_count, (size_t)P->ntiles) == FTP_OK &&
-              dalloc(&L->tile_off, (size_t)P->ntiles + 1) == FTP_OK &&
-              dalloc(&L->cursor, (size_t)P->ntiles) == FTP_OK &&
-              dalloc(&L->cell, nobs) == FTP_OK && dalloc(&L->cell_s, nobs) == FTP_OK;
-    unsigned char* b[5] = {};
-    const size_t sizes[5] = {nobs * P->rsz, nobs * P->rsz, nobs * P->csz, nobs * P->csz,
-                             (size_t)P->ngrid * P->csz};
-    for (int i = 0; i < 5 && ok; ++i) ok = dalloc(&b[i], sizes[i]) == FTP_OK;
-    L->frac = b[0];
-    L->frac_s = b[1];
-    L->coef = b[2];
-    L->coef_s = b[3];
-    L->grid = b[4];
-    if (ok) ok = cudaMemset(L->mom_scratch, 0, kMomentScratchBytes) == cudaSuccess;
+    const bool ok = cudaStreamCreateWithFlags(&L->s, cudaStreamNonBlocking) == cudaSuccess &&
+                    cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       free_lane(L);
@@ -837,10 +829,25 @@ struct BLaunch {
   int64_t seg_first, units_first, cseg_first, units;
   int nseg;
 };
+// Batched step (a): a chunk's curves sorted by NFFT grid length and cut into
+// groups whose grids fit the grid buffer; per group one spreading launch,
+// one batched FFT per grid-size class, one gather launch.
+struct BFftClass {
+  int64_t n, goff;  // grid length; first element of the class's grids in the buffer
+  int count;
+};
+struct BSub {
+  int64_t desc_first;  // first StepACurve of the group in the descriptor blob
+  int ncurves;
+  int64_t pref_first;  // spread prefix at pref_first, gather prefix ncurves + 1 later
+  int64_t spread_tiles = 0, gather_tiles = 0, grid_elems = 0;
+  std::vector<BFftClass> classes;
+};
 struct BChunk {
   int64_t c0, c1, sums_elems, nf_total;
   int Hs;
   std::vector<BLaunch> launches;
+  std::vector<BSub> subs;
   int64_t items;  // (template, frequency) output items of the chunk's curves
   int64_t obs_total = 0, tiles_total = 0;  // preparation scratch of the chunk
 };
@@ -879,8 +886,16 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
   return h;
 }
 
+// Lanes that run a group's batched FFTs (one class per lane, round-robin).
+int fft_lanes_used(ftp_plan_t P, const BSub& sb) {
+  return (int)std::max<int64_t>(
+      1, std::min<int64_t>(std::min<int64_t>(1 + (int64_t)P->xlanes.size(), P->sum_lanes),
+                           (int64_t)sb.classes.size()));
+}
+
 ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
-                                const std::vector<BChunk>& chunks, const RootsSeg* d_segs,
+                                const std::vector<BChunk>& chunks, const StepACurve* d_stepa,
+                                const int64_t* d_pref, const RootsSeg* d_segs,
                                 const int64_t* d_units, const CurveDesc* d_curves,
                                 const int* d_cseg, double* const* o, uint8_t* of,
                                 int64_t extent, const BatchScreen* scr,
@@ -894,9 +909,10 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
     const BChunk& ch = chunks[q];
     if (tm) cudaEventRecord(P->bev[5 * q + 0], s);
     // step (a) preparation of every curve of the chunk in one launch
-    // (moments, cells, tile order), then spreading, FFT and gather of each
-    // curve, round-robin over the lanes (fork/join through events, so a
-    // captured graph holds parallel branches)
+    // (moments, cells, tile order); then per group of curves one spreading
+    // launch, one batched FFT per grid-size class (classes round-robin over
+    // the lanes, fork/join through events, so a captured graph holds
+    // parallel branches) and one gather launch
     if (P->mixed) {
       launch_prep_batch<float>(pb.curves + ch.c0, (int)(ch.c1 - ch.c0), P->d_bmom, pb.tile_cnt,
                                pb.tile_off, pb.cell, (float*)pb.frac, (float2*)pb.coef,
@@ -908,27 +924,52 @@ ftp_status enqueue_batch_device(ftp_plan_t P, const std::vector<BCurve>& cv,
                                 s);
     }
     *launches += 1;
-    const int used = (int)std::min<int64_t>(
-        std::min<int64_t>(1 + (int64_t)P->xlanes.size(), P->sum_lanes), ch.c1 - ch.c0);
-    if (used > 1) {
-      FTP_CK(cudaEventRecord(P->fork, s));
-      for (int l = 1; l < used; ++l) FTP_CK(cudaStreamWaitEvent(P->xlanes[l - 1]->s, P->fork, 0));
-    }
-    for (int64_t c = ch.c0; c < ch.c1; ++c) {
-      const BCurve& b = cv[(size_t)c];
-      const int l = (int)((c - ch.c0) % used);
-      SumLane& L = l == 0 ? P->l0 : *P->xlanes[l - 1];
-      ftp_status st = run_sums_prepped(
-          P, L, b.k0, b.nf, b.Hc, b.ngrid, b.ntiles, pb.tile_off + b.tile_base,
-          pb.cell_s + b.obs_base, (unsigned char*)pb.frac_s + (size_t)b.obs_base * (P->csz / 2),
-          (unsigned char*)pb.coef_s + (size_t)b.obs_base * P->csz,
-          (unsigned char*)P->d_bsums + (size_t)b.sums_off * P->csz, b.nf_pad, launches);
-      if (st != FTP_OK) return st;
-    }
-    for (int l = 1; l < used; ++l) {
-      SumLane& L = *P->xlanes[l - 1];
-      FTP_CK(cudaEventRecord(L.done, L.s));
-      FTP_CK(cudaStreamWaitEvent(s, L.done, 0));
+    for (const BSub& sb : ch.subs) {
+      const StepACurve* sc = d_stepa + sb.desc_first;
+      const int64_t* spre = d_pref + sb.pref_first;
+      const int64_t* gpre = spre + sb.ncurves + 1;
+      if (P->mixed) {
+        launch_spread_batch<float>(sc, spre, sb.ncurves, sb.spread_tiles, P->m, P->beta,
+                                   P->d_status, s);
+      } else {
+        launch_spread_batch<double>(sc, spre, sb.ncurves, sb.spread_tiles, P->m, P->beta,
+                                    P->d_status, s);
+      }
+      *launches += 1;
+      const int used = fft_lanes_used(P, sb);
+      if (used > 1) {
+        FTP_CK(cudaEventRecord(P->fork, s));
+        for (int l = 1; l < used; ++l) FTP_CK(cudaStreamWaitEvent(P->xlanes[l - 1]->s, P->fork, 0));
+      }
+      for (size_t k = 0; k < sb.classes.size(); ++k) {
+        const BFftClass& fc = sb.classes[k];
+        const int l = (int)(k % (size_t)used);
+        SumLane& L = l == 0 ? P->l0 : *P->xlanes[l - 1];
+        cufftHandle fft;
+        ftp_status st = get_fft_many(P, L, fc.n, fc.count, &fft);  // made before: a lookup
+        if (st != FTP_OK) return st;
+        if (cufftSetStream(fft, l == 0 ? s : L.s) != CUFFT_SUCCESS) return FTP_ERR_CUDA;
+        void* g = static_cast<unsigned char*>(P->d_bgrid) + (size_t)fc.goff * P->csz;
+        const cufftResult fr =
+            P->mixed ? cufftExecC2C(fft, (cufftComplex*)g, (cufftComplex*)g, CUFFT_INVERSE)
+                     : cufftExecZ2Z(fft, (cufftDoubleComplex*)g, (cufftDoubleComplex*)g,
+                                    CUFFT_INVERSE);
+        if (fr != CUFFT_SUCCESS) return FTP_ERR_CUDA;
+      }
+      for (int l = 1; l < used; ++l) {
+        SumLane& L = *P->xlanes[l - 1];
+        FTP_CK(cudaEventRecord(L.done, L.s));
+        FTP_CK(cudaStreamWaitEvent(s, L.done, 0));
+      }
+      if (P->mixed) {
+        launch_gather_batch<float>(sc, gpre, sb.ncurves, sb.gather_tiles, P->m, P->beta,
+                                   P->d_status, s);
+      } else {
+        launch_gather_batch<double>(sc, gpre, sb.ncurves, sb.gather_tiles, P->m, P->beta,
+                                    P->d_status, s);
+      }
+      *launches += 1;
+      FTP_CK(cudaGetLastError());
     }
     if (tm) cudaEventRecord(P->bev[5 * q + 1], s);
     if (scr && scr->moments_out)
@@ -1152,7 +1193,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   std::vector<BCurve> cv((size_t)ncurves);
   std::vector<BChunk> chunks;
   {
-    BChunk cur{0, 0, 0, 0, 0, {}, 0};
+    BChunk cur{0, 0, 0, 0, 0, {}, {}, 0};
     for (int64_t c = 0; c < ncurves; ++c) {
       BCurve& b = cv[(size_t)c];
       const ftp_grid& g = grids[c];
@@ -1179,7 +1220,7 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
                          cur.nf_total + b.nf > ((int64_t)1 << 30));
       if (full) {
         chunks.push_back(cur);
-        cur = BChunk{c, c, 0, 0, 0, {}, 0};
+        cur = BChunk{c, c, 0, 0, 0, {}, {}, 0};
       }
       b.sums_off = cur.sums_elems;
       b.redo_base = cur.nf_total;
@@ -1194,6 +1235,66 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       cur.c1 = c + 1;
     }
     chunks.push_back(cur);
+  }
+  // ---- batched step (a): per chunk, the curves sorted by grid length and
+  //      cut into groups whose grids fit the grid buffer (twice the chunk
+  //      budget; a larger single curve gets a group of its own).  sa_curve /
+  //      sa_goff: the curve and grid offset of each StepACurve, group after
+  //      group; sa_pref: each group's spread prefix, then its gather prefix.
+  std::vector<int64_t> sa_curve, sa_goff, sa_pref;
+  int64_t max_group_grid = 0;
+  int max_classes = 1;
+  {
+    const int64_t budget = (int64_t)(2 * P->chunk_bytes / P->csz);
+    for (BChunk& ch : chunks) {
+      std::vector<int64_t> order;
+      for (int64_t c = ch.c0; c < ch.c1; ++c) order.push_back(c);
+      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return cv[(size_t)a].ngrid < cv[(size_t)b].ngrid;
+      });
+      BSub cur{};
+      bool open = false;
+      auto close = [&]() {
+        cur.pref_first = (int64_t)sa_pref.size();
+        int64_t acc = 0;
+        sa_pref.push_back(0);
+        for (int i = 0; i < cur.ncurves; ++i) {
+          acc += cv[(size_t)sa_curve[(size_t)(cur.desc_first + i)]].ntiles;
+          sa_pref.push_back(acc);
+        }
+        cur.spread_tiles = acc;
+        acc = 0;
+        sa_pref.push_back(0);
+        for (int i = 0; i < cur.ncurves; ++i) {
+          const BCurve& b = cv[(size_t)sa_curve[(size_t)(cur.desc_first + i)]];
+          acc += gather_tile_count(!P->mixed, b.k0, b.nf, b.Hc);
+          sa_pref.push_back(acc);
+        }
+        cur.gather_tiles = acc;
+        max_group_grid = std::max(max_group_grid, cur.grid_elems);
+        max_classes = std::max(max_classes, (int)cur.classes.size());
+        ch.subs.push_back(cur);
+        open = false;
+      };
+      for (int64_t c : order) {
+        const BCurve& b = cv[(size_t)c];
+        if (open && cur.grid_elems + b.ngrid > budget) close();
+        if (!open) {
+          cur = BSub{};
+          cur.desc_first = (int64_t)sa_curve.size();
+          cur.ncurves = 0;
+          open = true;
+        }
+        if (cur.classes.empty() || cur.classes.back().n != b.ngrid)
+          cur.classes.push_back(BFftClass{b.ngrid, cur.grid_elems, 0});
+        cur.classes.back().count++;
+        sa_curve.push_back(c);
+        sa_goff.push_back(cur.grid_elems);
+        cur.grid_elems += b.ngrid;
+        cur.ncurves++;
+      }
+      if (open) close();
+    }
   }
 
   // ---- templates (grouped by H) and the segment tables of every chunk
@@ -1322,7 +1423,9 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     }
   }
   const size_t off_prep = off_rowoff + al64(rowoff.size() * sizeof(int64_t));
-  const size_t blob = off_prep + al64(prep.size() * sizeof(PrepCurve));
+  const size_t off_stepa = off_prep + al64(prep.size() * sizeof(PrepCurve));
+  const size_t off_pref = off_stepa + al64(sa_curve.size() * sizeof(StepACurve));
+  const size_t blob = off_pref + al64(sa_pref.size() * sizeof(int64_t));
 
   // ---- workspace (growing it drops a captured graph)
   st = grow_dev(reinterpret_cast<unsigned char**>(&P->d_bsums), &P->bsums_cap,
@@ -1330,6 +1433,9 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   if (st == FTP_OK) st = grow_dev(&P->d_bmom, &P->bmom_cap, max_chunk_curves * MO_WORDS, &grew);
   if (st == FTP_OK) st = grow_dev(&P->d_bmark, &P->bmark_cap, (size_t)max_nf_total, &grew);
   if (st == FTP_OK) st = grow_dev(&P->d_bdesc, &P->bdesc_cap, blob, &grew);
+  if (st == FTP_OK)
+    st = grow_dev(reinterpret_cast<unsigned char**>(&P->d_bgrid), &P->bgrid_cap,
+                  (size_t)max_group_grid * P->csz, &grew);
   // preparation scratch: cells (unsorted, sorted), fractions, coefficients,
   // tile counters and offsets of the largest chunk
   const size_t rsz = P->csz / 2;
@@ -1376,25 +1482,55 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   memcpy(P->h_bdesc + off_cseg, cseg.data(), cseg.size() * sizeof(int));
   memcpy(P->h_bdesc + off_scur, scurves.data(), scurves.size() * sizeof(ScreenCurve));
   memcpy(P->h_bdesc + off_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t));
+  PrepBufs pbufs{};
+  pbufs.curves = reinterpret_cast<const PrepCurve*>(P->d_bdesc + off_prep);
+  pbufs.cell = reinterpret_cast<int*>(P->d_bprep + pb_cell);
+  pbufs.cell_s = pbufs.cell + mo;
+  pbufs.frac = P->d_bprep + pb_frac;
+  pbufs.frac_s = P->d_bprep + pb_frac + mo * rsz;
+  pbufs.coef = P->d_bprep + pb_coef;
+  pbufs.coef_s = P->d_bprep + pb_coef + mo * P->csz;
+  pbufs.tile_cnt = reinterpret_cast<int*>(P->d_bprep + pb_tile);
+  pbufs.tile_off = pbufs.tile_cnt + mt;
   memcpy(P->h_bdesc + off_prep, prep.data(), prep.size() * sizeof(PrepCurve));
-  // step (a) lanes, then every FFT size on every lane that runs one: making a
-  // plan may resize (and so synchronise) a work area
   {
-    int64_t most = 0;
-    for (const BChunk& ch : chunks) most = std::max(most, ch.c1 - ch.c0);
-    st = ensure_lanes(P, (int)std::min<int64_t>(P->sum_lanes, most), &grew);
-    if (st != FTP_OK) return st;
-  }
-  for (const BChunk& ch : chunks) {
-    const int used = (int)std::min<int64_t>(
-        std::min<int64_t>(1 + (int64_t)P->xlanes.size(), P->sum_lanes), ch.c1 - ch.c0);
-    for (int64_t c = ch.c0; c < ch.c1; ++c) {
-      const int l = (int)((c - ch.c0) % used);
-      cufftHandle h;
-      st = get_fft(P, l == 0 ? P->l0 : *P->xlanes[l - 1], cv[(size_t)c].ngrid, &h);
-      if (st != FTP_OK) return st;
+    std::vector<StepACurve> sa(sa_curve.size());
+    for (size_t i = 0; i < sa.size(); ++i) {
+      const BCurve& b = cv[(size_t)sa_curve[i]];
+      StepACurve& d = sa[i];
+      d.tile_off = pbufs.tile_off + b.tile_base;
+      d.cell_s = pbufs.cell_s + b.obs_base;
+      d.frac_s = static_cast<const unsigned char*>(pbufs.frac_s) + (size_t)b.obs_base * rsz;
+      d.coef_s = static_cast<const unsigned char*>(pbufs.coef_s) + (size_t)b.obs_base * P->csz;
+      d.grid = static_cast<unsigned char*>(P->d_bgrid) + (size_t)sa_goff[i] * P->csz;
+      d.sums = static_cast<unsigned char*>(P->d_bsums) + (size_t)b.sums_off * P->csz;
+      d.ngrid = b.ngrid;
+      d.ntiles = b.ntiles;
+      d.k0 = b.k0;
+      d.nf = b.nf;
+      d.nf_pad = b.nf_pad;
+      d.Hs = b.Hc;
+      d.pad_ = 0;
     }
+    memcpy(P->h_bdesc + off_stepa, sa.data(), sa.size() * sizeof(StepACurve));
+    memcpy(P->h_bdesc + off_pref, sa_pref.data(), sa_pref.size() * sizeof(int64_t));
   }
+  // step (a) lanes, then every batched FFT of every group on the lane that
+  // runs it (before any capture: making a plan may resize, and so
+  // synchronise, a work area)
+  st = ensure_lanes(P, std::min(P->sum_lanes, max_classes), &grew);
+  if (st != FTP_OK) return st;
+  for (const BChunk& ch : chunks)
+    for (const BSub& sb : ch.subs) {
+      const int used = fft_lanes_used(P, sb);
+      for (size_t k = 0; k < sb.classes.size(); ++k) {
+        const int l = (int)(k % (size_t)used);
+        cufftHandle h;
+        st = get_fft_many(P, l == 0 ? P->l0 : *P->xlanes[l - 1], sb.classes[k].n,
+                          sb.classes[k].count, &h);
+        if (st != FTP_OK) return st;
+      }
+    }
   if (P->timing) {
     while (P->bev.size() < 5 * chunks.size()) {
       cudaEvent_t e;
@@ -1424,16 +1560,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
   const int* d_cseg = reinterpret_cast<const int*>(P->d_bdesc + off_cseg);
   const ScreenCurve* d_scur = reinterpret_cast<const ScreenCurve*>(P->d_bdesc + off_scur);
   const int64_t* d_rowoff = reinterpret_cast<const int64_t*>(P->d_bdesc + off_rowoff);
-  PrepBufs pbufs{};
-  pbufs.curves = reinterpret_cast<const PrepCurve*>(P->d_bdesc + off_prep);
-  pbufs.cell = reinterpret_cast<int*>(P->d_bprep + pb_cell);
-  pbufs.cell_s = pbufs.cell + mo;
-  pbufs.frac = P->d_bprep + pb_frac;
-  pbufs.frac_s = P->d_bprep + pb_frac + mo * rsz;
-  pbufs.coef = P->d_bprep + pb_coef;
-  pbufs.coef_s = P->d_bprep + pb_coef + mo * P->csz;
-  pbufs.tile_cnt = reinterpret_cast<int*>(P->d_bprep + pb_tile);
-  pbufs.tile_off = pbufs.tile_cnt + mt;
+  const StepACurve* d_stepa = reinterpret_cast<const StepACurve*>(P->d_bdesc + off_stepa);
+  const int64_t* d_pref = reinterpret_cast<const int64_t*>(P->d_bdesc + off_pref);
   double* o[4] = {power, theta1, theta2, theta3};
   uint8_t* of = flags;
   if (!out_dev) {
@@ -1487,8 +1615,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     // second identical call: capture the device work once, then launch it
     cudaGraph_t graph = nullptr;
     FTP_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                              scr, d_scur, d_rowoff, pbufs, &launches);
+    st = enqueue_batch_device(P, cv, chunks, d_stepa, d_pref, d_segs, d_units, d_curves, d_cseg,
+                              o, of, extent, scr, d_scur, d_rowoff, pbufs, &launches);
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     cudaGraphExec_t exec = nullptr;
     if (st == FTP_OK && ce == cudaSuccess && graph &&
@@ -1506,13 +1634,13 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
       if (st != FTP_OK) return st;
       P->eager_key = 0;  // capture failed: stay eager for this call pattern
       launches = 0;
-      st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                                scr, d_scur, d_rowoff, pbufs, &launches);
+      st = enqueue_batch_device(P, cv, chunks, d_stepa, d_pref, d_segs, d_units, d_curves,
+                                d_cseg, o, of, extent, scr, d_scur, d_rowoff, pbufs, &launches);
       if (st != FTP_OK) return st;
     }
   } else {
-    st = enqueue_batch_device(P, cv, chunks, d_segs, d_units, d_curves, d_cseg, o, of, extent,
-                              scr, d_scur, d_rowoff, pbufs, &launches);
+    st = enqueue_batch_device(P, cv, chunks, d_stepa, d_pref, d_segs, d_units, d_curves, d_cseg,
+                              o, of, extent, scr, d_scur, d_rowoff, pbufs, &launches);
     if (st != FTP_OK) return st;
     if (graphable) P->eager_key = key;
   }

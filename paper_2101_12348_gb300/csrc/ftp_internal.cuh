@@ -110,6 +110,35 @@ void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int
                    int64_t nf_pad, int Hs, int m, double beta, typename C2<R>::type* sums,
                    const int* status, cudaStream_t s);
 
+// One curve of a batched step (a): its observations in spreading-tile order,
+// its NFFT grid (inside a batch's grid buffer) and its sum rows.
+struct StepACurve {
+  const int* tile_off;  // ntiles + 1 offsets into cell_s / frac_s / coef_s
+  const int* cell_s;
+  const void* frac_s;   // R[n]
+  const void* coef_s;   // C2<R>[n]
+  void* grid;           // C2<R>[ngrid]
+  void* sums;           // C2<R>[3 Hs][nf_pad]
+  int64_t ngrid, ntiles, k0, nf, nf_pad;
+  int32_t Hs, pad_;
+};
+static_assert(sizeof(StepACurve) == 96, "StepACurve layout");
+
+// Spreading and gather of `ncurves` curves in one launch each: spread
+// tile t of the list belongs to the curve c with spread_prefix[c] <= t <
+// spread_prefix[c + 1] (likewise the gather tiles); the prefixes have
+// ncurves + 1 entries, the last being the total.
+template <typename R>
+void launch_spread_batch(const StepACurve* curves, const int64_t* spread_prefix, int ncurves,
+                         int64_t total_tiles, int m, double beta, const int* status,
+                         cudaStream_t s);
+template <typename R>
+void launch_gather_batch(const StepACurve* curves, const int64_t* gather_prefix, int ncurves,
+                         int64_t total_tiles, int m, double beta, const int* status,
+                         cudaStream_t s);
+// Gather tiles of one curve (host side sizing of the work lists).
+int64_t gather_tile_count(bool fp64, int64_t k0, int64_t nf, int Hs);
+
 void launch_direct_sums(const double* t, const double* y, const double* dy, int64_t n,
                         const double* moments, const int* status, double df, int64_t k0,
                         const int* list, const int* count, int cap, int Hs, int64_t nf_pad,

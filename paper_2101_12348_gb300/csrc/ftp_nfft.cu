@@ -457,7 +457,74 @@ __device__ __forceinline__ void smem_atomic_add2(typename C2<R>::type* p, R a, R
 // contribution that lands in its tile into shared memory - from the points
 // binned to its own tile and to its two neighbours, whose windows reach
 // across the boundary - and then writes the whole tile, zeros included, with
-// one TMA bulk store.
+// one TMA bulk store.  spread_tile does tile b of one curve's grid; the
+// single-curve kernel runs one CTA per tile, the batched one walks a list of
+// (curve, tile) pairs.
+template <typename R>
+__device__ __forceinline__ void spread_tile(int64_t b, const int* __restrict__ off,
+                                            const int* __restrict__ cell_s,
+                                            const R* __restrict__ frac_s,
+                                            const typename C2<R>::type* __restrict__ coef_s,
+                                            int64_t ngrid, int64_t ntiles, int m, R beta,
+                                            typename C2<R>::type* __restrict__ grid,
+                                            typename C2<R>::type* tile) {
+  using Cx = typename C2<R>::type;
+  for (int i = threadIdx.x; i < kSpreadTile; i += blockDim.x) {
+    Cx z;
+    z.x = R(0);
+    z.y = R(0);
+    tile[i] = z;
+  }
+  __syncthreads();
+  int64_t nb[3];
+  int nnb;
+  if (ntiles == 1) {
+    nb[0] = 0;
+    nnb = 1;
+  } else if (ntiles == 2) {
+    nb[0] = 0;
+    nb[1] = 1;
+    nnb = 2;
+  } else {
+    nb[0] = (b == 0) ? ntiles - 1 : b - 1;
+    nb[1] = b;
+    nb[2] = (b + 1 == ntiles) ? 0 : b + 1;
+    nnb = 3;
+  }
+  const int w2 = 2 * m;
+  const R inv_m = R(1) / R(m);
+  for (int q = 0; q < nnb; ++q) {
+    const int start = off[nb[q]];
+    const int cnt = off[nb[q] + 1] - start;
+    const int total = cnt * w2;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      const int p = start + e / w2;
+      const int d = e % w2 - (m - 1);
+      int64_t ca = (int64_t)cell_s[p] + d;
+      if (ca < 0) ca += ngrid;
+      if (ca >= ngrid) ca -= ngrid;
+      if ((ca >> kSpreadTileShift) != b) continue;
+      const R phi = kb_window<R>((R)d - frac_s[p], inv_m, beta);
+      const Cx c = coef_s[p];
+      smem_atomic_add2<R>(&tile[ca & (kSpreadTile - 1)], c.x * phi, c.y * phi);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // Make the generic-proxy shared-memory writes visible to the bulk copy,
+    // and wait until the copy has read the tile before it is reused.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    Cx* dst = grid + b * kSpreadTile;
+    asm volatile(
+        "cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+        "cp.async.bulk.commit_group;\n\t"
+        "cp.async.bulk.wait_group.read 0;" ::"l"(dst),
+        "r"(smem_addr(tile)), "r"((unsigned)(kSpreadTile * sizeof(Cx)))
+        : "memory");
+  }
+  __syncthreads();
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) spread_kernel(const int* __restrict__ off,
                                                      const int* __restrict__ cell_s,
@@ -468,60 +535,39 @@ __global__ void __launch_bounds__(256) spread_kernel(const int* __restrict__ off
                                                      const int* __restrict__ status) {
   using Cx = typename C2<R>::type;
   __shared__ __align__(128) Cx tile[kSpreadTile];
-  const int64_t b = blockIdx.x;
-  for (int i = threadIdx.x; i < kSpreadTile; i += blockDim.x) {
-    Cx z;
-    z.x = R(0);
-    z.y = R(0);
-    tile[i] = z;
+  if (status[ST_CODE] != DEV_OK) return;
+  spread_tile<R>(blockIdx.x, off, cell_s, frac_s, coef_s, ngrid, ntiles, m, beta, grid, tile);
+}
+
+// Index of the unit-list entry holding global tile t: the last c with
+// prefix[c] <= t (prefix has n + 1 ascending entries).
+__device__ __forceinline__ int find_curve(const int64_t* __restrict__ prefix, int n, int64_t t) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= t) lo = mid;
+    else hi = mid;
   }
-  __syncthreads();
-  if (status[ST_CODE] == DEV_OK) {
-    int64_t nb[3];
-    int nnb;
-    if (ntiles == 1) {
-      nb[0] = 0;
-      nnb = 1;
-    } else if (ntiles == 2) {
-      nb[0] = 0;
-      nb[1] = 1;
-      nnb = 2;
-    } else {
-      nb[0] = (b == 0) ? ntiles - 1 : b - 1;
-      nb[1] = b;
-      nb[2] = (b + 1 == ntiles) ? 0 : b + 1;
-      nnb = 3;
-    }
-    const int w2 = 2 * m;
-    const R inv_m = R(1) / R(m);
-    for (int q = 0; q < nnb; ++q) {
-      const int start = off[nb[q]];
-      const int cnt = off[nb[q] + 1] - start;
-      const int total = cnt * w2;
-      for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int p = start + e / w2;
-        const int d = e % w2 - (m - 1);
-        int64_t ca = (int64_t)cell_s[p] + d;
-        if (ca < 0) ca += ngrid;
-        if (ca >= ngrid) ca -= ngrid;
-        if ((ca >> kSpreadTileShift) != b) continue;
-        const R phi = kb_window<R>((R)d - frac_s[p], inv_m, beta);
-        const Cx c = coef_s[p];
-        smem_atomic_add2<R>(&tile[ca & (kSpreadTile - 1)], c.x * phi, c.y * phi);
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // Make the generic-proxy shared-memory writes visible to the bulk copy.
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    Cx* dst = grid + b * kSpreadTile;
-    asm volatile(
-        "cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
-        "cp.async.bulk.commit_group;\n\t"
-        "cp.async.bulk.wait_group.read 0;" ::"l"(dst),
-        "r"(smem_addr(tile)), "r"((unsigned)(kSpreadTile * sizeof(Cx)))
-        : "memory");
+  return lo;
+}
+
+// Spreading of many curves in one launch: global tile t of the list belongs
+// to curve c with spread_prefix[c] <= t < spread_prefix[c + 1].
+template <typename R>
+__global__ void __launch_bounds__(256) spread_batch_kernel(const StepACurve* __restrict__ curves,
+                                                           const int64_t* __restrict__ prefix,
+                                                           int ncurves, int m, R beta,
+                                                           const int* __restrict__ status) {
+  using Cx = typename C2<R>::type;
+  __shared__ __align__(128) Cx tile[kSpreadTile];
+  if (status[ST_CODE] != DEV_OK) return;
+  const int64_t total = prefix[ncurves];
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const int c = find_curve(prefix, ncurves, t);
+    const StepACurve cd = curves[c];
+    spread_tile<R>(t - prefix[c], cd.tile_off, cd.cell_s, static_cast<const R*>(cd.frac_s),
+                   static_cast<const Cx*>(cd.coef_s), cd.ngrid, cd.ntiles, m, beta,
+                   static_cast<Cx*>(cd.grid), tile);
   }
 }
 
@@ -539,6 +585,79 @@ template <typename R> struct GatherTile;
 template <> struct GatherTile<float> { static constexpr int T = 2048; };
 template <> struct GatherTile<double> { static constexpr int T = 1024; };
 
+// Number of gather tiles of one curve.
+template <typename R>
+__host__ __device__ __forceinline__ int64_t gather_tiles(int64_t k0, int64_t nf, int Hs) {
+  return ((int64_t)2 * Hs * (k0 + nf - 1) - k0) / GatherTile<R>::T + 1;
+}
+
+// Gather tile `tile` of one curve (every thread of the CTA calls it).
+template <typename R>
+__device__ __forceinline__ void gather_tile(int64_t tile, const typename C2<R>::type* __restrict__ X,
+                                            int64_t ngrid, int64_t k0, int64_t nf, int64_t nf_pad,
+                                            int Hs, int m, R bt, typename C2<R>::type* __restrict__ sums,
+                                            typename C2<R>::type* sw, typename C2<R>::type* sy,
+                                            int64_t (*kb)[2]) {
+  using Cx = typename C2<R>::type;
+  constexpr int T = GatherTile<R>::T;
+  const int H2 = 2 * Hs;
+  const int64_t K1 = k0 + nf - 1;  // largest K
+  const int64_t jlo = k0, jhi = (int64_t)H2 * K1;
+  const R c2m = R(6.283185307179586476925286766559) * (R)m / (R)ngrid;
+  const int64_t J0 = jlo + tile * T;
+  const int64_t J1 = J0 + T - 1 < jhi ? J0 + T - 1 : jhi;  // inclusive
+  __syncthreads();  // the previous tile's shared values are consumed
+  if ((int)threadIdx.x < H2) {
+    const int64_t h = threadIdx.x + 1;
+    const int64_t lo = (J0 + h - 1) / h, hi = J1 / h;
+    kb[threadIdx.x][0] = lo > k0 ? lo : k0;
+    kb[threadIdx.x][1] = hi < K1 ? hi : K1;
+  }
+  for (int i = threadIdx.x; i <= (int)(J1 - J0); i += blockDim.x) {
+    const int64_t j = J0 + i;
+    const Cx xp = X[j];
+    const Cx xm = X[ngrid - j];
+    // the window transform in the working precision: its relative error is
+    // at the rounding level of the sums themselves
+    const R a = c2m * (R)j;
+    const R z = sqrt(bt * bt - a * a);
+    const R inv = z / (R(2 * m) * sinh(z));
+    Cx gw, gy;
+    gw.x = R(0.5) * (xp.x + xm.x) * inv;
+    gw.y = R(0.5) * (xp.y - xm.y) * inv;
+    gy.x = R(0.5) * (xp.y + xm.y) * inv;
+    gy.y = -R(0.5) * (xp.x - xm.x) * inv;
+    sw[i] = gw;
+    sy[i] = gy;
+  }
+  __syncthreads();
+  for (int h = 1; h <= H2; ++h) {
+    const int64_t lo = kb[h - 1][0], hi = kb[h - 1][1];
+    for (int64_t K = lo + threadIdx.x; K <= hi; K += blockDim.x) {
+      const int i = (int)(h * K - J0);
+      sums[(int64_t)(h - 1) * nf_pad + (K - k0)] = sw[i];
+      if (h <= Hs) sums[(int64_t)(H2 + h - 1) * nf_pad + (K - k0)] = sy[i];
+    }
+  }
+}
+
+// Zeros in the row padding [nf, nf_pad) of one curve's sum rows (the roots
+// kernels read whole work units), grid-strided over `nthreads` threads from
+// thread index `first`.
+template <typename R>
+__device__ __forceinline__ void zero_sum_padding(typename C2<R>::type* __restrict__ sums,
+                                                 int64_t nf, int64_t nf_pad, int Hs,
+                                                 int64_t first, int64_t nthreads) {
+  using Cx = typename C2<R>::type;
+  const int64_t npad = nf_pad - nf;
+  for (int64_t q = first; q < (int64_t)3 * Hs * npad; q += nthreads) {
+    Cx zero;
+    zero.x = R(0);
+    zero.y = R(0);
+    sums[(q / npad) * nf_pad + nf + q % npad] = zero;
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) gather_kernel(const typename C2<R>::type* __restrict__ X,
                                                      int64_t ngrid, int64_t k0, int64_t nf,
@@ -550,57 +669,34 @@ __global__ void __launch_bounds__(256) gather_kernel(const typename C2<R>::type*
   __shared__ Cx sw[T], sy[T];
   __shared__ int64_t kb[2 * kMaxH][2];  // K range of each harmonic in the tile
   if (status[ST_CODE] != DEV_OK) return;
-  const int H2 = 2 * Hs;
-  const int64_t K1 = k0 + nf - 1;  // largest K
-  const int64_t jlo = k0, jhi = (int64_t)H2 * K1;
-  const int64_t ntiles = (jhi - jlo) / T + 1;
-  // row padding [nf, nf_pad) read by whole work units: zeros
-  const int64_t npad = nf_pad - nf;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)3 * Hs * npad;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    Cx zero;
-    zero.x = R(0);
-    zero.y = R(0);
-    sums[(q / npad) * nf_pad + nf + q % npad] = zero;
-  }
-  const R bt = (R)beta;
-  const R c2m = R(6.283185307179586476925286766559) * (R)m / (R)ngrid;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t J0 = jlo + tile * T;
-    const int64_t J1 = J0 + T - 1 < jhi ? J0 + T - 1 : jhi;  // inclusive
-    __syncthreads();  // the previous tile's shared values are consumed
-    if ((int)threadIdx.x < H2) {
-      const int64_t h = threadIdx.x + 1;
-      const int64_t lo = (J0 + h - 1) / h, hi = J1 / h;
-      kb[threadIdx.x][0] = lo > k0 ? lo : k0;
-      kb[threadIdx.x][1] = hi < K1 ? hi : K1;
-    }
-    for (int i = threadIdx.x; i <= (int)(J1 - J0); i += blockDim.x) {
-      const int64_t j = J0 + i;
-      const Cx xp = X[j];
-      const Cx xm = X[ngrid - j];
-      // the window transform in the working precision: its relative error is
-      // at the rounding level of the sums themselves
-      const R a = c2m * (R)j;
-      const R z = sqrt(bt * bt - a * a);
-      const R inv = z / (R(2 * m) * sinh(z));
-      Cx gw, gy;
-      gw.x = R(0.5) * (xp.x + xm.x) * inv;
-      gw.y = R(0.5) * (xp.y - xm.y) * inv;
-      gy.x = R(0.5) * (xp.y + xm.y) * inv;
-      gy.y = -R(0.5) * (xp.x - xm.x) * inv;
-      sw[i] = gw;
-      sy[i] = gy;
-    }
-    __syncthreads();
-    for (int h = 1; h <= H2; ++h) {
-      const int64_t lo = kb[h - 1][0], hi = kb[h - 1][1];
-      for (int64_t K = lo + threadIdx.x; K <= hi; K += blockDim.x) {
-        const int i = (int)(h * K - J0);
-        sums[(int64_t)(h - 1) * nf_pad + (K - k0)] = sw[i];
-        if (h <= Hs) sums[(int64_t)(H2 + h - 1) * nf_pad + (K - k0)] = sy[i];
-      }
-    }
+  zero_sum_padding<R>(sums, nf, nf_pad, Hs, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                      (int64_t)gridDim.x * blockDim.x);
+  const int64_t ntiles = gather_tiles<R>(k0, nf, Hs);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    gather_tile<R>(tile, X, ngrid, k0, nf, nf_pad, Hs, m, (R)beta, sums, sw, sy, kb);
+}
+
+// Gather of many curves in one launch: global tile t of the list belongs to
+// curve c with gather_prefix[c] <= t < gather_prefix[c + 1]; the CTA that
+// takes a curve's first tile also zeros its row padding.
+template <typename R>
+__global__ void __launch_bounds__(256) gather_batch_kernel(const StepACurve* __restrict__ curves,
+                                                           const int64_t* __restrict__ prefix,
+                                                           int ncurves, int m, double beta,
+                                                           const int* __restrict__ status) {
+  using Cx = typename C2<R>::type;
+  constexpr int T = GatherTile<R>::T;
+  __shared__ Cx sw[T], sy[T];
+  __shared__ int64_t kb[2 * kMaxH][2];
+  if (status[ST_CODE] != DEV_OK) return;
+  const int64_t total = prefix[ncurves];
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const int c = find_curve(prefix, ncurves, t);
+    const StepACurve cd = curves[c];
+    Cx* sums = static_cast<Cx*>(cd.sums);
+    if (t == prefix[c]) zero_sum_padding<R>(sums, cd.nf, cd.nf_pad, cd.Hs, threadIdx.x, blockDim.x);
+    gather_tile<R>(t - prefix[c], static_cast<const Cx*>(cd.grid), cd.ngrid, cd.k0, cd.nf,
+                   cd.nf_pad, cd.Hs, m, (R)beta, sums, sw, sy, kb);
   }
 }
 
@@ -900,7 +996,7 @@ template <typename R>
 void launch_gather(const typename C2<R>::type* X, int64_t ngrid, int64_t k0, int64_t nf,
                    int64_t nf_pad, int Hs, int m, double beta, typename C2<R>::type* sums,
                    const int* status, cudaStream_t s) {
-  const int64_t ntiles = ((int64_t)2 * Hs * (k0 + nf - 1) - k0) / GatherTile<R>::T + 1;
+  const int64_t ntiles = gather_tiles<R>(k0, nf, Hs);
   const int64_t bmax = (int64_t)current_sms() * 6;
   int64_t blocks = ntiles < bmax ? ntiles : bmax;
   if (blocks < 1) blocks = 1;
@@ -926,6 +1022,32 @@ void launch_prep_one(const PrepCurve& pc, double* moments, int* tile_cnt, int* t
                                         frac_s, coef_s, status);
 }
 
+template <typename R>
+void launch_spread_batch(const StepACurve* curves, const int64_t* spread_prefix, int ncurves,
+                         int64_t total_tiles, int m, double beta, const int* status,
+                         cudaStream_t s) {
+  const int64_t bmax = (int64_t)current_sms() * 8;
+  int64_t blocks = total_tiles < bmax ? total_tiles : bmax;
+  if (blocks < 1) blocks = 1;
+  spread_batch_kernel<R><<<(unsigned)blocks, 256, 0, s>>>(curves, spread_prefix, ncurves, m,
+                                                           (R)beta, status);
+}
+
+template <typename R>
+void launch_gather_batch(const StepACurve* curves, const int64_t* gather_prefix, int ncurves,
+                         int64_t total_tiles, int m, double beta, const int* status,
+                         cudaStream_t s) {
+  const int64_t bmax = (int64_t)current_sms() * 6;
+  int64_t blocks = total_tiles < bmax ? total_tiles : bmax;
+  if (blocks < 1) blocks = 1;
+  gather_batch_kernel<R><<<(unsigned)blocks, 256, 0, s>>>(curves, gather_prefix, ncurves, m, beta,
+                                                           status);
+}
+
+int64_t gather_tile_count(bool fp64, int64_t k0, int64_t nf, int Hs) {
+  return fp64 ? gather_tiles<double>(k0, nf, Hs) : gather_tiles<float>(k0, nf, Hs);
+}
+
 #define FTP_INST(R)                                                                            \
   template void launch_points<R>(const double*, const double*, const double*, int64_t,         \
                                  const double*, const int*, double, int64_t, int*, int*, R*,   \
@@ -941,7 +1063,11 @@ void launch_prep_one(const PrepCurve& pc, double* moments, int* tile_cnt, int* t
   template void launch_prep_batch<R>(const PrepCurve*, int, double*, int*, int*, int*, R*,      \
                                      C2<R>::type*, int*, R*, C2<R>::type*, int*, cudaStream_t); \
   template void launch_prep_one<R>(const PrepCurve&, double*, int*, int*, int*, R*,             \
-                                   C2<R>::type*, int*, R*, C2<R>::type*, int*, cudaStream_t);
+                                   C2<R>::type*, int*, R*, C2<R>::type*, int*, cudaStream_t);   \
+  template void launch_spread_batch<R>(const StepACurve*, const int64_t*, int, int64_t, int,    \
+                                       double, const int*, cudaStream_t);                       \
+  template void launch_gather_batch<R>(const StepACurve*, const int64_t*, int, int64_t, int,    \
+                                       double, const int*, cudaStream_t);
 FTP_INST(float)
 FTP_INST(double)
 #undef FTP_INST
