@@ -1048,6 +1048,16 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
     if constexpr (PH == 1) {
     // ---- final polynomial F_p, p = 0..3H-1, in the working precision:
     //      [psi^p] (2 MM' d(YM') - YM' d(MM')) = sum_{j+l=p+1} (2l - j) m_j y_l
+    //      with m_j = [psi^j] MM' (j = 0..4H) and y_l = [psi^l] YM' (l = 0..2H,
+    //      y_H = 0), laid out once in the sums' shared memory (dead after the
+    //      assembly) so that the sum is a branch-free convolution.
+    R2* Mx = reinterpret_cast<R2*>(Z64);
+    R2* Yx = Mx + (4 * H + 1);
+    static_assert((6 * H + 2) * sizeof(R2) <= C::G_F - C::G_Z64, "convolution arrays fit");
+    for (int j = gl; j <= 4 * H; j += G) Mx[j] = (j >= 2 * H) ? Aw[j - 2 * H] : cconj(Aw[2 * H - j]);
+    for (int l = gl; l <= 2 * H; l += G)
+      Yx[l] = (l == H) ? mk<R2>(0, 0) : (l > H) ? Bw[l - H] : cconj(Bw[H - l]);
+    __syncwarp();
     R2 Fl[C::NFL];
     R fmax2 = R(0);
 #pragma unroll
@@ -1057,12 +1067,12 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
       if (p < C::NF) {
         const int jlo = p + 1 - 2 * H > 0 ? p + 1 - 2 * H : 0;
         const int jhi = p + 1 < 4 * H ? p + 1 : 4 * H;
+        R cf = (R)(2 * (p + 1) - 3 * jlo);  // 2l - j = 2(p + 1) - 3j, exact
+#pragma unroll 4
         for (int j = jlo; j <= jhi; ++j) {
-          const int l = p + 1 - j;
-          if (l == H) continue;
-          const R2 mj = (j >= 2 * H) ? Aw[j - 2 * H] : cconj(Aw[2 * H - j]);
-          const R2 yl = (l > H) ? Bw[l - H] : cconj(Bw[H - l]);
-          acc = cfma(cscale(mj, (R)(2 * l - j)), yl, acc);
+          const R2 t = cmul(Mx[j], Yx[p + 1 - j]);
+          acc = mk<R2>(fma(cf, t.x, acc.x), fma(cf, t.y, acc.y));
+          cf -= R(3);
         }
         if (p == C::NF - 1) acc.x = R(0);  // F_{D/2} = -conj(F_{D/2}) is imaginary
       }
