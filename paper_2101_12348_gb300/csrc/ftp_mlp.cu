@@ -163,6 +163,35 @@ __device__ __forceinline__ void store_row(unsigned char* tile, int row, int col0
     *reinterpret_cast<uint4*>(tile + tc::core_off(row, col0 + q * 8, HID)) = tc::pack8(v + q * 8);
 }
 
+// The forward kernel's X tiles, prefetched into registers: thread t holds
+// the chunks (row, 8 features) c = t + 128 u, u < KP / 8, of a tile, loaded
+// while the previous tile is in the tensor cores and epilogues.
+template <int KP> struct XChunks {
+  float v[KP / 8][8];
+};
+template <int KP>
+__device__ __forceinline__ void load_x(const float* __restrict__ X, int64_t n, int64_t r0,
+                                       int nfeat, XChunks<KP>& c) {
+#pragma unroll
+  for (int u = 0; u < KP / 8; ++u) {
+    const int t = threadIdx.x + HID * u;
+    const int r = t / (KP / 8), q = t % (KP / 8);
+    const int64_t i = r0 + r;
+    const float* x = X + i * nfeat;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) c.v[u][e] = (i < n && q * 8 + e < nfeat) ? x[q * 8 + e] : 0.f;
+  }
+}
+template <int KP>
+__device__ __forceinline__ void store_x(const XChunks<KP>& c, unsigned char* sX) {
+#pragma unroll
+  for (int u = 0; u < KP / 8; ++u) {
+    const int t = threadIdx.x + HID * u;
+    const int r = t / (KP / 8), q = t % (KP / 8);
+    *reinterpret_cast<uint4*>(sX + tc::core_off(r, q * 8, KP)) = tc::pack8(c.v[u]);
+  }
+}
+
 template <int KP>
 __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restrict__ P, int nfeat,
                                                           const float* __restrict__ X, int64_t n,
@@ -188,9 +217,13 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
   uint32_t phase = 0;
   bool ok = true;
   const int64_t ntiles = (n + HID - 1) / HID;
+  XChunks<KP> xc;
+  if (blockIdx.x < ntiles) load_x<KP>(X, n, (int64_t)blockIdx.x * HID, nfeat, xc);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * HID;
-    stage_x<KP>(X, RowMap{nullptr, 0, n}, n, r0, nfeat, sX);
+    store_x<KP>(xc, sX);
+    // the next tile's features load while this one is in flight
+    if (tile + gridDim.x < ntiles) load_x<KP>(X, n, (tile + gridDim.x) * HID, nfeat, xc);
     mma_sync_point();
     if (tid == 0) {
 #pragma unroll
@@ -203,13 +236,27 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
     phase ^= 1u;
     if (!ok) break;
     tc::fence_after();
-#pragma unroll 1
-    for (int ch = 0; ch < 4; ++ch) {
-      float v[32];
-      tc::tmem_ld32(tl + ch * 32, v);
+    // A1 = bf16(relu(Z1 + b1)): bias in FP32, then two values per conversion
+    // and per ReLU; the next 32 columns load from TMEM while this chunk is
+    // converted
+    uint32_t rb[2][32];
+    tc::tmem_ld32_issue(tl, rb[0]);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + vec[ch * 32 + j], 0.f);
-      store_row(sA1, tid, ch * 32, v);
+    for (int ch = 0; ch < 4; ++ch) {
+      tc::tmem_wait_ld(rb[ch & 1]);
+      if (ch < 3) tc::tmem_ld32_issue(tl + (ch + 1) * 32, rb[(ch + 1) & 1]);
+      const float* v = reinterpret_cast<const float*>(rb[ch & 1]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint4 w;
+        uint32_t* wp = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = q * 8 + 2 * e;
+          wp[e] = tc::relu2(tc::pack2(v[j] + vec[ch * 32 + j], v[j + 1] + vec[ch * 32 + j + 1]));
+        }
+        *reinterpret_cast<uint4*>(sA1 + tc::core_off(tid, ch * 32 + q * 8, HID)) = w;
+      }
     }
     mma_sync_point();
     if (tid == 0) {
@@ -223,16 +270,24 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
     phase ^= 1u;
     if (!ok) break;
     tc::fence_after();
-    float s = 0.f;
-#pragma unroll 1
-    for (int ch = 0; ch < 4; ++ch) {
-      float v[32];
-      tc::tmem_ld32(tl + ch * 32, v);
+    // s = A2 . w3 + b3 with A2 = bf16(relu(Z2 + b2)): FP32 accumulation of
+    // the even and the odd columns in the two halves of a packed pair
+    uint64_t s2 = 0ull;
+    tc::tmem_ld32_issue(tl, rb[0]);
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        s = fmaf(tc::bf16_round(fmaxf(v[j] + vec[HID + ch * 32 + j], 0.f)),
-                 vec[2 * HID + ch * 32 + j], s);
+    for (int ch = 0; ch < 4; ++ch) {
+      tc::tmem_wait_ld(rb[ch & 1]);
+      if (ch < 3) tc::tmem_ld32_issue(tl + (ch + 1) * 32, rb[(ch + 1) & 1]);
+      const float* v = reinterpret_cast<const float*>(rb[ch & 1]);
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const uint32_t a = tc::relu2(
+            tc::pack2(v[j] + vec[HID + ch * 32 + j], v[j + 1] + vec[HID + ch * 32 + j + 1]));
+        s2 = tc::fma2(tc::pk(tc::bf16_lo(a), tc::bf16_hi(a)),
+                      tc::pk(vec[2 * HID + ch * 32 + j], vec[2 * HID + ch * 32 + j + 1]), s2);
+      }
     }
+    const float s = tc::pk_sum(s2);
     if (r0 + tid < n) score[r0 + tid] = s + b3;
     tc::fence_before();
     __syncthreads();
