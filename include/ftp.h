@@ -308,7 +308,7 @@ ftp_status ftp_plan_info(ftp_plan_t plan, int64_t* grid_len, int* half_width, in
  *                  precision (|F(z)| above 8 D eps sum_k |F_k| |z|^k);
  *   resolved       frequencies re-solved from direct FP64 sums: those where
  *                  the a-posteriori estimate of the error of P caused by the
- *                  NFFT sums exceeded 1e-5 (FTP_MIXED) or 1e-10 (FTP_FP64) -
+ *                  NFFT sums exceeded 2.5e-5 (FTP_MIXED) or 1e-10 (FTP_FP64) -
  *                  clustered phases make MM = Var(M) a small difference of
  *                  O(1) sums - and those with a non-converged item;
  *   resolved_nonconverged  the latter kind among them;
@@ -413,7 +413,7 @@ ftp_status ftp_roots_first_phase_ms(ftp_plan_t plan, float* ms);
  * FTP_ERR_INVALID_ARG, and so do pointers to another GPU's memory.
  * Unlike ftp_periodogram it cannot re-solve anything from the observations,
  * which it does not see: items whose estimated error of P from the sums
- * exceeds 1e-5 (FTP_MIXED) or 1e-10 (FTP_FP64) get FTP_FLAG_UNRESOLVED, and
+ * exceeds 2.5e-5 (FTP_MIXED) or 1e-10 (FTP_FP64) get FTP_FLAG_UNRESOLVED, and
  * items that hit the Aberth iteration cap keep FTP_FLAG_NONCONVERGED.  The
  * flags array is the only per-item report of either.  Each call copies its
  * small parameter tables from host memory into the scratch array and waits

@@ -66,10 +66,13 @@ constexpr int kMaxH = 16;
 // Bound on the absolute error of one NFFT sum Z_h (relative to sum w = 1),
 // used by the a-posteriori error estimate of P, and the estimated error of P
 // above which a frequency is re-solved from direct FP64 sums: FP32 NFFT
-// (mixed path; measured at most 2.1e-7 on the long lightcurve with m = 4,
-// sigma = 1.5 against direct FP64 sums) and FP64 NFFT (FP64 path).
-constexpr double kSumErrF32 = 4e-7;
-constexpr double kRedoTolF32 = 1e-5;
+// (mixed path, m = 5, sigma = 1.25: measured at most 5.0e-7 against direct
+// FP64 sums on the long, bank and survey lightcurves; twice that here) and
+// FP64 NFFT (FP64 path).
+constexpr double kSumErrF32 = 1e-6;
+// The estimate is an upper bound of |dP| for sums within that error; a
+// quarter of the 1e-4 tolerance of the mixed path leaves a 4x margin.
+constexpr double kRedoTolF32 = 2.5e-5;
 constexpr double kSumErrF64 = 2e-13;
 constexpr double kRedoTolF64 = 1e-10;
 
