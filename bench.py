@@ -55,8 +55,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="timed steps of the FP64 path (0 skips it)")
-    ap.add_argument("--n-freq", type=int, default=250_000,
-                    help="frequencies of the grid (smaller only for profiling captures)")
+    ap.add_argument("--n-freq", type=int, default=None,
+                    help="frequencies of the grid of the long and bank workloads (default "
+                         "2.5e5 and 1e6; smaller only for profiling captures)")
     ap.add_argument("--workload", choices=["long", "survey", "bank", "screen", "small", "hsweep"],
                     default="long",
                     help="long: one long lightcurve (the headline line); survey: 4096 "
@@ -317,7 +318,7 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.set_device(dev)
     # one lightcurve per rank: rank r analyses its own seeded curve of the
     # workload's shape (curves are independent: no data exchange)
-    lc, tpl, grid = synth.long_curve(nf=args.n_freq, seed=1002 + 1000 * rank)
+    lc, tpl, grid = synth.long_curve(nf=args.n_freq or 250_000, seed=1002 + 1000 * rank)
     nf, D = grid.nf, 6 * tpl.H - 2
     stream = torch.cuda.Stream(device=dev)
     tpls = [(tpl.c, tpl.s)]
@@ -719,7 +720,7 @@ def run_bank(args, world, rank, local, pg):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    lc, bank_all, grid = synth.bank_curve()
+    lc, bank_all, grid = synth.bank_curve(nf=args.n_freq or 1_000_000)
     # templates shared out across ranks (r, r + world, ...): each rank runs
     # its templates on the whole grid; the sums are recomputed per rank
     mine = shard.partition_strided(len(bank_all), world)[rank]

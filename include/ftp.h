@@ -479,6 +479,22 @@ void ftp_mlp_destroy(ftp_mlp_t mlp);
  * ftp_mlp_param_count floats); set also resets the Adam state. */
 ftp_status ftp_mlp_get_params(ftp_mlp_t mlp, float* params);
 ftp_status ftp_mlp_set_params(ftp_mlp_t mlp, const float* params);
+/*
+ * ftp_mlp_get_state / ftp_mlp_set_state - the whole training state, for a
+ * checkpoint: the parameters and Adam's first and second moments (host or
+ * device arrays of ftp_mlp_param_count floats each, none nullable) and the
+ * number of Adam steps taken, which keys the minibatch draws of
+ * ftp_mlp_train and Adam's bias correction.  A handle given the state that
+ * another handle of the same nfeat returned continues training bit for bit
+ * as that handle would have (the gradient reductions have a fixed order).
+ * set_state: steps must lie in [0, 2^31 - 2^20]; FTP_ERR_INVALID_ARG
+ * otherwise or for a null pointer.  Both calls synchronise the handle's
+ * stream.
+ */
+ftp_status ftp_mlp_get_state(ftp_mlp_t mlp, float* params, float* adam_m, float* adam_v,
+                             int64_t* steps);
+ftp_status ftp_mlp_set_state(ftp_mlp_t mlp, const float* params, const float* adam_m,
+                             const float* adam_v, int64_t steps);
 
 /* Scores of n rows of X [n][nfeat] (FP32, host or device) into scores [n]. */
 ftp_status ftp_mlp_forward(ftp_mlp_t mlp, const float* X, int64_t n, float* scores);

@@ -148,6 +148,35 @@ ftp_status ftp_mlp_get_params(ftp_mlp_t h, float* params) {
   return FTP_OK;
 }
 
+ftp_status ftp_mlp_get_state(ftp_mlp_t h, float* params, float* adam_m, float* adam_v,
+                             int64_t* steps) {
+  if (!h || !params || !adam_m || !adam_v || !steps) return FTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const size_t pb = sizeof(float) * (size_t)h->np;
+  MLP_CK(cudaMemcpyAsync(params, h->d_params, pb, cudaMemcpyDefault, h->stream));
+  MLP_CK(cudaMemcpyAsync(adam_m, h->d_m, pb, cudaMemcpyDefault, h->stream));
+  MLP_CK(cudaMemcpyAsync(adam_v, h->d_v, pb, cudaMemcpyDefault, h->stream));
+  MLP_CK(cudaStreamSynchronize(h->stream));
+  *steps = h->step;
+  return FTP_OK;
+}
+
+ftp_status ftp_mlp_set_state(ftp_mlp_t h, const float* params, const float* adam_m,
+                             const float* adam_v, int64_t steps) {
+  // the step count keys the minibatch draws and Adam's bias correction (an
+  // int in the update kernel)
+  if (!h || !params || !adam_m || !adam_v || steps < 0 || steps > (int64_t)INT32_MAX - (1 << 20))
+    return FTP_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const size_t pb = sizeof(float) * (size_t)h->np;
+  MLP_CK(cudaMemcpyAsync(h->d_params, params, pb, cudaMemcpyDefault, h->stream));
+  MLP_CK(cudaMemcpyAsync(h->d_m, adam_m, pb, cudaMemcpyDefault, h->stream));
+  MLP_CK(cudaMemcpyAsync(h->d_v, adam_v, pb, cudaMemcpyDefault, h->stream));
+  MLP_CK(cudaStreamSynchronize(h->stream));
+  h->step = steps;
+  return FTP_OK;
+}
+
 ftp_status ftp_mlp_create(ftp_mlp_t* out, int nfeat, const float* params, uint64_t seed,
                           int device, void* cuda_stream) {
   if (!out) return FTP_ERR_INVALID_ARG;

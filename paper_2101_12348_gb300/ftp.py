@@ -48,7 +48,8 @@ EXPORTS = ("ftp_plan", "ftp_sums", "ftp_periodogram", "ftp_batch", "ftp_destroy"
            "ftp_set_batch_tuning", "ftp_get_batch_tuning", "ftp_batch_autotune",
            "ftp_set_positive_amplitude", "ftp_multiband_periodogram",
            "ftp_shared_multiband", "ftp_roots_first_phase_ms", "ftp_set_solver_limits",
-           "ftp_set_fault_injection", "ftp_alu_peak")
+           "ftp_set_fault_injection", "ftp_alu_peak", "ftp_mlp_get_state",
+           "ftp_mlp_set_state")
 
 
 class FtpGrid(C.Structure):
@@ -111,6 +112,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.ftp_mlp_destroy.restype = None
     lib.ftp_mlp_get_params.argtypes = [vp, vp]
     lib.ftp_mlp_set_params.argtypes = [vp, vp]
+    lib.ftp_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
+    lib.ftp_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
     lib.ftp_mlp_forward.argtypes = [vp, vp, i64, vp]
     lib.ftp_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp]
     lib.ftp_mlp_train.argtypes = [vp, vp, vp, i64, i64, i64, f32, u64, vp]
@@ -280,6 +283,19 @@ def ftp_mlp_get_params(mlp: int, out) -> None:
 
 def ftp_mlp_set_params(mlp: int, params) -> None:
     _check(load().ftp_mlp_set_params(mlp, _ptr(params)), "ftp_mlp_set_params")
+
+
+def ftp_mlp_get_state(mlp: int, params, adam_m, adam_v) -> int:
+    """Fills the three arrays; returns the number of Adam steps taken."""
+    steps = C.c_int64(0)
+    _check(load().ftp_mlp_get_state(mlp, _ptr(params), _ptr(adam_m), _ptr(adam_v),
+                                    C.byref(steps)), "ftp_mlp_get_state")
+    return int(steps.value)
+
+
+def ftp_mlp_set_state(mlp: int, params, adam_m, adam_v, steps: int) -> None:
+    _check(load().ftp_mlp_set_state(mlp, _ptr(params), _ptr(adam_m), _ptr(adam_v), int(steps)),
+           "ftp_mlp_set_state")
 
 
 def ftp_mlp_forward(mlp: int, X, n: int, scores) -> None:

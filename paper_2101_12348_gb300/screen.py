@@ -11,6 +11,8 @@ and sequences the calls.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from . import ftp
@@ -35,6 +37,64 @@ class Surrogate:
 
     def set_params(self, p) -> None:
         ftp.ftp_mlp_set_params(self.h, np.ascontiguousarray(p, dtype=np.float32))
+
+    def state(self) -> dict:
+        """Parameters, Adam moments and the Adam step count (host copies)."""
+        st = {k: np.empty(self.nparams, dtype=np.float32) for k in ("params", "adam_m", "adam_v")}
+        st["steps"] = ftp.ftp_mlp_get_state(self.h, st["params"], st["adam_m"], st["adam_v"])
+        return st
+
+    def set_state(self, st: dict) -> None:
+        f32 = [np.ascontiguousarray(st[k], dtype=np.float32) for k in ("params", "adam_m", "adam_v")]
+        if any(a.shape != (self.nparams,) for a in f32):
+            raise ValueError(f"training state of {self.nparams} parameters expected")
+        ftp.ftp_mlp_set_state(self.h, *f32, int(st["steps"]))
+
+    def save(self, path: str) -> None:
+        """Checkpoint of the whole training state (.npz), written to a
+        temporary file and renamed, so a crash leaves the old one intact."""
+        st = self.state()
+        tmp = f"{path}.tmp-{os.getpid()}"
+        with open(tmp, "wb") as f:
+            np.savez(f, H_feat=np.int64(self.H_feat), steps=np.int64(st["steps"]),
+                     params=st["params"], adam_m=st["adam_m"], adam_v=st["adam_v"])
+            f.flush()
+            os.fsync(f.fileno())
+        os.replace(tmp, path)
+
+    @classmethod
+    def load(cls, path: str, device: int = 0) -> "Surrogate":
+        with np.load(path) as z:
+            sur = cls(int(z["H_feat"]), params=z["params"], device=device)
+            sur.set_state({k: z[k] for k in ("params", "adam_m", "adam_v", "steps")})
+        return sur
+
+    def train_to(self, X, y, rows: int, total_steps: int, checkpoint: str, every: int,
+                 batch: int = 2048, lr: float = 2e-3, seed: int = 1) -> int:
+        """Train until `total_steps` Adam steps have been taken in all,
+        writing the training state to `checkpoint` every `every` steps and
+        at the end.  If `checkpoint` exists it is loaded first, so calling
+        this again with the same arguments after an interruption continues
+        where the last checkpoint left off and ends in the same state as an
+        uninterrupted run.  Returns the steps taken by this call."""
+        if every < 1 or total_steps < 0:
+            raise ValueError("every >= 1 and total_steps >= 0 required")
+        if os.path.exists(checkpoint):
+            with np.load(checkpoint) as z:
+                if int(z["H_feat"]) != self.H_feat:
+                    raise ValueError(f"{checkpoint} holds a network of H_feat = {int(z['H_feat'])}")
+                self.set_state({k: z[k] for k in ("params", "adam_m", "adam_v", "steps")})
+        done = self.state()["steps"]
+        if done > total_steps:
+            raise ValueError(f"{checkpoint} is already past {total_steps} steps ({done})")
+        taken = 0
+        while done < total_steps:
+            k = min(every, total_steps - done)
+            self.train(X, y, rows, k, batch, lr, seed)
+            done += k
+            taken += k
+            self.save(checkpoint)
+        return taken
 
     def forward(self, X, n=None, scores=None):
         n = X.shape[0] if n is None else n
