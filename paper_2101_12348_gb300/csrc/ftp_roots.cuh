@@ -288,6 +288,12 @@ __device__ __noinline__ bool pseudo_zero(R2 z, const R2* Fs) {
 template <int NS, int D, bool kFast, typename R, typename R2>
 __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const int (&idx)[NS],
                                             const R2* Fs, R2* Zs, R tol) {
+  // unroll factors of the Horner and pair loops (measured per H on the
+  // long lightcurve): 4 for Horner, 5 where D + 1 is a multiple of 5 (H = 6,
+  // 11); 2 for the pair loop at five or more slots per lane or low degree,
+  // where 4 costs registers and scheduling, else 4
+  constexpr int kUH = (D + 1) % 5 == 0 && D <= 64 ? 5 : 4;
+  constexpr int kUP = NS >= 5 || D < 16 ? 2 : 4;
   R2 uu[NS], p[NS], dp[NS], S[NS];
   bool outside[NS];
 #pragma unroll
@@ -313,7 +319,7 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
       UYn[q] = pk2(-uu[2 * q].y, -uu[2 * q + 1].y);
       PX[q] = PY[q] = DX[q] = DY[q] = 0ull;
     }
-#pragma unroll 2
+#pragma unroll (kUH)
     for (int c = D; c >= 0; --c) {
       const R2 f = Fs[c];
       const f2p FX = pk2(f.x, f.x), FY = pk2(f.y, f.y);
@@ -342,7 +348,7 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
       SX[q] = SYn[q] = 0ull;
     }
     const f2p tiny2 = pk2(1e-30f, 1e-30f);
-#pragma unroll 2
+#pragma unroll (kUP)
     for (int j = 0; j < D; ++j) {
       const R2 zj = Zs[j];
       const f2p JX = pk2(zj.x, zj.x), JY = pk2(zj.y, zj.y);
@@ -400,17 +406,23 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
   }
 #pragma unroll
   for (int r = 0; r < NS; ++r) {
-    // Newton ratio p/p'.  Outside the disc use the anti-self-inversive
-    // identity p(z) = -z^D conj(p(u)), u = 1/conj(z):
-    //   p/p' = z / (D - conj(p'(u)/p(u)) / z).
-    R2 N;
+    // Aberth correction w = N / (1 - N S) = 1 / (p'/p - S), N = p/p' the
+    // Newton ratio, formed as one quotient.  Outside the disc the
+    // anti-self-inversive identity p(z) = -z^D conj(p(u)), u = 1/conj(z),
+    // gives p'/p = (D z - conj(p'(u)/p(u))) / z^2:
+    //   inside:  w = p / (p' - p S);
+    //   outside: w = z^2 / (D z - conj(p'(u)/p(u)) - S z^2).
+    R2 num, den;
     if (outside[r]) {
       const R2 q = cconj(cdiv(dp[r], p[r]));
-      N = cdiv(z[r], csub(mk<R2>((R)D, 0), cdiv(q, z[r])));
+      const R2 z2 = cmul(z[r], z[r]);
+      num = z2;
+      den = csub(csub(mk<R2>(R(D) * z[r].x, R(D) * z[r].y), q), cmul(S[r], z2));
     } else {
-      N = cdiv(p[r], dp[r]);
+      num = p[r];
+      den = csub(dp[r], cmul(p[r], S[r]));
     }
-    R2 w = cdiv(N, csub(mk<R2>(1, 0), cmul(N, S[r])));
+    R2 w = cdiv(num, den);
     if (!finite2(w)) w = mk<R2>(0, 0);
     if (!conv[r]) {
       const R zz = cabs2(z[r]);
