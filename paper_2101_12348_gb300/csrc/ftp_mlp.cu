@@ -14,6 +14,12 @@
 //   g_W2 = bf16(dZ2)^T A1, dA1 = bf16(dZ2) W2b, dZ1 = dA1 * [Z1 > 0]
 //   g_b1 = sum dZ1, g_W1 = bf16(dZ1)^T bf16(x)
 //
+// The forward kernel adds b1 and b2 on the tensor core: W1's operand tile
+// carries both as three-term BF16 splits (b to about 24 bits, so Z1 and Z2
+// are the same FP32 sums), b1 against ones in the X tile and b2 against an
+// indicator operand, which keeps the shared-memory pipe, the forward's
+// bound, free of per-tile bias loads.
+//
 // Tiles of 128 rows.  One thread owns one row (its TMEM lane).  Every
 // operand tile is written once to shared memory in the core-matrix layout of
 // ftp_tc.cuh; the products that need a transposed operand read the same bytes
@@ -39,7 +45,8 @@ template <int KP> struct FwdL {
   static constexpr int W2 = W1 + HID * KP * 2;
   static constexpr int X = W2 + T128;
   static constexpr int A1 = X + HID * KP * 2;
-  static constexpr int VEC = A1 + T128;  // b1, b2, bf16(w3): [3][128] FP32
+  static constexpr int IND = A1 + T128;  // 8 x KP indicator rows (b2 selector)
+  static constexpr int VEC = IND + 8 * KP * 2;  // b1, b2, bf16(w3): [3][128] FP32
   static constexpr int BAR = VEC + 3 * HID * 4;
   static constexpr int SLOT = BAR + 16;
   static constexpr int BYTES = SLOT + 16;
@@ -71,9 +78,21 @@ __device__ __forceinline__ void mma_sync_point() {
 }
 
 // Weights into shared memory as BF16 operand tiles, vectors as FP32.
+// With `fold` (the forward kernel), W1's operand tile also carries the
+// biases as three-term BF16 splits b = hi + mid + lo (hi = bf16(b), mid =
+// bf16(b - hi), lo = bf16(b - hi - mid): b to about 24 bits): b1 in columns
+// nfeat .. nfeat + 2, which meet ones in the X tile, and b2 in columns
+// nfeat + 3 .. nfeat + 5, which meet ones in the indicator rows; so the
+// tensor core adds both, in FP32, and no thread loads a bias per tile.
+__device__ __forceinline__ float bias_part(float b, int part) {
+  const float hi = tc::bf16_round(b);
+  const float mid = tc::bf16_round(b - hi);
+  return part == 0 ? hi : part == 1 ? mid : tc::bf16_round(b - hi - mid);
+}
+
 template <int KP>
 __device__ void load_weights(const float* __restrict__ P, int nfeat, unsigned char* sW1,
-                             unsigned char* sW2, float* vec) {
+                             unsigned char* sW2, float* vec, bool fold = false) {
   const float* W1 = P;
   const float* b1 = P + HID * nfeat;
   const float* W2 = b1 + HID;
@@ -84,8 +103,11 @@ __device__ void load_weights(const float* __restrict__ P, int nfeat, unsigned ch
     float v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int k = q * 8 + e;
-      v[e] = k < nfeat ? W1[r * nfeat + k] : 0.f;
+      const int k = q * 8 + e, f = k - nfeat;
+      v[e] = k < nfeat              ? W1[r * nfeat + k]
+             : fold && f < 3        ? bias_part(b1[r], f)
+             : fold && f < 6        ? bias_part(b2[r], f - 3)
+                                    : 0.f;
     }
     *reinterpret_cast<uint4*>(sW1 + tc::core_off(r, q * 8, KP)) = tc::pack8(v);
   }
@@ -179,7 +201,10 @@ __device__ __forceinline__ void load_x(const float* __restrict__ X, int64_t n, i
     const int64_t i = r0 + r;
     const float* x = X + i * nfeat;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) c.v[u][e] = (i < n && q * 8 + e < nfeat) ? x[q * 8 + e] : 0.f;
+    for (int e = 0; e < 8; ++e) {
+      const int k = q * 8 + e;
+      c.v[u][e] = k < nfeat ? (i < n ? x[k] : 0.f) : k < nfeat + 3 ? 1.f : 0.f;
+    }
   }
 }
 template <int KP>
@@ -189,6 +214,29 @@ __device__ __forceinline__ void store_x(const XChunks<KP>& c, unsigned char* sX)
     const int t = threadIdx.x + HID * u;
     const int r = t / (KP / 8), q = t % (KP / 8);
     *reinterpret_cast<uint4*>(sX + tc::core_off(r, q * 8, KP)) = tc::pack8(c.v[u]);
+  }
+}
+
+// bf16(relu(Z)) of this thread's TMEM lane (128 FP32 columns, biases already
+// in Z) into its row of a 128 x 128 operand tile: ReLU and rounding in one
+// conversion per pair; the next 32 columns load from TMEM while this chunk
+// is converted.
+__device__ __forceinline__ void relu_epilogue(uint32_t tl, unsigned char* tile, int row) {
+  uint32_t rb[2][32];
+  tc::tmem_ld32_issue(tl, rb[0]);
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) {
+    tc::tmem_wait_ld(rb[ch & 1]);
+    if (ch < 3) tc::tmem_ld32_issue(tl + (ch + 1) * 32, rb[(ch + 1) & 1]);
+    const float* v = reinterpret_cast<const float*>(rb[ch & 1]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 w;
+      uint32_t* wp = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) wp[e] = tc::pack2_relu(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1]);
+      *reinterpret_cast<uint4*>(tile + tc::core_off(row, ch * 32 + q * 8, HID)) = w;
+    }
   }
 }
 
@@ -206,7 +254,20 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
   const int tid = threadIdx.x, warp = tid >> 5;
   if (status[ST_CODE] != DEV_OK) return;
   if (warp == 0) tc::tmem_alloc(slot, 128);
-  load_weights<KP>(P, nfeat, sW1, sW2, vec);
+  load_weights<KP>(P, nfeat, sW1, sW2, vec, true);
+  // indicator rows: ones in the b2 columns of W1's tile; the descriptor
+  // repeats these 8 rows over all 128 (row-group stride 0)
+  unsigned char* sI = sm + L::IND;
+  for (int c = tid; c < 8 * (KP / 8); c += blockDim.x) {
+    const int r = c % 8, q = c / 8;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int f = q * 8 + e - nfeat;
+      v[e] = f >= 3 && f < 6 ? 1.f : 0.f;
+    }
+    *reinterpret_cast<uint4*>(sI + tc::core_off(r, q * 8, KP)) = tc::pack8(v);
+  }
   const float b3 = P[mlp_param_count(nfeat) - 1];
   if (tid == 0) tc::bar_init(bar);
   mma_sync_point();
@@ -214,6 +275,7 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
   constexpr uint32_t id = tc::idesc_bf16(128, 128, false, false);
   const uint32_t aX = tc::sa(sX), aW1 = tc::sa(sW1), aA1 = tc::sa(sA1), aW2 = tc::sa(sW2);
+  const uint32_t aI = tc::sa(sI);
   uint32_t phase = 0;
   bool ok = true;
   const int64_t ntiles = (n + HID - 1) / HID;
@@ -236,55 +298,47 @@ __global__ void __launch_bounds__(128) mlp_forward_kernel(const float* __restric
     phase ^= 1u;
     if (!ok) break;
     tc::fence_after();
-    // A1 = bf16(relu(Z1 + b1)): bias in FP32, then two values per conversion
-    // and per ReLU; the next 32 columns load from TMEM while this chunk is
-    // converted
-    uint32_t rb[2][32];
-    tc::tmem_ld32_issue(tl, rb[0]);
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-      tc::tmem_wait_ld(rb[ch & 1]);
-      if (ch < 3) tc::tmem_ld32_issue(tl + (ch + 1) * 32, rb[(ch + 1) & 1]);
-      const float* v = reinterpret_cast<const float*>(rb[ch & 1]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint4 w;
-        uint32_t* wp = reinterpret_cast<uint32_t*>(&w);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = q * 8 + 2 * e;
-          wp[e] = tc::relu2(tc::pack2(v[j] + vec[ch * 32 + j], v[j + 1] + vec[ch * 32 + j + 1]));
-        }
-        *reinterpret_cast<uint4*>(sA1 + tc::core_off(tid, ch * 32 + q * 8, HID)) = w;
-      }
-    }
+    // A1 = bf16(relu(Z1)) into its operand tile (b1 came with the MMA)
+    relu_epilogue(tl, sA1, tid);
     mma_sync_point();
     if (tid == 0) {
+      // Z2 = b2 (indicator rows x W1's tile), then += A1 W2^T
+#pragma unroll
+      for (int ks = 0; ks < KP / 16; ++ks)
+        tc::mma_bf16(tmem, tc::sdesc(aI + ks * 256, 128, 0),
+                     tc::sdesc(aW1 + ks * 256, 128, (KP / 8) * 128), id, ks > 0);
 #pragma unroll
       for (int ks = 0; ks < HID / 16; ++ks)
         tc::mma_bf16(tmem, tc::sdesc(aA1 + ks * 256, 128, 2048),
-                     tc::sdesc(aW2 + ks * 256, 128, 2048), id, ks > 0);
+                     tc::sdesc(aW2 + ks * 256, 128, 2048), id, 1);
       tc::mma_commit(bar);
     }
     ok = __syncthreads_and(tc::bar_wait(bar, phase));
     phase ^= 1u;
     if (!ok) break;
     tc::fence_after();
-    // s = A2 . w3 + b3 with A2 = bf16(relu(Z2 + b2)): FP32 accumulation of
-    // the even and the odd columns in the two halves of a packed pair
+    // s = A2 . w3 + b3 with A2 = bf16(relu(Z2)): ReLU and rounding in one
+    // conversion per pair, FP32 accumulation of the even and the odd columns
+    // in the two halves of a packed pair
     uint64_t s2 = 0ull;
-    tc::tmem_ld32_issue(tl, rb[0]);
+    {
+      uint32_t rb[2][32];
+      tc::tmem_ld32_issue(tl, rb[0]);
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-      tc::tmem_wait_ld(rb[ch & 1]);
-      if (ch < 3) tc::tmem_ld32_issue(tl + (ch + 1) * 32, rb[(ch + 1) & 1]);
-      const float* v = reinterpret_cast<const float*>(rb[ch & 1]);
+      for (int ch = 0; ch < 4; ++ch) {
+        tc::tmem_wait_ld(rb[ch & 1]);
+        if (ch < 3) tc::tmem_ld32_issue(tl + (ch + 1) * 32, rb[(ch + 1) & 1]);
+        const float* v = reinterpret_cast<const float*>(rb[ch & 1]);
+        const ulonglong2* wq = reinterpret_cast<const ulonglong2*>(vec + 2 * HID + ch * 32);
 #pragma unroll
-      for (int j = 0; j < 32; j += 2) {
-        const uint32_t a = tc::relu2(
-            tc::pack2(v[j] + vec[HID + ch * 32 + j], v[j + 1] + vec[HID + ch * 32 + j + 1]));
-        s2 = tc::fma2(tc::pk(tc::bf16_lo(a), tc::bf16_hi(a)),
-                      tc::pk(vec[2 * HID + ch * 32 + j], vec[2 * HID + ch * 32 + j + 1]), s2);
+        for (int j = 0; j < 32; j += 4) {
+          const ulonglong2 w = wq[j / 4];  // a 16-byte broadcast load: two w3 pairs
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const uint32_t a2 = tc::pack2_relu(v[j + 2 * e], v[j + 2 * e + 1]);
+            s2 = tc::fma2(tc::pk(tc::bf16_lo(a2), tc::bf16_hi(a2)), e ? w.y : w.x, s2);
+          }
+        }
       }
     }
     const float s = tc::pk_sum(s2);
@@ -546,7 +600,7 @@ int launch_mlp_forward(const float* params, int nfeat, const float* X, int64_t n
   // three CTAs per SM (128 TMEM columns each) so one CTA's epilogue overlaps
   // another's MMA
   const int64_t grid = ntiles < 3 * (int64_t)num_sms ? ntiles : 3 * (int64_t)num_sms;
-  if (nfeat <= 16) {
+  if (nfeat + 6 <= 16) {  // the biases take six columns of W1's tile
     static int once = set_smem(mlp_forward_kernel<16>, FwdL<16>::BYTES);
     if (once) return -1;
     mlp_forward_kernel<16><<<(unsigned)grid, 128, FwdL<16>::BYTES, s>>>(params, nfeat, X, n,

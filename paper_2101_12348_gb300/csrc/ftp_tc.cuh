@@ -197,11 +197,12 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
-// max(x, 0) of both halves of a packed BF16 pair.  Rounding keeps the sign,
-// so bf16(max(z, 0)) = max(bf16(z), 0): the ReLU may follow the rounding.
-__device__ __forceinline__ uint32_t relu2(uint32_t v) {
+// Two FP32 values as a packed BF16 pair of max(v, 0), rounded to nearest
+// even, lo in the low half: one conversion instruction for both, ReLU
+// included (rounding keeps the sign, so this is also max(bf16(v), 0)).
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
   uint32_t d;
-  asm("max.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(v), "r"(0u));
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
 // The two halves of a packed BF16 pair as FP32 (exact).
