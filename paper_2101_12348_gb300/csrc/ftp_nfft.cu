@@ -141,18 +141,31 @@ __global__ void __launch_bounds__(256) moments_pass1(const double* __restrict__ 
   p.nbad = block_reduce(nbad, shl, OpSum());
   if (threadIdx.x == 0) part[blockIdx.x] = p;
   if (!last_block(ticket)) return;
+  // the last block reduces the partials with all its threads (L2 loads: the
+  // other blocks wrote them)
+  s0 = s1 = sy = 0;
+  ymin = INFINITY;
+  ymax = -INFINITY;
+  nzero = nbad = 0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    const MomentPartial* r = part + b;
+    s0 += __ldcg(&r->s0);
+    s1 += __ldcg(&r->s1);
+    sy += __ldcg(&r->sy);
+    ymin = fmin(ymin, __ldcg(&r->ymin));
+    ymax = fmax(ymax, __ldcg(&r->ymax));
+    nzero += __ldcg(&r->nzero);
+    nbad += __ldcg(&r->nbad);
+  }
+  MomentPartial q;
+  q.s0 = block_reduce(s0, shd, OpSum());
+  q.s1 = block_reduce(s1, shd, OpSum());
+  q.sy = block_reduce(sy, shd, OpSum());
+  q.ymin = block_reduce(ymin, shd, OpMin());
+  q.ymax = block_reduce(ymax, shd, OpMax());
+  q.nzero = block_reduce(nzero, shl, OpSum());
+  q.nbad = block_reduce(nbad, shl, OpSum());
   if (threadIdx.x == 0) {
-    MomentPartial q = part[0];
-    for (unsigned b = 1; b < gridDim.x; ++b) {
-      const MomentPartial r = part[b];
-      q.s0 += r.s0;
-      q.s1 += r.s1;
-      q.sy += r.sy;
-      q.ymin = fmin(q.ymin, r.ymin);
-      q.ymax = fmax(q.ymax, r.ymax);
-      q.nzero += r.nzero;
-      q.nbad += r.nbad;
-    }
     finish_pass1(q, n, moments, status);
     *ticket = 0u;  // ready for the next reduction
   }
@@ -177,9 +190,10 @@ __global__ void __launch_bounds__(256) moments_pass2(const double* __restrict__ 
   yy = block_reduce(yy, shd, OpSum());
   if (threadIdx.x == 0) part[blockIdx.x] = yy;
   if (!last_block(ticket)) return;
+  double tot = 0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) tot += __ldcg(part + b);
+  tot = block_reduce(tot, shd, OpSum());
   if (threadIdx.x == 0) {
-    double tot = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) tot += part[b];
     moments[MO_YY] = tot / moments[MO_WSUM];
     *ticket = 0u;
   }

@@ -1124,35 +1124,32 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
       Lg[q] = __log2f(fmaf(fx, fx, fmaf(fy, fy, 1.17549435e-38f)));
     }
     __syncwarp();
-    // Vertices: lane 0 of each group runs a monotone chain over the left half
-    // k = 0..D/2 (a point is popped unless strictly above the chord), and the
-    // hull's left half is that chain while it still rises — by symmetry the
-    // rest lies under the horizontal edge to the mirror vertex.  The same set
-    // as testing every point against all D + 1 points (strict: collinear
-    // points are not vertices), in O(D) instead of O(D^2) work per item.
-    unsigned long long vmask = 1ull;  // k = 0 is always a vertex
-    if (gl == 0) {
-      unsigned char* stk = reinterpret_cast<unsigned char*>(Lg + (HD + 1));
-      int sz = 0;
-#pragma unroll 1
-      for (int k = 0; k <= HD; ++k) {
-        const float Lk = Lg[k];
-        while (sz >= 2) {
-          const int o = stk[sz - 2], q = stk[sz - 1];
-          const float cr = (float)(q - o) * (Lk - Lg[o]) - (float)(k - o) * (Lg[q] - Lg[o]);
-          if (cr >= 0.0f) --sz;  // q not strictly above the chord o -> k (NaN: kept)
-          else break;
-        }
-        stk[sz++] = (unsigned char)k;
+    // Vertices of the upper hull of the left half k = 0..D/2 that it reaches
+    // while still rising — by symmetry the rest of the hull lies under the
+    // horizontal edge to the mirror vertex.  Point q is a hull vertex iff it
+    // lies strictly above every chord from a point left of it to a point
+    // right of it, i.e. iff L(q) = min over o < q of the slope o -> q exceeds
+    // R(q) = max over k > q of the slope q -> k; L(q) is then the slope of
+    // the hull edge into q, so the hull still rises into q iff L(q) > 0
+    // (collinear points are not vertices; k = 0 always is).  The lanes of a
+    // group test their points in parallel, O(D^2 / G) independent slopes per
+    // lane, where a monotone chain would be a serial O(D) walk on one lane.
+    unsigned long long vmask = 0ull;
+    for (int q = gl; q <= HD; q += G) {
+      if (q == 0) continue;
+      const float Lq = Lg[q];
+      float lo = 3.0e38f, hi = -3.0e38f;
+#pragma unroll 4
+      for (int j = 0; j <= HD; ++j) {
+        const float sl = (Lq - Lg[j]) * fast_rcp((float)(q - j));  // slope j -> q (q -> j)
+        if (j < q) lo = fminf(lo, sl);
+        if (j > q) hi = fmaxf(hi, sl);
       }
-#pragma unroll 1
-      for (int i = 1; i < sz; ++i) {
-        const int p = stk[i - 1], q = stk[i];
-        if (!(Lg[q] > Lg[p])) break;
-        vmask |= 1ull << q;
-      }
+      if (lo > hi && lo > 0.0f && Lq == Lq) vmask |= 1ull << q;  // (a NaN point is none)
     }
-    vmask = __shfl_sync(0xffffffffu, vmask, 0, G);
+#pragma unroll
+    for (int sh = G / 2; sh > 0; sh >>= 1) vmask |= __shfl_xor_sync(0xffffffffu, vmask, sh, G);
+    vmask |= 1ull;
 
     // ---- (c) Aberth-Ehrlich on F (degree D), roots i = r*G + gl
     R2 z[RR];
