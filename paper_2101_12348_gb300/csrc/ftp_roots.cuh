@@ -70,6 +70,11 @@ struct Cfg {
   // FP64-class steps: float-float on the mixed path (FP32 sums and Aberth),
   // native FP64 on the FP64 path and the re-solve pass (FP64 sums)
   static constexpr bool kDD = kFast && sizeof(S2) == 8;
+  // Off-circle roots settle early (aberth_step) in that same main mixed
+  // kernel only, and at H >= 8: the FP64 path and the re-solve passes iterate
+  // every root to the tolerance, and below H = 8 the test costs about what
+  // the iterations it saves do (measured at H = 2, 4, 6).
+  static constexpr bool kSettle = kDD && H >= 8;
   using W = std::conditional_t<kDD, wide::dd, double>;
   using WC = typename wide::CT<W>::type;
   static constexpr int D = 6 * H - 2;
@@ -281,13 +286,35 @@ __device__ __noinline__ bool pseudo_zero(R2 z, const R2* Fs) {
 }
 
 // ------------------------------------------------------------ Aberth step
+// Only the zeros of F on the unit circle are stationary points of P (Section
+// 2, end); the others come in pairs z, 1/conj(z) and serve the candidate
+// list only through their projections onto the circle, which cannot beat the
+// best stationary value.  So a root may stop iterating (be "settled") before
+// it meets the tolerance once it is known to lie off the circle: its
+// correction w is
+//   - small:            |w| < kSettleStep max(1, |z|),
+//   - a Newton step:    the repulsion term of the Aberth denominator is at
+//                       most kSettleDom of the Newton term (|p S| <= 0.1
+//                       |p'|), so w ~ p/p' and the root is within ~|w| of z
+//                       (and no other approximation lies within ~10 |w| of z,
+//                       whose 1/(z - z_j) would dominate S),
+//   - far from the circle: | |z| - 1 | > kSettleDist |w| + kSettleGap.
+// The settled root keeps its position in the pair sums of the others, which
+// still converge to the tolerance (the fixed points of the iteration are the
+// zeros of F whatever the other approximations are).
+constexpr float kSettleStep = 1e-2f, kSettleDom = 0.1f, kSettleDist = 50.0f,
+                kSettleGap = 1e-3f;
+
 // One Aberth-Ehrlich iteration for the NS root slots of a lane.  Slot r holds
 // root idx[r] of the item (idx < 0: an empty slot, marked converged), z[r] its
 // position; Fs holds F's D + 1 coefficients and Zs the positions of all D
 // roots of the item (read for the pair sums, written back at the end).
-template <int NS, int D, bool kFast, typename R, typename R2>
+// kSettle: roots known to lie off the unit circle stop early (above) and are
+// marked in settled[] (one byte per root of the item).
+template <int NS, int D, bool kFast, bool kSettle, typename R, typename R2>
 __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const int (&idx)[NS],
-                                            const R2* Fs, R2* Zs, R tol) {
+                                            const R2* Fs, R2* Zs, R tol,
+                                            unsigned char* settled) {
   // unroll factors of the Horner and pair loops (measured per H on the
   // long lightcurve): 4 for Horner, 5 where D + 1 is a multiple of 5 (H = 6,
   // 11); 2 for the pair loop at five or more slots per lane or low degree,
@@ -412,21 +439,48 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
     // gives p'/p = (D z - conj(p'(u)/p(u))) / z^2:
     //   inside:  w = p / (p' - p S);
     //   outside: w = z^2 / (D z - conj(p'(u)/p(u)) - S z^2).
-    R2 num, den;
+    // den = newt - rep: the Newton term (z^2 p'/p outside, p' inside) and
+    // the repulsion term of the other roots (S z^2 outside, p S inside)
+    R2 num, den, newt, rep;
     if (outside[r]) {
       const R2 q = cconj(cdiv(dp[r], p[r]));
       const R2 z2 = cmul(z[r], z[r]);
       num = z2;
-      den = csub(csub(mk<R2>(R(D) * z[r].x, R(D) * z[r].y), q), cmul(S[r], z2));
+      if constexpr (kSettle) {
+        newt = csub(mk<R2>(R(D) * z[r].x, R(D) * z[r].y), q);
+        rep = cmul(S[r], z2);
+        den = csub(newt, rep);
+      } else {
+        den = csub(csub(mk<R2>(R(D) * z[r].x, R(D) * z[r].y), q), cmul(S[r], z2));
+      }
     } else {
       num = p[r];
-      den = csub(dp[r], cmul(p[r], S[r]));
+      if constexpr (kSettle) {
+        newt = dp[r];
+        rep = cmul(p[r], S[r]);
+        den = csub(newt, rep);
+      } else {
+        den = csub(dp[r], cmul(p[r], S[r]));
+      }
     }
     R2 w = cdiv(num, den);
     if (!finite2(w)) w = mk<R2>(0, 0);
     if (!conv[r]) {
       const R zz = cabs2(z[r]);
-      conv[r] = cabs2(w) <= tol * tol * (zz > R(1) ? zz : R(1));
+      if constexpr (kSettle) {
+        const R sc = zz > R(1) ? zz : R(1);
+        const R w2 = cabs2(w);
+        bool done = w2 <= tol * tol * sc;
+        if (!done && w2 < R(kSettleStep * kSettleStep) * sc &&
+            cabs2(rep) <= R(kSettleDom * kSettleDom) * cabs2(newt)) {
+          const R az = zz * fast_rsqrt(zz), aw = w2 * fast_rsqrt(w2);  // w2 > 0 here
+          done = fabs(az - R(1)) > R(kSettleDist) * aw + R(kSettleGap);
+          if (done) settled[idx[r]] = 1;
+        }
+        conv[r] = done;
+      } else {
+        conv[r] = cabs2(w) <= tol * tol * (zz > R(1) ? zz : R(1));
+      }
       z[r] = csub(z[r], w);
     }
   }
@@ -440,9 +494,10 @@ __device__ __forceinline__ void aberth_step(R2 (&z)[NS], bool (&conv)[NS], const
 // Iterations over NS slots per lane until every root converged (false) or,
 // if NT < NS, until every group of the warp has at most NT * G unconverged
 // roots (true: time to compact).
-template <int G, int NS, int NT, int D, bool kAccept, typename R, typename R2>
+template <int G, int NS, int NT, int D, bool kAccept, bool kSettle, typename R, typename R2>
 __device__ __forceinline__ bool aberth_run(R2 (&z)[NS], bool (&conv)[NS], const int (&idx)[NS],
-                                           const R2* Fs, R2* Zs, R tol, int& iters, int maxit) {
+                                           const R2* Fs, R2* Zs, R tol, int& iters, int maxit,
+                                           unsigned char* settled) {
 #pragma unroll 1
   for (; iters < maxit; ++iters) {
     if constexpr (kAccept) {
@@ -472,7 +527,7 @@ __device__ __forceinline__ bool aberth_run(R2 (&z)[NS], bool (&conv)[NS], const 
       for (int sh = G; sh < 32; sh <<= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, sh));
       if (wmax <= NT * G) return true;
     }
-    aberth_step<NS, D, sizeof(R) == 4>(z, conv, idx, Fs, Zs, tol);
+    aberth_step<NS, D, sizeof(R) == 4, kSettle>(z, conv, idx, Fs, Zs, tol, settled);
   }
   return false;
 }
@@ -1151,7 +1206,11 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
     for (int sh = G / 2; sh > 0; sh >>= 1) vmask |= __shfl_xor_sync(0xffffffffu, vmask, sh, G);
     vmask |= 1ull;
 
-    // ---- (c) Aberth-Ehrlich on F (degree D), roots i = r*G + gl
+    // ---- (c) Aberth-Ehrlich on F (degree D), roots i = r*G + gl.  The
+    //      settled-root marks follow the compaction lists (D shorts) in the
+    //      sums' shared memory, clear of the hull's D/2 + 1 floats.
+    unsigned char* const settled = reinterpret_cast<unsigned char*>(Z64) + rup(2 * D + 4, 16);
+    static_assert(rup(2 * D + 4, 16) + D <= C::NA * 16, "settled-root marks fit");
     R2 z[RR];
     bool conv[RR];
 #pragma unroll
@@ -1176,7 +1235,10 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
         z[r] = mk<R2>((R)(rad * cs), (R)(rad * sn));
       }
       conv[r] = (i >= D) || constant;
-      if (i < D) Zs[i] = z[r];
+      if (i < D) {
+        Zs[i] = z[r];
+        if constexpr (C::kSettle) settled[i] = 0;
+      }
     }
     __syncwarp();
     // Iterations over all RR slots per lane until every group of the warp has
@@ -1192,19 +1254,19 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
       int idx[RR];
 #pragma unroll
       for (int r = 0; r < RR; ++r) idx[r] = r * G + gl < D ? r * G + gl : -1;
-      if (aberth_run<G, RR, RS, D, C::kAccept>(z, conv, idx, Fs, Zs, tol, iters, a.maxit)) {
+      if (aberth_run<G, RR, RS, D, C::kAccept, C::kSettle>(z, conv, idx, Fs, Zs, tol, iters, a.maxit, settled)) {
         if constexpr (RS < RR) {
           R2 z2[RS];
           bool c2[RS];
           int i2[RS];
           compact_roots<G, RR, RS>(conv, idx, act, Zs, gl, z2, c2, i2);
-          if (aberth_run<G, RS, RT, D, C::kAccept>(z2, c2, i2, Fs, Zs, tol, iters, a.maxit)) {
+          if (aberth_run<G, RS, RT, D, C::kAccept, C::kSettle>(z2, c2, i2, Fs, Zs, tol, iters, a.maxit, settled)) {
             if constexpr (RT < RS) {
               R2 z3[RT];
               bool c3[RT];
               int i3[RT];
               compact_roots<G, RS, RT>(c2, i2, act, Zs, gl, z3, c3, i3);
-              aberth_run<G, RT, RT, D, C::kAccept>(z3, c3, i3, Fs, Zs, tol, iters, a.maxit);
+              aberth_run<G, RT, RT, D, C::kAccept, C::kSettle>(z3, c3, i3, Fs, Zs, tol, iters, a.maxit, settled);
 #pragma unroll
               for (int k = 0; k < RT; ++k) lane_nc = lane_nc || !c3[k];
             }
@@ -1224,8 +1286,11 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
       // of F to the working precision (the lanes split the roots): stalled
       // clusters are accepted here and need no re-solve
       bool bad = false;
+      // (settled roots lie off the circle by construction and are not
+      // zeros of F to the working precision)
       if (nonconv)
-        for (int i = gl; i < D; i += G) bad = bad || !pseudo_zero<D, R>(Zs[i], Fs);
+        for (int i = gl; i < D; i += G)
+          bad = bad || (!(C::kSettle && settled[i]) && !pseudo_zero<D, R>(Zs[i], Fs));
       nonconv = gor<G>(bad);
     }
 
