@@ -1,5 +1,6 @@
-// Instantiations of the assembly + roots kernel for float2 sums from the FP32 NFFT, FP32 Aberth (mixed path), H = 1..16.
-#include "ftp_roots.cuh"
+// Instantiations of the root-stage kernels for float2 sums from the FP32 NFFT, FP32 Aberth (mixed
+// path), H = 1..16: the first kernel and the one-lane-per-item evaluation kernel.
+#include "ftp_eval.cuh"
 
 namespace ftp {
 
@@ -23,7 +24,7 @@ int launch_roots_mixed(const RootsArgs& a, int num_sms, cudaStream_t s) {
   switch (a.H) {
 #define FTP_CASE(h) \
   case h:           \
-    return roots::launch_h<float2, float, h, pick_g(h)>(a, num_sms, s);
+    return roots::launch_h_mixed<h, pick_g(h)>(a, num_sms, s);
     FTP_CASE(1) FTP_CASE(2) FTP_CASE(3) FTP_CASE(4) FTP_CASE(5) FTP_CASE(6) FTP_CASE(7) FTP_CASE(8)
     FTP_CASE(9) FTP_CASE(10) FTP_CASE(11) FTP_CASE(12) FTP_CASE(13) FTP_CASE(14) FTP_CASE(15)
     FTP_CASE(16)
