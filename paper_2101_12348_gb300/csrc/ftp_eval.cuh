@@ -48,16 +48,20 @@ __device__ __forceinline__ void eval_sums(wide::ddc ps, const wide::ddc* KE, con
 #pragma unroll
   for (int i = 0; i < 9; ++i) v[i] = w_zero<W>();
   ddc pw = ps;
+  // the next e's sums are loaded one iteration ahead
+  float2 zn = Z(1), yn = Y(1);
 #pragma unroll 1
   for (int e = 1; e <= 2 * H; ++e) {
-    const float2 z = Z(e);
+    const float2 z = zn;
+    const float2 y = yn;
+    if (e < 2 * H) zn = Z(e + 1);
+    if (e < H) yn = Y(e + 1);
     const ddc zc = mkc(w_off<W>(z.x), w_off<W>(-z.y));  // conj(Z_e)
     const ddc t = c_mul<W>(c_mul<W>(zc, KE[e]), pw);
     v[0] = w_add(v[0], re(t));
     v[1] = w_add(v[1], w_mulf(im(t), (float)e));
     v[2] = w_add(v[2], w_mulf(re(t), (float)(e * e)));
     if (e <= H) {
-      const float2 y = Y(e);
       const ddc al = AL[e - 1];
       const ddc tb = c_mul<W>(c_mul<W>(al, mkc(w_off<W>(y.x), w_off<W>(-y.y))), pw);
       v[3] = w_add(v[3], re(tb));
