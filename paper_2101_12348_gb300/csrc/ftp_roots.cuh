@@ -304,6 +304,8 @@ __device__ __noinline__ bool pseudo_zero(R2 z, const R2* Fs) {
 // zeros of F whatever the other approximations are).
 constexpr float kSettleStep = 1e-2f, kSettleDom = 0.1f, kSettleDist = 50.0f,
                 kSettleGap = 1e-3f;
+// Candidate roots: | |z|^2 - 1 | below this (|z| within about 0.05 of 1).
+constexpr float kNearCircle = 0.1f;
 
 // One Aberth-Ehrlich iteration for the NS root slots of a lane.  Slot r holds
 // root idx[r] of the item (idx < 0: an empty slot, marked converged), z[r] its
@@ -1294,22 +1296,62 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
       nonconv = gor<G>(bad);
     }
 
-    // ---- candidates: P at every root scaled onto |psi| = 1 (working precision).
-    //      Rolled loops over the lane's root slots (roots read back from
-    //      shared memory): this phase runs once per item, so its code is kept
-    //      short rather than unrolled.
+    // ---- candidates: P at the roots near the unit circle, scaled onto
+    //      |psi| = 1 (working precision).  Only zeros of F on the circle are
+    //      stationary points of P; the others (pairs z, 1/conj(z)) add
+    //      candidates that cannot beat the best stationary value.  The group
+    //      lists its roots with | |z|^2 - 1 | < kNearCircle (|z| within about
+    //      0.05 of 1, far beyond the working-precision error of a root on the
+    //      circle) in the compaction array, which is free now, and scores the
+    //      list: one round of the loop in nearly every item instead of RR.  A
+    //      group with no such root scores every root.  Rolled loops (roots
+    //      read back from shared memory): this phase runs once per item.
+    short* const cand = reinterpret_cast<short*>(Z64);
+    int ncand = 1;
+    bool every_root = true;
+    {
+      bool near[RR];
+      int mine = 0;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        const int i = r * G + gl;
+        near[r] = !constant && i < D && fabs(cabs2(Zs[i]) - R(1)) < R(kNearCircle);  // NaN: no
+        mine += near[r] ? 1 : 0;
+      }
+      int incl = mine;  // every lane runs the shuffles (groups differ in `constant`)
+#pragma unroll
+      for (int sh = 1; sh < G; sh <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, sh, G);
+        if (gl >= sh) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, G - 1, G);
+      int pos = incl - mine;
+#pragma unroll
+      for (int r = 0; r < RR; ++r)
+        if (near[r]) cand[pos++] = (short)(r * G + gl);
+      if (!constant) {
+        every_root = total == 0;
+        ncand = every_root ? D : total;
+      }
+    }
+    __syncwarp();
+    int nround = (ncand + G - 1) / G;  // rounds: the warp's longest list
+#pragma unroll
+    for (int sh = G; sh < 32; sh <<= 1) nround = max(nround, __shfl_xor_sync(0xffffffffu, nround, sh));
     R sc[RR], key[RR];
+    int rix[RR];
     R lmax = R(-1);
     const R a0w = Aw[0].x;
 #pragma unroll 1
-    for (int r = 0; r < RR; ++r) {
-      const int i = r * G + gl;
+    for (int r = 0; r < nround; ++r) {
+      const int q = r * G + gl;
+      const int i = q < ncand ? (every_root ? q : (int)cand[q]) : -1;
       R s = R(-1), kk = R(0);
       bool have = false;
       R2 p = mk<R2>(1, 0);
       if (constant) {
         have = (i == 0);
-      } else if (i < D) {
+      } else if (i >= 0) {
         const R2 zi = Zs[i];
         const R m2 = cabs2(zi);
         have = m2 > R(0) && isfinite(m2);
@@ -1328,6 +1370,7 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
       }
       sc[r] = s;
       key[r] = kk;
+      rix[r] = i;
     }
     const R pmax = gmax<G>(lmax);
     const R thr = pmax - tie * (pmax > R(0) ? pmax : R(0));
@@ -1336,10 +1379,10 @@ __global__ void __launch_bounds__(128, roots_min_blocks<R, H, PH>()) roots_kerne
     R bkey = R(1e30);
     int bslot = -1;
 #pragma unroll 1
-    for (int r = 0; r < RR; ++r)
+    for (int r = 0; r < nround; ++r)
       if (sc[r] >= thr && sc[r] >= R(0) && key[r] < bkey) {
         bkey = key[r];
-        bslot = r * G + gl;
+        bslot = rix[r];
       }
     R2 bpsi = mk<R2>(1, 0);
     if (bslot >= 0 && !constant) {
