@@ -147,6 +147,7 @@ struct ftp_plan_s {
   // pinned host staging
   int* h_status = nullptr;
   unsigned long long* h_counters = nullptr;
+  int* h_redo_count = nullptr;  // pinned: length of the re-solve list after the main pass
   double2* h_alpha = nullptr;
   int* h_rows = nullptr;
   // instrumentation
@@ -484,12 +485,17 @@ cudaError_t reset_call(ftp_plan_t P) {
   return e;
 }
 
-ftp_status finish(ftp_plan_t P) {
+// Queues the read-back of the device status and the solver counters.
+ftp_status read_back(ftp_plan_t P) {
   FTP_CK(cudaMemcpyAsync(P->h_status, P->d_status, sizeof(int) * ST_WORDS,
                          cudaMemcpyDeviceToHost, P->stream));
   FTP_CK(cudaMemcpyAsync(P->h_counters, P->d_counters, sizeof(unsigned long long) * CNT_WORDS,
                          cudaMemcpyDeviceToHost, P->stream));
-  FTP_CK(cudaStreamSynchronize(P->stream));
+  return FTP_OK;
+}
+
+// The call's result from the values read back (the stream has finished).
+ftp_status finish_host(ftp_plan_t P) {
 #ifdef FTP_DEVICE_CHECKS
   if (P->h_status[ST_DBG_N] != 0) {
     fprintf(stderr, "ftp device check failed: site %d value %d bound %d (%d failures)\n",
@@ -512,6 +518,13 @@ ftp_status finish(ftp_plan_t P) {
     cudaGetLastError();
   }
   return (ftp_status)P->h_status[ST_CODE];
+}
+
+ftp_status finish(ftp_plan_t P) {
+  const ftp_status st = read_back(P);
+  if (st != FTP_OK) return st;
+  FTP_CK(cudaStreamSynchronize(P->stream));
+  return finish_host(P);
 }
 
 ftp_status check_templates(ftp_plan_t P, const ftp_template* tpl, int ntpl) {
@@ -651,25 +664,33 @@ ftp_status run_roots(ftp_plan_t P, RootsKind kind, const void* sums, int H, int 
 // the Aberth iteration cap are recomputed the same way with the larger cap
 // redo_maxit and a rounding-level acceptance of stalled roots, and on the
 // mixed path items still at the cap then once more with FP64 iterations.
-ftp_status solve(ftp_plan_t P, const double* dt, const double* dyv, const double* ddy,
-                 int64_t nobs, double df, int64_t k0, int64_t nf, int Hs,
-                 const std::vector<HGroup>& groups, const double2* alpha, const int* rows,
-                 const int* row0, double* const* o, uint8_t* flags, int64_t out_elems,
-                 int* launches) {
-  const bool redo = true;
-  if (redo) {
-    FTP_CK(cudaMemsetAsync(P->d_redo_mark, 0, sizeof(int) * nf, P->stream));
-    FTP_CK(cudaMemsetAsync(P->d_redo_count, 0, sizeof(int), P->stream));
-  }
+//
+// The main pass (solve_main) lists the frequencies to re-solve on the device;
+// the caller reads the list's length back with the call's status at the sync
+// the call makes anyway and runs the re-solve passes (solve_redo) only when
+// the list is not empty, so a call with nothing to re-solve launches none of
+// their kernels.
+ftp_status solve_main(ftp_plan_t P, int64_t nf, int Hs, const std::vector<HGroup>& groups,
+                      const double2* alpha, const int* rows, const int* row0, double* const* o,
+                      uint8_t* flags, int64_t out_elems, int* launches) {
+  FTP_CK(cudaMemsetAsync(P->d_redo_mark, 0, sizeof(int) * nf, P->stream));
+  FTP_CK(cudaMemsetAsync(P->d_redo_count, 0, sizeof(int), P->stream));
   const RootsKind kind = P->mixed ? ROOTS_MIXED : ROOTS_FP64;
   for (const HGroup& g : groups) {
-    ftp_status st = run_roots(P, kind, P->d_sums, g.H, Hs, nf, nullptr, nullptr, redo,
+    ftp_status st = run_roots(P, kind, P->d_sums, g.H, Hs, nf, nullptr, nullptr, true,
                               alpha + (size_t)g.first * kMaxH, row0 ? row0 : rows + g.first,
                               g.count, o, flags, nf, out_elems, launches, true);
     if (st != FTP_OK) return st;
   }
   ev_rec(P, 5);
-  if (!redo) return FTP_OK;
+  return FTP_OK;
+}
+
+ftp_status solve_redo(ftp_plan_t P, const double* dt, const double* dyv, const double* ddy,
+                      int64_t nobs, double df, int64_t k0, int64_t nf, int Hs,
+                      const std::vector<HGroup>& groups, const double2* alpha, const int* rows,
+                      const int* row0, double* const* o, uint8_t* flags, int64_t out_elems,
+                      int* launches) {
   launch_direct_sums(dt, dyv, ddy, nobs, P->d_moments, P->d_status, df, k0, P->d_redo_list,
                      P->d_redo_count, (int)nf, Hs, P->nf_pad, P->d_redo_sums,
                      (int64_t)3 * P->max_H * P->nf_pad, P->d_status, P->stream);
@@ -1742,6 +1763,7 @@ void ftp_destroy(ftp_plan_t P) {
   if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
   if (P->h_status) cudaFreeHost(P->h_status);
   if (P->h_counters) cudaFreeHost(P->h_counters);
+  if (P->h_redo_count) cudaFreeHost(P->h_redo_count);
   if (P->h_alpha) cudaFreeHost(P->h_alpha);
   if (P->h_rows) cudaFreeHost(P->h_rows);
   for (auto& e : P->ev)
@@ -1866,6 +1888,7 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
     return fail(FTP_ERR_CUDA);
   if (cudaMallocHost(&P->h_status, sizeof(int) * ST_WORDS) != cudaSuccess ||
       cudaMallocHost(&P->h_counters, sizeof(unsigned long long) * CNT_WORDS) != cudaSuccess ||
+      cudaMallocHost(&P->h_redo_count, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&P->h_alpha, sizeof(double2) * kMaxH * max_templates) != cudaSuccess ||
       cudaMallocHost(&P->h_rows, sizeof(int) * max_templates) != cudaSuccess)
     return fail(FTP_ERR_OOM);
@@ -2030,10 +2053,23 @@ ftp_status ftp_periodogram(ftp_plan_t P, const double* t, const double* y, const
     for (int i = 0; i < 4; ++i) o[i] = P->d_out + (size_t)i * P->max_templates * nf;
     of = flags ? P->d_flags : nullptr;
   }
-  st = solve(P, dt, dyv, ddy, nobs, P->grid.df, P->grid.k0, nf, Hs, groups, P->d_alpha, P->d_rows,
-             nullptr, o, of, direct ? (int64_t)nout : (int64_t)P->max_templates * nf, &launches);
+  const int64_t out_elems = direct ? (int64_t)nout : (int64_t)P->max_templates * nf;
+  st = solve_main(P, nf, Hs, groups, P->d_alpha, P->d_rows, nullptr, o, of, out_elems, &launches);
   if (st != FTP_OK) return st;
+  // status, counters and the re-solve list's length in one read-back
+  st = read_back(P);
+  if (st != FTP_OK) return st;
+  FTP_CK(cudaMemcpyAsync(P->h_redo_count, P->d_redo_count, sizeof(int), cudaMemcpyDeviceToHost,
+                         P->stream));
   ev_rec(P, 6);
+  FTP_CK(cudaStreamSynchronize(P->stream));
+  const bool redo = P->h_status[ST_CODE] == DEV_OK && *P->h_redo_count > 0;
+  if (redo) {
+    st = solve_redo(P, dt, dyv, ddy, nobs, P->grid.df, P->grid.k0, nf, Hs, groups, P->d_alpha,
+                    P->d_rows, nullptr, o, of, out_elems, &launches);
+    if (st != FTP_OK) return st;
+    ev_rec(P, 6);
+  }
   if (!direct) {
     double* dsto[4] = {power, theta1, theta2, theta3};
     for (int i = 0; i < 4; ++i)
@@ -2042,7 +2078,9 @@ ftp_status ftp_periodogram(ftp_plan_t P, const double* t, const double* y, const
       FTP_CK(cudaMemcpyAsync(flags, P->d_flags, nout, cudaMemcpyDefault, P->stream));
   }
   P->last_launches = launches;
-  return finish(P);
+  if (redo) return finish(P);
+  if (!direct) FTP_CK(cudaStreamSynchronize(P->stream));
+  return finish_host(P);
 }
 
 ftp_status ftp_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, const double* t,
