@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(const RootsArgs a) {
     return lo;
   };
 
+  // the a-posteriori error test's constants
+  const bool check_err = a.sum_err > 0.0;
+  const float se = (float)a.sum_err, rtol = (float)a.redo_tol;
   unsigned st_redo = 0, st_redo_nc = 0, st_final = 0;
   int cur_tau = -1, seg_hint = 0;
   const double* cur_mom = nullptr;
@@ -195,22 +198,26 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(const RootsArgs a) {
 #pragma unroll 1
     while (pending) {
       const int t0 = __shfl_sync(0xffffffffu, tau, __ffs(pending) - 1);
-      if (t0 != cur_tau) {  // warp-uniform: K_e and alpha_n of template t0
+      if (t0 != cur_tau) {  // warp-uniform: alpha_n, K_e and sum |alpha_n| of template t0
+        // (float-float from the FP64 alpha_n, one conversion each: the FP64 pipe
+        // of this GPU is ~75x slower than the FP32 one)
         __syncwarp();
         const double2* al = a.alpha + (size_t)t0 * kMaxH;
-        for (int e = lane; e <= 2 * H; e += 32) {
-          double2 kk = make_double2(0.0, 0.0);
-          for (int n = 1; n <= H; ++n) {
-            if (e - n >= 1 && e - n <= H) kk = cfma(al[n - 1], al[e - n - 1], kk);
-            if (n - e >= 1) kk = cfma(cscale(al[n - 1], 2.0), cconj(al[n - e - 1]), kk);
-          }
-          KE[e] = mkc(w_of<W>(kk.x), w_of<W>(kk.y));
-        }
         if (lane < H) AL[lane] = mkc(w_of<W>(al[lane].x), w_of<W>(al[lane].y));
+        __syncwarp();
+        for (int e = lane; e <= 2 * H; e += 32) {
+          WC kk = c_zero<W>();
+          for (int n = 1; n <= H; ++n) {
+            if (e - n >= 1 && e - n <= H) kk = c_add<W>(kk, c_mul<W>(AL[n - 1], AL[e - n - 1]));
+            if (n - e >= 1)
+              kk = c_add<W>(kk, c_mulf<W>(c_mul<W>(AL[n - 1], c_conj<W>(AL[n - e - 1])), 2.0f));
+          }
+          KE[e] = kk;
+        }
         if (lane == 0) {
-          double sa = 0.0;
-          for (int n = 0; n < H; ++n) sa += sqrt(cabs2(al[n]));
-          *SA = (float)sa;
+          float sa = 0.0f;
+          for (int n = 0; n < H; ++n) sa += sqrtf(w_f(c_abs2<W>(AL[n])));
+          *SA = sa;
         }
         cur_tau = t0;
         __syncwarp();
@@ -260,8 +267,10 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(const RootsArgs a) {
           if (pass == 1) {
             const W MM1 = w_sub(Q, w_mul(Mb, Mb));
             const W YM1 = w_mulf(v[3], 2.0f);
-            const double m0 = w_d(MM0), m1 = w_d(MM1), y0 = w_d(YM0), y1 = w_d(YM1);
-            if (m1 > 0.0 && y1 * y1 * m0 >= y0 * y0 * m1 * (1.0 - 1e-11)) {
+            // P1 >= P0 (1 - 1e-11): YM1^2 MM0 >= YM0^2 MM1 (1 - 1e-11), float-float
+            const W lhs = w_mul(w_mul(YM1, YM1), MM0);
+            const W rhs = w_mul(w_mul(w_mul(YM0, YM0), MM1), w_of<W>(1.0 - 1e-11));
+            if (w_f(MM1) > 0.0f && w_f(w_sub(lhs, rhs)) >= 0.0f) {
               MM = MM1;
               YM = YM1;
               Mbar = Mb;
@@ -341,18 +350,18 @@ __global__ void __launch_bounds__(128, 4) eval_kernel(const RootsArgs a) {
       // ---- a-posteriori error of P from the NFFT sums: |dZ| <= e gives
       //      |dMM| <= 9 e (sum|alpha|)^2 and |dYM| <= 2 e sum|alpha| sqrt(YY)
       bool redo = false;
-      if (a.sum_err > 0.0) {
+      if (check_err) {
         if (degenerate) {
           redo = true;
         } else {
-          const float sa = *SA, se = (float)a.sum_err;
+          const float sa = *SA;
           const float Pf = w_f(P), Mf = MMf;
           const float dMM = 9.0f * se * sa * sa;
           const float dYM = 2.0f * se * sa * (YYr * fast_rsqrt(YYr));
           const float q = fmaxf(Pf, 0.0f) * fast_rcp(YYr * Mf);
           const float sq = q > 0.0f ? q * fast_rsqrt(q) : 0.0f;
           const float err = Pf * dMM * fast_rcp(Mf) + 2.0f * sq * dYM;
-          redo = !(err <= (float)a.redo_tol);
+          redo = !(err <= rtol);
         }
       }
 
