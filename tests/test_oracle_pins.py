@@ -156,6 +156,36 @@ def test_brute_force_phase_scan(seed, H):
         assert abs(b[0] - r["theta3"][0]) <= 1e-8 * max(1.0, abs(b[0]))
 
 
+@pytest.mark.parametrize("H", [1, 2, 3, 6, 10, 16])
+def test_near_circle_roots_carry_the_best_power(H):
+    """Only zeros of F on the unit circle are stationary points of P(theta2),
+    so scoring the projections of the roots within about 0.05 of the circle
+    (| |z|^2 - 1 | < 0.1, the GPU kernels' candidate list) gives the same best
+    power as scoring every root (the paper's candidate set), and the same best
+    phase; the reduced list is never empty while P depends on theta2.  Also
+    checked: the best power agrees with a dense brute-force phase scan."""
+    for seed in range(3):
+        lc, tpl = small_case(seed, n_obs=60, H=H, signal=0.3 if seed != 1 else 0.0)
+        rng = np.random.default_rng(700 + 10 * H + seed)
+        for f in rng.uniform(0.1, 3.0, 3):
+            pol = oracle.polynomials_at(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s)
+            F = pol["F"] / np.max(np.abs(pol["F"]))
+            z = np.polynomial.polynomial.polyroots(F)
+            near = np.abs(np.abs(z) ** 2 - 1.0) < 0.1
+            assert near.any()
+            th_all = np.mod(np.angle(z), TWO_PI)
+            args = (lc.t, lc.y, pol["w"], pol["ybar"], pol["YY"], f, tpl.c, tpl.s)
+            P_all, t1_all, _, _ = oracle.fit_at_phase(*args, th_all)
+            P_near, t1_near, _, _ = oracle.fit_at_phase(*args, th_all[near])
+            assert abs(P_near.max() - P_all.max()) <= 1e-13 * max(P_all.max(), 1e-300)
+            b_all = oracle.choose_best(P_all, t1_all, th_all)
+            b_near = oracle.choose_best(P_near, t1_near, th_all[near])
+            assert abs(np.angle(np.exp(1j * (th_all[b_all] - th_all[near][b_near])))) <= 1e-9
+            if seed == 0:
+                Pb, _ = brute_force_best(lc.t, lc.y, lc.dy, f, tpl.c, tpl.s, n_grid=1 << 14)
+                assert abs(P_near.max() - Pb) <= 1e-9
+
+
 @pytest.mark.parametrize("seed", range(3))
 def test_bounds_and_mhls_ceiling(seed):
     """0 <= P_FTP <= P_MHLS(H) <= 1: the template model is nested in the
