@@ -99,7 +99,12 @@ typedef enum {
 
 #define FTP_MAX_H 16
 
-/* Trial-frequency grid f_k = (k0 + k) * df, k = 0..nf-1, k0 >= 1. */
+/* Trial-frequency grid f_k = (k0 + k) * df, k = 0..nf-1, k0 >= 1.  The last
+ * bin k0 + nf - 1 may be at most FTP_MAX_BIN: a grid beyond it would need an
+ * FFT of more than 2^31 cells, and ftp_plan and ftp_batch return
+ * FTP_ERR_UNSUPPORTED for it (df <= 0, k0 < 1 or nf < 1 are
+ * FTP_ERR_INVALID_ARG). */
+#define FTP_MAX_BIN ((int64_t)1 << 30)
 typedef struct {
   double df;
   int64_t k0;

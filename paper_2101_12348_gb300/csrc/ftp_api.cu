@@ -233,6 +233,19 @@ struct ftp_plan_s {
 
 namespace {
 
+// Largest harmonic bin (k0 + nf - 1) a grid may reach.  Any grid beyond it
+// needs more than the 2^31 FFT cells a 1-D cuFFT plan takes, so it is
+// unsupported; the bound is checked before any grid arithmetic, where
+// 2 H (k0 + nf - 1) could otherwise overflow and size a grid too small for
+// the bins the kernels read.
+constexpr int64_t kMaxBin = FTP_MAX_BIN;
+
+ftp_status check_grid(const ftp_grid& g) {
+  if (!(g.df > 0.0) || !isfinite(g.df) || g.k0 < 1 || g.nf < 1) return FTP_ERR_INVALID_ARG;
+  if (g.k0 > kMaxBin || g.nf > kMaxBin || g.k0 + g.nf - 1 > kMaxBin) return FTP_ERR_UNSUPPORTED;
+  return FTP_OK;
+}
+
 int64_t next_smooth(int64_t x) {
   if (x < 1) x = 1;
   for (int64_t v = x;; ++v) {
@@ -1178,8 +1191,8 @@ ftp_status run_batch(ftp_plan_t P, int64_t ncurves, const int64_t* obs_off, cons
     if (obs_off[c] < 0 || n < 2) return FTP_ERR_INVALID_ARG;
     if (n > P->max_nobs) return FTP_ERR_UNSUPPORTED;
     const ftp_grid& g = grids[c];
-    if (!(g.df > 0.0) || !isfinite(g.df) || g.k0 < 1 || g.nf < 1)
-      return FTP_ERR_INVALID_ARG;
+    const ftp_status gs = check_grid(g);
+    if (gs != FTP_OK) return gs;
     if (feat_only ? scr->feat_row[c] < 0 : out_off[c] < 0) return FTP_ERR_INVALID_ARG;
     if (g.nf > P->grid.nf) return FTP_ERR_UNSUPPORTED;
     if (!feat_only && tpl_of_curve && (tpl_of_curve[c] < 0 || tpl_of_curve[c] >= nbank))
@@ -1781,9 +1794,9 @@ ftp_status ftp_plan(ftp_plan_t* out, int64_t max_nobs, int max_H, ftp_grid grid,
   *out = nullptr;
   if (max_nobs < 2 || max_H < 1 || max_templates < 1) return FTP_ERR_INVALID_ARG;
   if (max_H > FTP_MAX_H) return FTP_ERR_UNSUPPORTED;
-  if (!(grid.df > 0.0) || !isfinite(grid.df) || grid.k0 < 1 || grid.nf < 1)
-    return FTP_ERR_INVALID_ARG;
   if (prec != FTP_FP64 && prec != FTP_MIXED) return FTP_ERR_INVALID_ARG;
+  const ftp_status gs = check_grid(grid);
+  if (gs != FTP_OK) return gs;
   if (max_nobs > ((int64_t)1 << 30)) return FTP_ERR_UNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

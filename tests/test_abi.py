@@ -51,6 +51,12 @@ def test_status_strings(lib):
     (dict(max_nobs=10, max_H=3, grid=(0.1, 0, 10)), 1),
     (dict(max_nobs=10, max_H=3, grid=(float("nan"), 1, 10)), 1),
     (dict(max_nobs=10, max_H=3, grid=(0.1, 1, 0)), 1),
+    # the last bin k0 + nf - 1 beyond 2^30 (an FFT of more than 2^31 cells),
+    # including bins whose grid arithmetic would overflow int64
+    (dict(max_nobs=10, max_H=3, grid=(0.1, 2**30, 2)), 8),
+    (dict(max_nobs=10, max_H=3, grid=(0.1, 1, 2**40)), 8),
+    (dict(max_nobs=10, max_H=3, grid=(0.1, 2**62, 10)), 8),
+    (dict(max_nobs=10, max_H=3, grid=(0.1, 2**62, 2**62)), 8),
 ])
 def test_plan_argument_validation(lib, args, expect):
     with pytest.raises(ftp.FtpError) as e:

@@ -291,6 +291,15 @@ def test_batch_matches_oracle(ftp, prec):
             ref = oracle.periodogram(lc.t, lc.y, lc.dy, g.freqs(), tp.c, tp.s)
             a = out2[c] + i * g.nf
             assert np.max(np.abs(o2[0][a:a + g.nf] - ref["power"])) <= TOL_P[prec]
+        # a curve whose grid reaches past the largest supported bin (here so
+        # far that 2 H (k0 + nf - 1) would overflow) is rejected on the host
+        # before any work is queued
+        bad = list(grids)
+        bad[1] = (grids[1][0], 2**62, grids[1][2])
+        with pytest.raises(ftp.FtpError) as e:
+            ftp.ftp_batch(plan.h, sv.obs_off, sv.t, sv.y, sv.dy, bad, out_off[:-1], bank,
+                          sv.tpl_of_curve, *o, fl)
+        assert e.value.status == 8
 
 
 @pytest.fixture(scope="module")
