@@ -204,6 +204,56 @@ def test_batch_survey_scale_sampled(ftp):
         assert np.max(np.abs(pc[sel] - ref["power"])) <= TOL_P["mixed"]
 
 
+def test_batch_full_survey_sampled(ftp, tmp_path):
+    """The batched survey at its full size, in the launch configuration the
+    benchmark times: 4096 curves from the same generator and seed, one mixed
+    plan on its own stream, device-resident arrays, step (a) lanes and roots
+    grid autotuned, then replayed from the captured graph.  Every power is
+    finite and in [0, 1], no item is left at the iteration cap, and on 16
+    sampled curves 20 random frequencies and the 3 highest peaks match the
+    oracle within 1e-4."""
+    sv = synth.survey(ncurves=4096, seed=1003)
+    bank = [(b.c, b.s) for b in sv.bank]
+    grid_t = [(g.df, g.k0, g.nf) for g in sv.grids]
+    out_off = np.zeros(sv.ncurves + 1, dtype=np.int64)
+    out_off[1:] = np.cumsum([g.nf for g in sv.grids])
+    tot = int(out_off[-1])
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream(device=dev)
+    dt, dyv, ddy = (torch.from_numpy(a).to(dev) for a in (sv.t, sv.y, sv.dy))
+    outs = [torch.empty(tot, dtype=torch.float64, device=dev) for _ in range(4)]
+    fl = torch.empty(tot, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    gj = max(sv.grids, key=lambda g: g.k0 + g.nf)
+    plan_grid = (gj.df, gj.k0, max(g.nf for g in sv.grids))
+    plan = ftp.ftp_plan(int(np.max(np.diff(sv.obs_off))), 6, plan_grid, len(bank), "mixed", 0,
+                        stream.cuda_stream)
+    try:
+        args = (plan, sv.obs_off, dt, dyv, ddy, grid_t, out_off[:-1], bank, sv.tpl_of_curve)
+        ftp.ftp_batch(*args, *outs, fl)
+        ftp.ftp_batch_autotune(*args, *outs, cache_path=str(tmp_path / "tuning.json"))
+        for _ in range(3):
+            ftp.ftp_batch(*args, *outs, fl)
+        assert ftp.ftp_batch_info(plan)["graph"] == 2
+        stats = ftp.ftp_solver_stats(plan)
+    finally:
+        ftp.ftp_destroy(plan)
+    assert stats["still_nonconverged"] == 0, stats
+    p = outs[0]
+    assert bool(torch.all(torch.isfinite(p)))
+    assert bool(torch.all((p >= -1e-6) & (p <= 1 + 1e-6)))
+    rng = np.random.default_rng(17)
+    for c in rng.choice(sv.ncurves, 16, replace=False):
+        lc = sv.curve(c)
+        g = sv.grids[c]
+        tp = sv.bank[sv.tpl_of_curve[c]]
+        pc = p[out_off[c]:out_off[c + 1]].cpu().numpy()
+        sel = np.unique(np.concatenate([rng.choice(g.nf, 20, replace=False),
+                                        np.argsort(-pc)[:3]]))
+        ref = oracle.periodogram(lc.t, lc.y, lc.dy, g.freqs()[sel], tp.c, tp.s)
+        assert np.max(np.abs(pc[sel] - ref["power"])) <= TOL_P["mixed"], c
+
+
 def test_batch_autotune_and_tuning_knobs(ftp, tmp_path):
     """ftp_batch_autotune times the step (a) lane count and the roots grid on
     the batch, keeps the fastest, writes them to the JSON cache, and a second
